@@ -1,0 +1,370 @@
+"""Benchmark: multislice ptychography loss + gradient (forward + adjoint) throughput on GB300.
+
+Workload (one step = one minibatch): 512x512x32 object of random ellipsoids, 128x128 probe
+with a random phase screen, 32x32 raster at 12 px with +-0.5 px jitter (1024 positions,
+minibatches of 128), 0.248 nm / 10 nm voxels, Poisson loss, gradients w.r.t. delta, beta,
+probe and positions, sqrt(L) checkpointing.  Unit of work: one (position, slice) forward +
+adjoint evaluation; one step is 128 x 32 = 4096 units.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  Multi-GPU (torchrun): every rank evaluates its own minibatches
+(the positions of an epoch are independent units), no collective on the data path, weak
+scaling; the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "position·slice fwd+adjoint evals/s vs plain GPU path at ≤1e-4 rel err; p50/p99"
+UNIT = "position·slice/s"
+WORKLOAD = "multislice"
+WORKLOAD_DESC = ("3D multislice far-field ptychography: object 512x512x32 (ellipsoids, delta<=5e-6, beta=delta/10), "
+                 "probe 128x128 with phase screen, 32x32 raster step 12 px +-0.5 px jitter, minibatch 128, "
+                 "Poisson loss, grads delta/beta/probe/positions, sqrt-checkpointing (every 6 of 32 slices)")
+SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def flops_per_unit(N: int) -> float:
+    """Algorithmic FP32 flops per (position, slice): 4 FFTs of N^2 (5 N^2 log2 N^2 each: forward
+    propagation 2, adjoint 2; checkpoint recompute not credited) + ~40 flops/pixel elementwise."""
+    return 4 * 5 * N * N * math.log2(N * N) + 40 * N * N
+
+
+def bytes_per_unit(N: int, L: int, cp: int) -> float:
+    """Algorithmic HBM bytes per (position, slice): delta+beta patch read (8 N^2), object-gradient
+    read-modify-write (16 N^2), checkpoint write+read (16 N^2 / cp)."""
+    return 8 * N * N + 16 * N * N + 16 * N * N / cp
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={SMI_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        try:
+            with open(self.path) as fh:
+                for line in fh:
+                    f = [t.strip() for t in line.split(",")]
+                    if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                        rows.append(f)
+            os.remove(self.path)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def _oracle_one(args):
+    import oracle
+    problem, d, b, probe, pos, Im = args
+    t = time.perf_counter()
+    oracle.loss_grad(problem, d, b, probe, pos, Im)
+    return time.perf_counter() - t
+
+
+def oracle_sample(w, I_meas_np, n_pos: int, workers: int):
+    """Time the FP64 oracle (as it stands) on n_pos positions of the minibatch, one position per
+    task, over a spawn pool of `workers` single-threaded processes.  Returns (wall s, positions)."""
+    import multiprocessing as mp
+    import numpy as np
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    N = w["problem"]["N"]
+    p = dict(w["problem"], B=1, Ly=N, Lx=N)
+    jobs = []
+    for i in range(n_pos):
+        # each task gets only its patch of the volume (the oracle reads nothing else for it)
+        pos = np.asarray(w["pos"][i:i + 1], np.float64)
+        c = np.floor(pos[0] + 0.5).astype(int)
+        crop = []
+        for vol in (w["delta"], w["beta"]):
+            out = np.zeros((vol.shape[0], N, N), vol.dtype)
+            ya, yb = max(c[0], 0), min(c[0] + N, vol.shape[1])
+            xa, xb = max(c[1], 0), min(c[1] + N, vol.shape[2])
+            out[:, ya - c[0]:yb - c[0], xa - c[1]:xb - c[1]] = vol[:, ya:yb, xa:xb]
+            crop.append(out)
+        jobs.append((p, crop[0], crop[1], w["probe"], pos - c, I_meas_np[i:i + 1]))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        pool.map(_oracle_one, jobs[:workers])          # warm: imports, DFT matrices
+        t = time.perf_counter()
+        pool.map(_oracle_one, jobs)
+        wall = time.perf_counter() - t
+    return wall, n_pos
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import numpy as np
+    from paper_2012_12686_gb300 import synth
+    w = synth.workload(WORKLOAD, seed=0)
+    L = w["problem"]["L"]
+    # measured data for the sampled positions come from the oracle itself (no GPU on this arm)
+    import oracle
+    cores = os.cpu_count() or 1
+    n_pos = cores
+    sample_pos = w["pos"][:n_pos]
+    Im = synth.poisson(oracle.forward(dict(w["problem"], B=n_pos), w["delta_meas"], w["beta_meas"], w["probe"],
+                                      sample_pos), 7)
+    ws = dict(w, pos=sample_pos)
+    budget_s = 150.0
+    times = []
+    t_all = time.perf_counter()
+    steps_run = 0
+    for k in range(args.warmup + args.steps):
+        wall, npos = oracle_sample(ws, Im, n_pos, cores)
+        if k >= args.warmup:
+            times.append(wall)
+            steps_run += 1
+        if time.perf_counter() - t_all > budget_s and steps_run >= 1:
+            break
+    mean_s = statistics.mean(times)
+    value = n_pos * L / mean_s
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": steps_run,
+            "warmup": args.warmup, "ms_per_step": mean_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD_DESC, "sample": f"{n_pos} positions x {L} slices per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n_pos} positions x {L} slices of one minibatch per step, "
+                                       f"one position per single-threaded process"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2012_12686_gb300 import synth
+    from paper_2012_12686_gb300.adorym import Engine, Problem
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    w = synth.workload(WORKLOAD, seed=0)
+    p = w["problem"]
+    N, L, B, M = p["N"], p["L"], p["B"], p["M"]
+    cp = p["checkpoint_every"] or int(math.ceil(math.sqrt(L)))
+    all_pos = w["all_pos"]
+    nb = len(all_pos) // B
+    units = B * L * M
+    with torch.cuda.stream(stream):
+        d = torch.from_numpy(w["delta"]).to(dev)
+        b = torch.from_numpy(w["beta"]).to(dev)
+        dm = torch.from_numpy(w["delta_meas"]).to(dev)
+        bm = torch.from_numpy(w["beta_meas"]).to(dev)
+        probe = torch.from_numpy(w["probe"]).to(dev)
+        pos_all = torch.from_numpy(all_pos).to(dev)
+        eng = Engine(local_rank, stream.cuda_stream)
+        oid = eng.register_object(d, b)
+        oid_m = eng.register_object(dm, bm)
+        prob = Problem.of(p)
+        # measured data of the epoch: forward model of the second object + Poisson noise
+        I_meas = torch.empty((nb, B, N, N), dtype=torch.float32, device=dev)
+        for k in range(nb):
+            eng.forward(prob, oid_m, probe, pos_all[k * B:(k + 1) * B].contiguous(), I_meas[k])
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(1234)
+        I_meas = torch.poisson(I_meas, generator=gen)
+        pos_b = [pos_all[k * B:(k + 1) * B].contiguous() for k in range(nb)]
+        loss = torch.zeros((), dtype=torch.float64, device=dev)
+        gd, gb = torch.zeros_like(d), torch.zeros_like(b)
+        gp = torch.zeros_like(probe)
+        gpos = torch.zeros((B, 2), dtype=torch.float32, device=dev)
+        flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+        eng.enable_kernel_timing(True)
+
+        def step(k):
+            eng.loss_grad(prob, oid, probe, pos_b[k % nb], I_meas[k % nb], loss, gd, gb, gp, gpos)
+
+        for k in range(args.warmup):
+            step(rank + k * world)
+        stream.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    path_ms = []
+    with ClockSampler(local_rank) as clk, torch.cuda.stream(stream):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            step(rank + (args.warmup + k) * world)
+            ev[k][1].record(stream)
+            path_ms.append(eng.kernel_ms())
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+    step_ms = [a.elapsed_time(bq) for a, bq in ev]
+    t_ours = sum(step_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_ours], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ours = float(tt.item())
+    value = units * args.steps * world / t_ours
+    ms_sorted = sorted(step_ms)
+    p50 = ms_sorted[len(ms_sorted) // 2]
+    p99 = ms_sorted[min(len(ms_sorted) - 1, int(math.ceil(0.99 * len(ms_sorted))) - 1)]
+
+    # ---- end to end through the public C ABI with pinned host buffers
+    n_e2e = max(3, min(args.steps, 50))
+    h_meas = [I_meas[k].cpu().pin_memory() for k in range(nb)]
+    h_pos = [pb.cpu().pin_memory() for pb in pos_b]
+    h_probe = probe.cpu().pin_memory()
+    h_loss = np.zeros(1, np.float64)
+    h_gp = torch.zeros(probe.shape, dtype=torch.complex64).pin_memory()
+    h_gpos = torch.zeros((B, 2), dtype=torch.float32).pin_memory()
+    eng.enable_kernel_timing(False)
+    with torch.cuda.stream(stream):
+        for k in range(2):
+            eng.loss_grad(prob, oid, h_probe, h_pos[k % nb], h_meas[k % nb], h_loss, gd, gb, h_gp, h_gpos)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for k in range(n_e2e):
+            eng.loss_grad(prob, oid, h_probe, h_pos[k % nb], h_meas[k % nb], h_loss, gd, gb, h_gp, h_gpos)
+        t_e2e = time.perf_counter() - t0
+    e2e_val = units * n_e2e / t_e2e
+    if world > 1:
+        tt = torch.tensor([t_e2e / n_e2e], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_val = units * world / float(tt.item())
+    h2d = h_meas[0].numel() * 4 + h_pos[0].numel() * 4 + h_probe.numel() * 8 + h_gp.numel() * 8
+    d2h = 8 + h_gp.numel() * 8 + h_gpos.numel() * 4
+
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = (peaks.get("sm_max_mhz") or 2070.0)
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    k_ms = statistics.mean(path_ms)
+    achieved = units * flops_per_unit(N) / (k_ms * 1e-3) / 1e12
+    hbm_ach = units * bytes_per_unit(N, L, cp) / (k_ms * 1e-3) / 1e9
+    src = open(os.path.join(ROOT, "paper_2012_12686_gb300", "csrc", "k_path.cu"), "rb").read() + \
+        open(os.path.join(ROOT, "paper_2012_12686_gb300", "csrc", "fft_block.cuh"), "rb").read()
+    traffic = profiled_traffic(hashlib.sha256(src).hexdigest()[:16])
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "global_batch": B * world, "slices": L, "tile": N,
+                       "parallelism": f"replica{world}" if world > 1 else "single", "l2": "flushed between steps"},
+            "latency_ms": {"p50": p50, "p99": p99},
+            "gpu_launches": 4 * args.steps,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak, "traffic": traffic,
+                         "kernel": "k_path<128,far>", "kernel_ms": k_ms,
+                         "peak_note": f"FP32 FMA peak derived: {props.multi_processor_count} SMs x 128 lanes x 2 "
+                                      f"x {sm_max:.0f} MHz",
+                         "hbm_algorithmic_gbs": hbm_ach, "hbm_peak_gbs": peaks.get("hbm_gbs", 6795.5)},
+            "clocks": clk.summary(), "wall_s_timed": wall}
+    if not args.no_cpu_baseline and world == 1:
+        cores = os.cpu_count() or 1
+        n_pos = 2 * cores
+        Im_np = I_meas[0, :n_pos].cpu().numpy()
+        ws = dict(w, pos=pos_b[0][:n_pos].cpu().numpy())
+        wall_c, npos = oracle_sample(ws, Im_np, n_pos, cores)
+        line["cpu_baseline"] = {"value": npos * L / wall_c, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{npos} positions x {L} slices of one minibatch, one position per "
+                                          f"single-threaded process ({wall_c:.1f} s wall)"}
+    print(json.dumps(line), flush=True)
+
+
+def profiled_traffic(src_hash: str):
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary, if it was taken
+    on the current kernel source (else null)."""
+    path = os.path.join(ROOT, "profiles", "k_path_multislice_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        return rec["dram_bytes_per_launch"] if rec.get("source_sha256_16") == src_hash else None
+    except Exception:
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * adorym.h -- C ABI of the GB300 loss-and-gradient engine for the multislice ptychography
+ * forward model of Adorym (Du et al., arXiv 2012.12686).
+ *
+ * The engine evaluates, for a minibatch of probe positions, the forward model y = F(x, theta)
+ * (Sec. 1, Eq. forward_model) of Algorithm 1 -- Fourier-shifted probe (Eq. fourier_shift),
+ * multislice propagation through the refractive-index object (Eqs. ri_modulation,
+ * fresnel_prop, paraxial_kernel), far-field (Eq. fraunhofer) or near-field Fresnel
+ * propagation to the detector, incoherent sum over probe modes (Eq. multimode) -- the data
+ * mismatch L (Eq. loss_function, in the forms of Eq. lsq_loss or Eq. poisson_loss), and the
+ * gradient of L with respect to the object (delta, beta), the probe and the probe positions
+ * (Sec. 2.3.2 "refinable parameters": probe position, and for holography the per-hologram
+ * translation of Eq. affine_transform).
+ *
+ * Conventions
+ *   - Object volumes are planar FP32, slice-major [Lz][Ly][Lx] (z along the beam).  The
+ *     paper's [Ly][Lx][Lz][2] layout (Sec. 2.1, ObjectFunction) maps to two such arrays.
+ *   - Complex arrays are interleaved (re, im) FP32 pairs, row-major [..][N][N].
+ *   - Positions are (y, x) in pixels of the object grid; the patch corner is
+ *     floor(pos + 1/2) and the residual is applied as a Fourier shift of the probe.
+ *   - Far-field patterns are in unshifted FFT order (DC at [0][0]); the far field is the
+ *     unitary transform with a positive exponent (negative phase convention, Sec. 2.2).
+ *   - Complex gradients are returned as dL/dRe + i dL/dIm.
+ *   - Every call is stream-ordered on the context's CUDA stream.
+ *
+ * Pointers
+ *   Array arguments may be device pointers or host pointers (pinned or pageable), except the
+ *   registered object volumes and the object-gradient volumes, which must be device memory.
+ *   Host inputs are copied to device staging inside the call; host outputs are copied back
+ *   and the call then waits for the stream.  With only device pointers (and a device
+ *   loss_out) the call is asynchronous.  The caller owns every array; the library owns its
+ *   workspace, twiddle/propagator tables, checkpoints and CUDA graphs.
+ *
+ * Errors
+ *   Every entry point returns ADORYM_OK or an error code and never aborts; the message of the
+ *   last error of a context is returned by adorym_last_error().  Kernels index the object only
+ *   after bounds checks (pixels outside the volume read as vacuum and their gradients are
+ *   dropped), so no input can make them access memory out of range.
+ */
+#ifndef ADORYM_H
+#define ADORYM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ADORYM_OK 0
+#define ADORYM_EINVAL 1      /* invalid argument (sizes, pointers, unsupported configuration) */
+#define ADORYM_ENOMEM 2      /* device memory could not be obtained / admission refused       */
+#define ADORYM_ETIMEDOUT 3   /* adorym_poll: the request did not finish within the timeout    */
+#define ADORYM_EDEVICE 4     /* a CUDA error was reported (message in adorym_last_error)      */
+#define ADORYM_ENOENT 5      /* unknown object id or ticket                                    */
+
+#define ADORYM_LOSS_LSQ 0     /* Eq. lsq_loss: mean (sqrt(I+eps) - sqrt(I_meas+eps))^2        */
+#define ADORYM_LOSS_POISSON 1 /* Eq. poisson_loss: mean (I - I_meas log(I+eps))               */
+
+typedef struct adorym_ctx adorym_ctx;
+
+/* One loss/gradient problem (the paper's reconstruct_ptychography parameters that reach the
+ * forward model, Sec. 2.7 "User interface", reduced to dimensionless pixel units). */
+typedef struct adorym_problem {
+  int N;              /* tile (probe / detector) side in pixels: 8..128 (powers of two);
+                         near field also 256, 512, 1024                                    */
+  int L;              /* slices each wave traverses                                        */
+  int M;              /* incoherent probe modes (Eq. multimode)                            */
+  int B;              /* far field: positions in the minibatch; near field: problems        */
+  int Ly, Lx, Lz;     /* object dims; must equal the registered object's.  Far field:
+                         Lz == L.  Near field: Ly == Lx == N and Lz == B * L (problem b uses
+                         slices [b L, (b+1) L)).                                           */
+  double kdz;         /* k * dz, k = 2 pi / lambda (Eq. ri_modulation)                      */
+  double lambda_dz_over_px2; /* lambda dz / dx^2: slice-to-slice paraxial step (Eq. paraxial_kernel) */
+  int farfield;       /* 1: far-field ptychography (Eq. fraunhofer); 0: near-field holography */
+  int n_dist;         /* near field: number of sample-detector distances (1..4)              */
+  double nf[4];       /* near field: Fresnel numbers dx^2 / (lambda z) of the distances       */
+  int loss;           /* ADORYM_LOSS_LSQ or ADORYM_LOSS_POISSON                              */
+  double eps;         /* eps of the loss terms (added to I and I_meas in LSQ, inside the log) */
+  int tomo;           /* 1: sample the object rotated by theta about y (Eq. rotation_transform) */
+  double theta;       /* tilt angle in radians                                              */
+  int checkpoint_every; /* adjoint checkpoint spacing in slices; 0 = ceil(sqrt(L))          */
+} adorym_problem;
+
+/* Create a context on CUDA device `device`, enqueueing on `cuda_stream` (a cudaStream_t; NULL =
+ * the legacy default stream).  *ctx receives the context.  Returns EINVAL / EDEVICE on failure. */
+int adorym_create(adorym_ctx** ctx, int device, void* cuda_stream);
+
+/* Wait for the context's work, release its workspace, graphs and serving threads. */
+void adorym_destroy(adorym_ctx* ctx);
+
+/* Message of the most recent error on this context ("" if none).  Owned by the context. */
+const char* adorym_last_error(adorym_ctx* ctx);
+
+/* Register a resident object volume: delta, beta device pointers to FP32 [Lz][Ly][Lx]
+ * (Sec. 2.1 refractive-index representation n = 1 - delta - i beta).  The memory stays owned
+ * by the caller and must outlive the registration; its contents may change between calls
+ * (an optimiser updating the object in place).  *obj_id receives the handle. */
+int adorym_register_object(adorym_ctx* ctx, const float* delta, const float* beta, int Lz, int Ly, int Lx,
+                           int* obj_id);
+
+/* Drop a registration.  Host-side only: work already enqueued keeps the volume pointers it was
+ * given, so the caller keeps the memory alive until that work has completed. */
+int adorym_unregister_object(adorym_ctx* ctx, int obj_id);
+
+/* Forward model only: predicted intensities y = F(x, theta) (Eq. forward_model, Algorithm 1).
+ *   probe  complex [M][N][N]: far field the probe modes; near field the illumination.
+ *   pos    far field [B][2] (y, x); near field per-hologram shifts [B][n_dist][2].
+ *   I_out  far field [B][N][N]; near field [B][n_dist][N][N] (FP32, overwritten). */
+int adorym_forward(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const float* probe, const float* pos,
+                   float* I_out);
+
+/* Loss and gradients (Eq. loss_function with Eq. lsq_loss / Eq. poisson_loss, averaged over the
+ * batch's detector pixels; adjoint with sqrt(L) checkpointing).
+ *   I_meas   measured intensities, same shape as I_out of adorym_forward.
+ *   loss_out one double (host or device), overwritten.  May be NULL.
+ *   g_delta, g_beta  device FP32 [Lz][Ly][Lx]; the gradient is ADDED (+=).  NULL skips both.
+ *   g_probe  complex [M][N][N]; ADDED (+=).  NULL skips it.
+ *   g_pos    far field [B][2] dL/dpos; near field [B][n_dist][2] dL/dshift; OVERWRITTEN.
+ *            NULL skips it.
+ *   I_out    optional predicted intensities (overwritten), or NULL. */
+int adorym_loss_grad(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const float* probe, const float* pos,
+                     const float* I_meas, double* loss_out, float* g_delta, float* g_beta, float* g_probe,
+                     float* g_pos, float* I_out);
+
+/* A loss/gradient request for the serving loop: the arguments of adorym_loss_grad. */
+typedef struct adorym_request {
+  adorym_problem problem;
+  int obj_id;
+  const float* probe;
+  const float* pos;
+  const float* I_meas;
+  double* loss_out;
+  float* g_delta;
+  float* g_beta;
+  float* g_probe;
+  float* g_pos;
+  float* I_out;
+} adorym_request;
+
+/* Serving loop.  adorym_submit queues a request and returns at once with *ticket.  A request
+ * is admitted when a slot is free and its device workspace fits the context's footprint
+ * budget; admitted requests run concurrently on separate streams as captured CUDA graphs
+ * (one graph per problem shape and slot), so requests that arrive while others run overlap
+ * with them on the device.  Array pointers must be device memory and stay valid until the
+ * request completes.  Requests whose footprint can never fit return ENOMEM at submit. */
+int adorym_submit(adorym_ctx* ctx, const adorym_request* req, uint64_t* ticket);
+
+/* Wait up to timeout_us microseconds (<0: forever, 0: test) for a ticket.  Returns ADORYM_OK
+ * once the request's outputs are complete (the ticket is then retired), ETIMEDOUT if it is still
+ * queued or running, ENOENT for an unknown ticket, or the request's own error code. */
+int adorym_poll(adorym_ctx* ctx, uint64_t ticket, int64_t timeout_us);
+
+/* Serving configuration: number of concurrent slots (streams, 1..16) and the device-memory
+ * footprint budget in bytes for admitted requests' workspaces (0 = no limit).  Only allowed
+ * while no request is in flight. */
+int adorym_serve_config(adorym_ctx* ctx, int slots, uint64_t budget_bytes);
+
+/* Serving statistics since the context was created: completed requests and the number of
+ * times a request had to wait for admission. */
+int adorym_serve_stats(adorym_ctx* ctx, uint64_t* completed, uint64_t* admission_waits);
+
+/* Kernel timing for roofline measurements.  With enable = 1, each later direct call records a
+ * CUDA event pair around its fused path kernel on the context's stream (not inside serving
+ * graphs).  adorym_kernel_ms returns the path kernel time of the most recent such call in
+ * milliseconds (it waits for that call's stop event). */
+int adorym_enable_kernel_timing(adorym_ctx* ctx, int enable);
+int adorym_kernel_ms(adorym_ctx* ctx, float* path_ms);
+
+/* Device workspace (bytes) that adorym_loss_grad needs for this problem, for admission
+ * planning by callers.  grads: bitmask 1 = object, 2 = probe, 4 = positions. */
+int adorym_workspace_bytes(const adorym_problem* p, int grads, uint64_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADORYM_H */

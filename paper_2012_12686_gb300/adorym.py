@@ -1,0 +1,214 @@
+"""ctypes binding of ``libadorym.so`` (argument marshalling only).
+
+Every step of the loss/gradient path runs in the library's CUDA kernels; this module only
+converts Python/torch/numpy arguments to the C ABI declared in ``include/adorym.h``.  If the
+library has not been built the import fails loudly: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libadorym.so")
+
+OK, EINVAL, ENOMEM, ETIMEDOUT, EDEVICE, ENOENT = 0, 1, 2, 3, 4, 5
+LOSS = {"lsq": 0, "poisson": 1}
+
+EXPORTS = ["adorym_create", "adorym_destroy", "adorym_last_error", "adorym_register_object",
+           "adorym_unregister_object", "adorym_forward", "adorym_loss_grad", "adorym_submit", "adorym_poll",
+           "adorym_serve_config", "adorym_serve_stats", "adorym_workspace_bytes", "adorym_enable_kernel_timing",
+           "adorym_kernel_ms"]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_int), ("M", ctypes.c_int), ("B", ctypes.c_int),
+                ("Ly", ctypes.c_int), ("Lx", ctypes.c_int), ("Lz", ctypes.c_int),
+                ("kdz", ctypes.c_double), ("lambda_dz_over_px2", ctypes.c_double),
+                ("farfield", ctypes.c_int), ("n_dist", ctypes.c_int), ("nf", ctypes.c_double * 4),
+                ("loss", ctypes.c_int), ("eps", ctypes.c_double), ("tomo", ctypes.c_int),
+                ("theta", ctypes.c_double), ("checkpoint_every", ctypes.c_int)]
+
+    @staticmethod
+    def of(d: dict) -> "Problem":
+        p = Problem()
+        for k in ("N", "L", "M", "B", "Ly", "Lx", "Lz"):
+            setattr(p, k, int(d[k]))
+        p.kdz = float(d["kdz"])
+        p.lambda_dz_over_px2 = float(d.get("lambda_dz_over_px2", 0.0))
+        p.farfield = int(d.get("farfield", 1))
+        nf = list(d.get("nf", []))
+        p.n_dist = len(nf)
+        for i, v in enumerate(nf[:4]):
+            p.nf[i] = float(v)
+        loss = d.get("loss", "lsq")
+        p.loss = LOSS[loss] if isinstance(loss, str) else int(loss)
+        p.eps = float(d.get("eps", 1e-6))
+        p.tomo = int(d.get("tomo", 0))
+        p.theta = float(d.get("theta", 0.0))
+        p.checkpoint_every = int(d.get("checkpoint_every", 0))
+        return p
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("problem", Problem), ("obj_id", ctypes.c_int),
+                ("probe", ctypes.c_void_p), ("pos", ctypes.c_void_p), ("I_meas", ctypes.c_void_p),
+                ("loss_out", ctypes.c_void_p), ("g_delta", ctypes.c_void_p), ("g_beta", ctypes.c_void_p),
+                ("g_probe", ctypes.c_void_p), ("g_pos", ctypes.c_void_p), ("I_out", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2012_12686_gb300.build` "
+                               "(the CUDA path has no fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64
+        L.adorym_create.argtypes = [ctypes.POINTER(vp), i32, vp]
+        L.adorym_destroy.argtypes = [vp]
+        L.adorym_destroy.restype = None
+        L.adorym_last_error.argtypes = [vp]
+        L.adorym_last_error.restype = ctypes.c_char_p
+        L.adorym_register_object.argtypes = [vp, vp, vp, i32, i32, i32, ctypes.POINTER(i32)]
+        L.adorym_unregister_object.argtypes = [vp, i32]
+        L.adorym_forward.argtypes = [vp, ctypes.POINTER(Problem), i32, vp, vp, vp]
+        L.adorym_loss_grad.argtypes = [vp, ctypes.POINTER(Problem), i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.adorym_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(u64)]
+        L.adorym_poll.argtypes = [vp, u64, ctypes.c_int64]
+        L.adorym_serve_config.argtypes = [vp, i32, u64]
+        L.adorym_serve_stats.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        L.adorym_workspace_bytes.argtypes = [ctypes.POINTER(Problem), i32, ctypes.POINTER(u64)]
+        L.adorym_enable_kernel_timing.argtypes = [vp, i32]
+        L.adorym_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+        for name in EXPORTS:
+            if name not in ("adorym_destroy", "adorym_last_error"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Address of a torch tensor / numpy array (must be contiguous), an int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported argument type {type(x)}")
+
+
+class AdorymError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"adorym error {code}: {msg}")
+        self.code = code
+
+
+class Engine:
+    """One library context bound to a CUDA device and stream (default: torch's current stream)."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self._ctx = ctypes.c_void_p()
+        rc = lib().adorym_create(ctypes.byref(self._ctx), device, ctypes.c_void_p(stream))
+        if rc:
+            raise AdorymError(rc, "adorym_create failed")
+
+    def close(self):
+        if self._ctx:
+            lib().adorym_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return lib().adorym_last_error(self._ctx).decode()
+
+    def _check(self, rc):
+        if rc:
+            raise AdorymError(rc, self.last_error())
+        return rc
+
+    def register_object(self, delta, beta) -> int:
+        Lz, Ly, Lx = delta.shape
+        oid = ctypes.c_int()
+        self._check(lib().adorym_register_object(self._ctx, _ptr(delta), _ptr(beta), Lz, Ly, Lx, ctypes.byref(oid)))
+        return oid.value
+
+    def unregister_object(self, obj_id: int):
+        self._check(lib().adorym_unregister_object(self._ctx, obj_id))
+
+    def forward(self, problem, obj_id, probe, pos, I_out):
+        p = problem if isinstance(problem, Problem) else Problem.of(problem)
+        return self._check(lib().adorym_forward(self._ctx, ctypes.byref(p), obj_id, _ptr(probe), _ptr(pos),
+                                                _ptr(I_out)))
+
+    def loss_grad(self, problem, obj_id, probe, pos, I_meas, loss_out=None, g_delta=None, g_beta=None,
+                  g_probe=None, g_pos=None, I_out=None):
+        p = problem if isinstance(problem, Problem) else Problem.of(problem)
+        return self._check(lib().adorym_loss_grad(self._ctx, ctypes.byref(p), obj_id, _ptr(probe), _ptr(pos),
+                                                  _ptr(I_meas), _ptr(loss_out), _ptr(g_delta), _ptr(g_beta),
+                                                  _ptr(g_probe), _ptr(g_pos), _ptr(I_out)))
+
+    def enable_kernel_timing(self, on: bool = True):
+        self._check(lib().adorym_enable_kernel_timing(self._ctx, 1 if on else 0))
+
+    def kernel_ms(self) -> float:
+        v = ctypes.c_float()
+        self._check(lib().adorym_kernel_ms(self._ctx, ctypes.byref(v)))
+        return v.value
+
+    # ---- serving
+    def serve_config(self, slots: int, budget_bytes: int = 0):
+        self._check(lib().adorym_serve_config(self._ctx, slots, budget_bytes))
+
+    def submit(self, problem, obj_id, probe, pos, I_meas, loss_out=None, g_delta=None, g_beta=None,
+               g_probe=None, g_pos=None, I_out=None) -> int:
+        r = Request()
+        r.problem = problem if isinstance(problem, Problem) else Problem.of(problem)
+        r.obj_id = obj_id
+        for k, v in (("probe", probe), ("pos", pos), ("I_meas", I_meas), ("loss_out", loss_out),
+                     ("g_delta", g_delta), ("g_beta", g_beta), ("g_probe", g_probe), ("g_pos", g_pos),
+                     ("I_out", I_out)):
+            setattr(r, k, _ptr(v))
+        t = ctypes.c_uint64()
+        self._check(lib().adorym_submit(self._ctx, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = -1) -> int:
+        rc = lib().adorym_poll(self._ctx, ticket, timeout_us)
+        if rc not in (OK, ETIMEDOUT):
+            raise AdorymError(rc, self.last_error())
+        return rc
+
+    def serve_stats(self):
+        c, w = ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(lib().adorym_serve_stats(self._ctx, ctypes.byref(c), ctypes.byref(w)))
+        return c.value, w.value
+
+
+def workspace_bytes(problem, grads: int = 7) -> int:
+    p = problem if isinstance(problem, Problem) else Problem.of(problem)
+    out = ctypes.c_uint64()
+    rc = lib().adorym_workspace_bytes(ctypes.byref(p), grads, ctypes.byref(out))
+    if rc:
+        raise AdorymError(rc, "invalid problem")
+    return out.value

@@ -1,0 +1,480 @@
+// C ABI entry points: context, object registration, validation, workspace planning, FP64-built
+// tables, host-argument staging and the launch sequence of one loss/gradient call.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "engine.h"
+
+namespace adorym {
+
+static const double kPi = 3.14159265358979323846;
+
+static bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+
+int validate(const adorym_problem& p, std::string* err) {
+  auto bad = [&](const char* m) {
+    *err = m;
+    return ADORYM_EINVAL;
+  };
+  if (p.M < 1 || p.M > 64) return bad("M (probe modes) must be in 1..64");
+  if (p.B < 1 || p.B > 65535) return bad("B must be in 1..65535");
+  if (p.L < 1) return bad("L must be >= 1");
+  if (p.loss != ADORYM_LOSS_LSQ && p.loss != ADORYM_LOSS_POISSON) return bad("loss must be LSQ (0) or Poisson (1)");
+  if (!(p.eps >= 0.0)) return bad("eps must be >= 0");
+  if (!std::isfinite(p.kdz) || !std::isfinite(p.lambda_dz_over_px2)) return bad("kdz / lambda_dz_over_px2 not finite");
+  if (p.checkpoint_every < 0 || p.checkpoint_every > p.L) return bad("checkpoint_every must be in 0..L");
+  if (p.farfield) {
+    if (!pow2_in(p.N, 8, 128)) return bad("far field: N must be a power of two in 8..128");
+    if (p.Lz != p.L) return bad("far field: Lz must equal L (the wave crosses every slice)");
+    if (p.Ly < 1 || p.Lx < 1) return bad("object dims must be >= 1");
+    if (p.tomo && !std::isfinite(p.theta)) return bad("theta not finite");
+  } else {
+    if (!pow2_in(p.N, 8, 128)) return bad("near field: N must be a power of two in 8..128");
+    if (p.tomo) return bad("tomography is defined for the far-field geometry only");
+    if (p.Ly != p.N || p.Lx != p.N) return bad("near field: Ly == Lx == N (full-field tiles)");
+    if ((long long)p.Lz != (long long)p.B * p.L) return bad("near field: Lz must equal B * L");
+    if (p.n_dist < 1 || p.n_dist > 4) return bad("near field: n_dist must be in 1..4");
+    for (int d = 0; d < p.n_dist; ++d)
+      if (!(p.nf[d] > 0.0) || !std::isfinite(p.nf[d])) return bad("near field: Fresnel numbers must be > 0");
+  }
+  return ADORYM_OK;
+}
+
+static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan* pl, std::string* err) {
+  int rc = validate(p, err);
+  if (rc) return rc;
+  Plan q;
+  q.p = p;
+  q.far = p.farfield != 0;
+  q.tomo = p.tomo != 0;
+  q.adj = adj;
+  q.want_obj = adj && (grads & 1);
+  q.want_probe = adj && (grads & 2);
+  q.want_pos = adj && (grads & 4);
+  q.want_loss = want_loss;
+  q.nd = q.far ? 1 : p.n_dist;
+  q.cp = p.checkpoint_every > 0 ? p.checkpoint_every : (int)std::ceil(std::sqrt((double)p.L));
+  if (q.cp < 1) q.cp = 1;
+  q.ncp = (p.L + q.cp - 1) / q.cp;
+  const size_t N = p.N, NN = N * N, B = p.B, M = p.M, f2 = sizeof(float2);
+  q.NN = NN;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o += al(bytes);
+    return r;
+  };
+  q.off_phat = take(M * NN * f2);
+  if (adj) {
+    q.off_ckpt = take(B * M * q.ncp * NN * f2);
+    q.off_seg = take(B * M * q.cp * NN * f2);
+    q.off_park = take(B * N * (N + 1) * f2);
+    if (!q.far) q.off_fbar = take(B * NN * f2);
+    q.off_qacc = take(B * M * NN * f2);
+    q.off_qsum = take(M * NN * f2);
+  }
+  q.off_far = take(B * (q.far ? 1 : q.nd + 1) * M * NN * f2);
+  q.off_gI = take(B * q.nd * NN * sizeof(float));
+  q.off_lossp = take(B * sizeof(double));
+  q.off_loss = take(sizeof(double));
+  if (q.tomo) {
+    const size_t V = (size_t)p.Lz * p.Ly * p.Lx * sizeof(float);
+    q.off_rot = take(2 * V);
+    if (q.want_obj) q.off_grot = take(2 * V);
+  }
+  q.bytes_probe = M * NN * f2;
+  q.bytes_pos = B * q.nd * 2 * sizeof(float);
+  q.bytes_meas = B * q.nd * NN * sizeof(float);
+  q.bytes_iout = q.bytes_meas;
+  q.off_s_probe = take(q.bytes_probe);
+  q.off_s_pos = take(q.bytes_pos);
+  q.off_s_meas = take(q.bytes_meas);
+  q.off_s_gprobe = take(q.bytes_probe);
+  q.off_s_gpos = take(q.bytes_pos);
+  q.off_s_iout = take(q.bytes_iout);
+  q.total = o;
+  *pl = q;
+  return ADORYM_OK;
+}
+
+static std::string table_key(const adorym_problem& p) {
+  char buf[256];
+  int n = snprintf(buf, sizeof buf, "%d|%.17g|%d", p.N, p.lambda_dz_over_px2, p.farfield ? 0 : p.n_dist);
+  if (!p.farfield)
+    for (int d = 0; d < p.n_dist; ++d) n += snprintf(buf + n, sizeof buf - n, "|%.17g", p.nf[d]);
+  return std::string(buf);
+}
+
+static double freq(int k, int N) { return (double)(k <= (N - 1) / 2 ? k : k - N) / (double)N; }
+
+int get_tables(adorym_ctx* ctx, const adorym_problem& p, Tables* out) {
+  const std::string key = table_key(p);
+  auto it = ctx->tables.find(key);
+  if (it != ctx->tables.end()) {
+    *out = it->second;
+    return ADORYM_OK;
+  }
+  const int N = p.N, nd = p.farfield ? 0 : p.n_dist;
+  std::vector<float2> h((size_t)(3 + nd) * N);
+  for (int m = 0; m < N; ++m) {   // W_N^m = exp(-2 pi i m / N), FP64 argument
+    const double a = 2.0 * kPi * (double)m / (double)N;
+    h[m] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  }
+  for (int k = 0; k < N; ++k) {   // paraxial kernel factor exp(i pi c f^2) / N (Eq. paraxial_kernel)
+    const double f = freq(k, N), ph = kPi * p.lambda_dz_over_px2 * f * f;
+    const float2 v = make_float2((float)(std::cos(ph) / N), (float)(std::sin(ph) / N));
+    h[N + k] = v;
+    h[2 * N + k] = v;
+  }
+  for (int d = 0; d < nd; ++d) {  // exp(i pi f^2 / N_F): lambda z / dx^2 = 1 / N_F
+    for (int k = 0; k < N; ++k) {
+      const double f = freq(k, N), ph = kPi * f * f / p.nf[d];
+      h[(size_t)(3 + d) * N + k] = make_float2((float)std::cos(ph), (float)std::sin(ph));
+    }
+  }
+  Tables t;
+  t.N = N;
+  t.nd = nd;
+  cudaError_t e = cudaMalloc(&t.dev, h.size() * sizeof(float2));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->err = "table allocation failed";
+    return ADORYM_ENOMEM;
+  }
+  e = cudaMemcpy(t.dev, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    ctx->err = std::string("table upload: ") + cudaGetErrorString(e);
+    return ADORYM_EDEVICE;
+  }
+  ctx->tables[key] = t;
+  *out = t;
+  return ADORYM_OK;
+}
+
+int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs& c, char* ws, cudaStream_t s,
+            std::string* err, cudaEvent_t ev_start, cudaEvent_t ev_stop) {
+  const adorym_problem& p = pl.p;
+  auto W = [&](size_t off) { return ws + off; };
+  auto chk = [&](cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return ADORYM_OK;
+    *err = std::string(what) + ": " + cudaGetErrorString(e);
+    return ADORYM_EDEVICE;
+  };
+  const float *vd = obj.d, *vb = obj.b;
+  float *gd = c.gd, *gb = c.gb;
+  const size_t V = (size_t)p.Lz * p.Ly * p.Lx;
+  const double cth = std::cos(p.theta), sth = std::sin(p.theta);
+  int rc;
+  if (pl.tomo) {
+    float* rot = reinterpret_cast<float*>(W(pl.off_rot));
+    if ((rc = chk(launch_rotate(obj.d, obj.b, rot, rot + V, p.Lz, p.Ly, p.Lx, (float)cth, (float)sth, s), "rotate")))
+      return rc;
+    vd = rot;
+    vb = rot + V;
+    if (pl.want_obj) {
+      float* grot = reinterpret_cast<float*>(W(pl.off_grot));
+      if ((rc = chk(cudaMemsetAsync(grot, 0, 2 * V * sizeof(float), s), "memset"))) return rc;
+      gd = grot;
+      gb = grot + V;
+    }
+  }
+  float2* phat = reinterpret_cast<float2*>(W(pl.off_phat));
+  if (pl.far) {
+    if ((rc = chk(launch_probe_hat(p.N, p.M, c.probe, phat, tab.tw(), s), "probe_hat"))) return rc;
+  }
+  PathArgs a{};
+  a.N = p.N;
+  a.L = p.L;
+  a.M = p.M;
+  a.B = p.B;
+  a.Ly = p.Ly;
+  a.Lx = p.Lx;
+  a.cp = pl.cp;
+  a.ncp = pl.ncp;
+  a.loss = p.loss;
+  a.adj = pl.adj ? 1 : 0;
+  a.n_dist = pl.nd;
+  a.eps = (float)p.eps;
+  a.kdz = (float)p.kdz;
+  a.inv_npix = 1.0 / ((double)p.B * pl.nd * (double)pl.NN);
+  a.vd = vd;
+  a.vb = vb;
+  a.probe = c.probe;
+  a.phat = phat;
+  a.pos = c.pos;
+  a.I_meas = c.I_meas;
+  a.I_out = c.I_out;
+  a.tw = tab.tw();
+  a.hy = tab.hy();
+  a.hx = tab.hx();
+  a.hd = pl.far ? nullptr : tab.hd();
+  if (pl.adj) {
+    a.ckpt = reinterpret_cast<float2*>(W(pl.off_ckpt));
+    a.seg = reinterpret_cast<float2*>(W(pl.off_seg));
+    a.park = reinterpret_cast<float2*>(W(pl.off_park));
+    a.fbar = pl.far ? nullptr : reinterpret_cast<float2*>(W(pl.off_fbar));
+    a.qacc = pl.want_probe ? reinterpret_cast<float2*>(W(pl.off_qacc)) : nullptr;
+    a.gd = pl.want_obj ? gd : nullptr;
+    a.gb = pl.want_obj ? gb : nullptr;
+    a.gpos = pl.want_pos ? c.g_pos : nullptr;
+  }
+  a.far = reinterpret_cast<float2*>(W(pl.off_far));
+  a.gI = reinterpret_cast<float*>(W(pl.off_gI));
+  a.lossp = reinterpret_cast<double*>(W(pl.off_lossp));
+  if (ev_start) cudaEventRecord(ev_start, s);
+  if ((rc = chk(launch_path(a, pl.far ? 1 : 0, s), "path"))) return rc;
+  if (ev_stop) cudaEventRecord(ev_stop, s);
+  if (pl.adj && (pl.want_probe || c.loss)) {
+    if ((rc = chk(launch_probe_grad(p.N, p.M, p.B, pl.far ? 1 : 0, a.qacc, reinterpret_cast<float2*>(W(pl.off_qsum)),
+                                    pl.want_probe ? c.g_probe : nullptr, tab.tw(), a.lossp, a.inv_npix, c.loss, s),
+                  "probe_grad")))
+      return rc;
+  }
+  if (pl.tomo && pl.want_obj) {
+    if ((rc = chk(launch_rotate_T(gd, gb, c.gd, c.gb, p.Lz, p.Ly, p.Lx, (float)cth, (float)sth, s), "rotate_T")))
+      return rc;
+  }
+  return ADORYM_OK;
+}
+
+int prepare_kernels(const adorym_problem& p, std::string* err) {
+  cudaError_t e = prepare_path(p.N, p.farfield ? 1 : 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *err = std::string("kernel attributes: ") + cudaGetErrorString(e);
+    return ADORYM_EDEVICE;
+  }
+  return ADORYM_OK;
+}
+
+}  // namespace adorym
+
+using namespace adorym;
+
+static int fail(adorym_ctx* ctx, int rc, const std::string& m) {
+  ctx->err = m;
+  return rc;
+}
+
+static int cuda_fail(adorym_ctx* ctx, cudaError_t e, const char* what) {
+  cudaGetLastError();
+  ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return ADORYM_EDEVICE;
+}
+
+// 1 = device (or managed), 0 = host (pinned or pageable), -1 = null
+static int ptr_kind(const void* p) {
+  if (!p) return -1;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? 1 : 0;
+}
+
+static int ensure_ws(adorym_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_cap) return ADORYM_OK;
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->ws) cudaFree(ctx->ws);
+  ctx->ws = nullptr;
+  ctx->ws_cap = 0;
+  const size_t cap = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&ctx->ws, cap);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, ADORYM_ENOMEM, "workspace allocation of " + std::to_string(cap) + " bytes failed");
+  }
+  ctx->ws_cap = cap;
+  return ADORYM_OK;
+}
+
+extern "C" {
+
+int adorym_create(adorym_ctx** out, int device, void* stream) {
+  if (!out) return ADORYM_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return ADORYM_EDEVICE;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return ADORYM_EDEVICE;
+  adorym_ctx* c = new adorym_ctx();
+  c->device = device;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  *out = c;
+  return ADORYM_OK;
+}
+
+void adorym_destroy(adorym_ctx* ctx) {
+  if (!ctx) return;
+  serve_shutdown(ctx);
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->ws) cudaFree(ctx->ws);
+  for (auto& kv : ctx->tables) cudaFree(kv.second.dev);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  delete ctx;
+}
+
+const char* adorym_last_error(adorym_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int adorym_register_object(adorym_ctx* ctx, const float* delta, const float* beta, int Lz, int Ly, int Lx,
+                           int* obj_id) {
+  if (!ctx || !obj_id) return ADORYM_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (Lz < 1 || Ly < 1 || Lx < 1) return fail(ctx, ADORYM_EINVAL, "object dims must be >= 1");
+  if (ptr_kind(delta) != 1 || ptr_kind(beta) != 1)
+    return fail(ctx, ADORYM_EINVAL, "object volumes must be device memory");
+  Object o;
+  o.d = delta;
+  o.b = beta;
+  o.Lz = Lz;
+  o.Ly = Ly;
+  o.Lx = Lx;
+  const int id = ctx->next_obj++;
+  ctx->objects[id] = o;
+  *obj_id = id;
+  return ADORYM_OK;
+}
+
+int adorym_unregister_object(adorym_ctx* ctx, int obj_id) {
+  if (!ctx) return ADORYM_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!ctx->objects.erase(obj_id)) return fail(ctx, ADORYM_ENOENT, "unknown object id");
+  return ADORYM_OK;
+}
+
+int adorym_workspace_bytes(const adorym_problem* p, int grads, uint64_t* bytes) {
+  if (!p || !bytes) return ADORYM_EINVAL;
+  Plan pl;
+  std::string err;
+  int rc = make_plan(*p, true, grads, true, &pl, &err);
+  if (rc) return rc;
+  *bytes = pl.total;
+  return ADORYM_OK;
+}
+
+static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const float* probe, const float* pos,
+                    const float* I_meas, double* loss_out, float* g_delta, float* g_beta, float* g_probe,
+                    float* g_pos, float* I_out, bool adj) {
+  if (!ctx) return ADORYM_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!p) return fail(ctx, ADORYM_EINVAL, "null problem");
+  if (!probe || !pos) return fail(ctx, ADORYM_EINVAL, "probe and pos are required");
+  if (adj && !I_meas) return fail(ctx, ADORYM_EINVAL, "I_meas is required for loss_grad");
+  if (!adj && !I_out) return fail(ctx, ADORYM_EINVAL, "I_out is required for forward");
+  if ((g_delta == nullptr) != (g_beta == nullptr))
+    return fail(ctx, ADORYM_EINVAL, "g_delta and g_beta must both be given or both be NULL");
+  auto it = ctx->objects.find(obj_id);
+  if (it == ctx->objects.end()) return fail(ctx, ADORYM_ENOENT, "unknown object id");
+  const Object& obj = it->second;
+  if (obj.Lz != p->Lz || obj.Ly != p->Ly || obj.Lx != p->Lx)
+    return fail(ctx, ADORYM_EINVAL, "problem Lz/Ly/Lx differ from the registered object");
+  if (g_delta && (ptr_kind(g_delta) != 1 || ptr_kind(g_beta) != 1))
+    return fail(ctx, ADORYM_EINVAL, "g_delta / g_beta must be device memory");
+  const int grads = (g_delta ? 1 : 0) | (g_probe ? 2 : 0) | (g_pos ? 4 : 0);
+  Plan pl;
+  std::string err;
+  int rc = make_plan(*p, adj, grads, loss_out != nullptr, &pl, &err);
+  if (rc) return fail(ctx, rc, err);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "set device");
+  Tables tab;
+  if ((rc = get_tables(ctx, *p, &tab))) return rc;
+  if ((rc = prepare_kernels(*p, &err))) return fail(ctx, rc, err);
+  if ((rc = ensure_ws(ctx, pl.total))) return rc;
+  char* ws = ctx->ws;
+  cudaStream_t s = ctx->stream;
+  bool sync_after = false;
+  CallPtrs c;
+  auto stage_in = [&](const void* src, size_t off, size_t bytes) -> const void* {
+    if (ptr_kind(src) == 1) return src;
+    cudaMemcpyAsync(ws + off, src, bytes, cudaMemcpyHostToDevice, s);
+    return ws + off;
+  };
+  c.probe = reinterpret_cast<const float2*>(stage_in(probe, pl.off_s_probe, pl.bytes_probe));
+  c.pos = reinterpret_cast<const float*>(stage_in(pos, pl.off_s_pos, pl.bytes_pos));
+  if (I_meas) c.I_meas = reinterpret_cast<const float*>(stage_in(I_meas, pl.off_s_meas, pl.bytes_meas));
+  c.gd = g_delta;
+  c.gb = g_beta;
+  const bool host_loss = loss_out && ptr_kind(loss_out) == 0;
+  const bool host_gprobe = g_probe && ptr_kind(g_probe) == 0;
+  const bool host_gpos = g_pos && ptr_kind(g_pos) == 0;
+  const bool host_iout = I_out && ptr_kind(I_out) == 0;
+  c.loss = loss_out ? (host_loss ? reinterpret_cast<double*>(ws + pl.off_loss) : loss_out) : nullptr;
+  if (g_probe) {
+    if (host_gprobe) {
+      cudaMemcpyAsync(ws + pl.off_s_gprobe, g_probe, pl.bytes_probe, cudaMemcpyHostToDevice, s);
+      c.g_probe = reinterpret_cast<float2*>(ws + pl.off_s_gprobe);
+    } else {
+      c.g_probe = reinterpret_cast<float2*>(g_probe);
+    }
+  }
+  if (g_pos) c.g_pos = host_gpos ? reinterpret_cast<float*>(ws + pl.off_s_gpos) : g_pos;
+  if (I_out) c.I_out = host_iout ? reinterpret_cast<float*>(ws + pl.off_s_iout) : I_out;
+  if (ctx->timing && !ctx->ev0) {
+    cudaEventCreate(&ctx->ev0);
+    cudaEventCreate(&ctx->ev1);
+  }
+  if ((rc = enqueue(pl, obj, tab, c, ws, s, &err, ctx->timing ? ctx->ev0 : nullptr, ctx->timing ? ctx->ev1 : nullptr)))
+    return fail(ctx, rc, err);
+  ctx->timed = ctx->timing;
+  if (host_loss) {
+    cudaMemcpyAsync(loss_out, c.loss, sizeof(double), cudaMemcpyDeviceToHost, s);
+    sync_after = true;
+  }
+  if (host_gprobe) {
+    cudaMemcpyAsync(g_probe, c.g_probe, pl.bytes_probe, cudaMemcpyDeviceToHost, s);
+    sync_after = true;
+  }
+  if (host_gpos) {
+    cudaMemcpyAsync(g_pos, c.g_pos, pl.bytes_pos, cudaMemcpyDeviceToHost, s);
+    sync_after = true;
+  }
+  if (host_iout) {
+    cudaMemcpyAsync(I_out, c.I_out, pl.bytes_iout, cudaMemcpyDeviceToHost, s);
+    sync_after = true;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "enqueue");
+  if (sync_after) {
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+  }
+  return ADORYM_OK;
+}
+
+int adorym_enable_kernel_timing(adorym_ctx* ctx, int enable) {
+  if (!ctx) return ADORYM_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->timing = enable != 0;
+  return ADORYM_OK;
+}
+
+int adorym_kernel_ms(adorym_ctx* ctx, float* path_ms) {
+  if (!ctx || !path_ms) return ADORYM_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!ctx->timed || !ctx->ev1) return fail(ctx, ADORYM_ENOENT, "no timed call yet");
+  cudaError_t e = cudaEventSynchronize(ctx->ev1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(path_ms, ctx->ev0, ctx->ev1);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel timing");
+  return ADORYM_OK;
+}
+
+int adorym_forward(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const float* probe, const float* pos,
+                   float* I_out) {
+  return run_call(ctx, p, obj_id, probe, pos, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, I_out, false);
+}
+
+int adorym_loss_grad(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const float* probe, const float* pos,
+                     const float* I_meas, double* loss_out, float* g_delta, float* g_beta, float* g_probe,
+                     float* g_pos, float* I_out) {
+  return run_call(ctx, p, obj_id, probe, pos, I_meas, loss_out, g_delta, g_beta, g_probe, g_pos, I_out, true);
+}
+
+}  // extern "C"

@@ -1,0 +1,95 @@
+// Host-side engine shared by the direct C ABI entry points and the serving loop.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/adorym.h"
+#include "kernels.cuh"
+
+namespace adorym {
+
+struct Object {
+  const float* d = nullptr;
+  const float* b = nullptr;
+  int Lz = 0, Ly = 0, Lx = 0;
+};
+
+// Workspace layout of one call (byte offsets into one device allocation, 256-byte aligned).
+struct Plan {
+  adorym_problem p{};
+  int cp = 1, ncp = 1, nd = 1;
+  bool far = true, tomo = false, adj = false;
+  bool want_obj = false, want_probe = false, want_pos = false, want_loss = false;
+  size_t NN = 0;
+  size_t off_phat = 0, off_ckpt = 0, off_seg = 0, off_park = 0, off_far = 0, off_gI = 0, off_fbar = 0,
+         off_lossp = 0, off_qacc = 0, off_qsum = 0, off_rot = 0, off_grot = 0, off_loss = 0;
+  // staging for host-memory arguments
+  size_t off_s_probe = 0, off_s_pos = 0, off_s_meas = 0, off_s_gprobe = 0, off_s_gpos = 0, off_s_iout = 0;
+  size_t bytes_probe = 0, bytes_pos = 0, bytes_meas = 0, bytes_iout = 0;
+  size_t total = 0;
+};
+
+// Device pointers of one call after staging.
+struct CallPtrs {
+  const float2* probe = nullptr;
+  const float* pos = nullptr;
+  const float* I_meas = nullptr;
+  double* loss = nullptr;
+  float* gd = nullptr;
+  float* gb = nullptr;
+  float2* g_probe = nullptr;
+  float* g_pos = nullptr;
+  float* I_out = nullptr;
+};
+
+int validate(const adorym_problem& p, std::string* err);
+int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan* plan, std::string* err);
+
+struct Tables {
+  float2* dev = nullptr;   // [tw N][hy N][hx N][hd n_dist*N]
+  int N = 0, nd = 0;
+  const float2* tw() const { return dev; }
+  const float2* hy() const { return dev + N; }
+  const float2* hx() const { return dev + 2 * N; }
+  const float2* hd() const { return dev + 3 * N; }
+};
+
+// Enqueue every kernel of one call on `s` with workspace `ws` (no allocation, no host sync):
+// safe inside CUDA stream capture.
+int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs& c, char* ws, cudaStream_t s,
+            std::string* err, cudaEvent_t ev_start = nullptr, cudaEvent_t ev_stop = nullptr);
+
+struct Serve;
+
+}  // namespace adorym
+
+struct adorym_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::mutex mu;                    // guards everything below
+  std::string err;
+  std::map<int, adorym::Object> objects;
+  int next_obj = 1;
+  char* ws = nullptr;
+  size_t ws_cap = 0;
+  std::map<std::string, adorym::Tables> tables;
+  bool timing = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // fused-kernel timing pair
+  bool timed = false;
+  adorym::Serve* serve = nullptr;    // owned; created by the first submit or serve_config
+};
+
+namespace adorym {
+int get_tables(adorym_ctx* ctx, const adorym_problem& p, Tables* out);   // ctx->mu held
+int prepare_kernels(const adorym_problem& p, std::string* err);         // attributes, outside capture
+void serve_shutdown(adorym_ctx* ctx);
+}  // namespace adorym

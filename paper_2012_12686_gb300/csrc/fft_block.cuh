@@ -1,0 +1,265 @@
+// Block-wide complex64 2-D FFT with the wavefield resident in shared memory.
+//
+// One CTA owns one N x N field (N = 8..128), stored row-major in shared
+// memory with a leading dimension LD = N + 1 (conflict-free for both the
+// row-mapped and the column-mapped passes below).  A 1-D transform of length
+// N = N1 * N2 is split into two in-place Cooley-Tukey stages; the data of a
+// task (one radix-N1 or radix-N2 sub-transform of one line) live in
+// registers between its load and store.
+//
+// Along one axis, with t the task index on a line:
+//   S1 (forward, radix N1, t < N2): v[i] = A[N2*i + t]  -> DFT_N1 -> * W_N^(s t k)
+//                                   -> A[N2*k + t]
+//   S2 (forward, radix N2, t < N1): v[i] = A[N2*t + i]  -> DFT_N2
+//                                   -> v[i] holds frequency t + N1*i
+//   S3 (inverse-side first stage, radix N2, t < N1): input v[i] = frequency
+//        t + N1*i (exactly S2's output), DFT_N2 -> * W_N^(s t k) -> A[N2*t + k]
+//   S4 (inverse-side second stage, radix N1, t < N2): v[i] = A[N2*i + t]
+//        -> DFT_N1 -> v[k] holds sample N2*k + t (natural order, in place)
+// S2 -> S3 and S4 -> S1 touch the same slots with the same task, so those
+// pairs fuse in registers.  A propagation step F^-1{F[.] H} over both axes
+// therefore costs six shared-memory round trips:
+//   C14 (cols: S4 | spatial op | S1), C2, R1, R23 (rows: S2 | freq op | S3),
+//   R4, C3
+// and the field is in natural spatial order in shared memory between steps.
+// After C2, smem row r holds y-frequency  r / N2 + N1 * (r % N2).
+//
+// Twiddles W_N^m = exp(-2 pi i m / N) come from a table built in FP64 on the
+// host and rounded once to FP32; the in-register DFT_R (R <= 16) uses
+// compile-time constants of exp(+-2 pi i k / 16).
+#pragma once
+#include <cuda_runtime.h>
+#include <utility>
+
+namespace adorym {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// cos / sin of 2 pi k / 16, k = 0..15 (exact values rounded to float)
+struct Unit16 {
+  static constexpr float c[16] = {1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+                                  0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+                                  -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
+                                  0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f};
+  static constexpr float s[16] = {0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f,
+                                  1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+                                  0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+                                  -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f};
+};
+
+// a * exp(S * 2 pi i K / R), K, R compile-time, R | 16
+template <int R, int K, int S>
+__device__ __forceinline__ float2 rot_const(float2 a) {
+  constexpr int k = K % R;
+  if constexpr (k == 0) {
+    return a;
+  } else if constexpr (2 * k == R) {
+    return make_float2(-a.x, -a.y);
+  } else if constexpr (4 * k == R) {  // exp(S i pi/2) = S i
+    return S > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+  } else if constexpr (4 * k == 3 * R) {  // exp(S i 3pi/2) = -S i
+    return S > 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+  } else {
+    constexpr int q = k * (16 / R);
+    constexpr float c = Unit16::c[q];
+    constexpr float s = S > 0 ? Unit16::s[q] : -Unit16::s[q];
+    return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
+  }
+}
+
+template <int R, int S, int... K>
+__device__ __forceinline__ void butterflies(float2 (&v)[R], const float2 (&e)[R / 2], const float2 (&o)[R / 2],
+                                            std::integer_sequence<int, K...>) {
+  ((v[K] = cadd(e[K], rot_const<R, K, S>(o[K])), v[K + R / 2] = csub(e[K], rot_const<R, K, S>(o[K]))), ...);
+}
+
+// In-register DFT of size R (1, 2, 4, 8, 16): v[k] <- sum_n v[n] exp(S 2 pi i n k / R)
+template <int R, int S>
+__device__ __forceinline__ void dft(float2 (&v)[R]) {
+  if constexpr (R == 1) {
+    return;
+  } else if constexpr (R == 2) {
+    float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  } else {
+    constexpr int H = R / 2;
+    float2 e[H], o[H];
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      e[i] = v[2 * i];
+      o[i] = v[2 * i + 1];
+    }
+    dft<H, S>(e);
+    dft<H, S>(o);
+    butterflies<R, S>(v, e, o, std::make_integer_sequence<int, H>{});
+  }
+}
+
+template <int S, int R>
+__device__ __forceinline__ void dft_s(float2 (&v)[R]) { dft<R, S>(v); }
+
+template <int R>
+__device__ __forceinline__ void dft_sign(float2 (&v)[R], int sign) {
+  if (sign < 0) dft<R, -1>(v); else dft<R, +1>(v);
+}
+
+// twiddle multiply v[k] *= W_N^(sign t k) from the FP64-built table tw[m] = exp(-2 pi i m / N)
+template <int R>
+__device__ __forceinline__ void twiddle(float2 (&v)[R], const float2* __restrict__ tw, int t, int sign) {
+#pragma unroll
+  for (int k = 1; k < R; ++k) {
+    float2 w = tw[t * k];
+    v[k] = sign < 0 ? cmul(v[k], w) : cmulc(v[k], w);
+  }
+}
+
+template <int N_>
+struct Geo;
+// NT threads per CTA; MINB resident CTAs per SM the register budget is sized for (128 regs/thread)
+template <> struct Geo<8>   { static constexpr int N1 = 4,  N2 = 2, NT = 64,  MINB = 8; };
+template <> struct Geo<16>  { static constexpr int N1 = 4,  N2 = 4, NT = 64,  MINB = 8; };
+template <> struct Geo<32>  { static constexpr int N1 = 8,  N2 = 4, NT = 128, MINB = 4; };
+template <> struct Geo<64>  { static constexpr int N1 = 8,  N2 = 8, NT = 256, MINB = 2; };
+template <> struct Geo<128> { static constexpr int N1 = 16, N2 = 8, NT = 512, MINB = 1; };
+
+template <int N>
+struct Field {
+  static constexpr int N1 = Geo<N>::N1, N2 = Geo<N>::N2, NT = Geo<N>::NT, LD = N + 1;
+  static constexpr int SMEM_FLOAT2 = N * LD;
+  // y-frequency held by smem row r after the column forward stages (C2)
+  __device__ static __forceinline__ int row_freq(int r) { return r / N2 + N1 * (r % N2); }
+};
+
+// ---------------------------------------------------------------------------
+// Column pass "14": tasks (x, t < N2); v[k] <-> sample y = N2*k + t.
+//   load:  regs from smem (always)
+//   s4:    0 = no S4 (slots already natural), else S4 with this sign
+//   op(v, x, t): spatial pointwise op on natural samples (may read/write global)
+//   s1:    0 = store natural, else S1 with this sign, then store
+// ---------------------------------------------------------------------------
+template <int N, class Op>
+__device__ __forceinline__ void pass_c14(float2* __restrict__ A, const float2* __restrict__ tw, int s4, int s1, Op op) {
+  using F = Field<N>;
+  constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD;
+  for (int tau = threadIdx.x; tau < N * N2; tau += F::NT) {
+    const int x = tau % N, t = tau / N;
+    float2 v[N1];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) v[i] = A[(N2 * i + t) * LD + x];
+    if (s4) dft_sign<N1>(v, s4);
+    op(v, x, t);
+    if (s1) {
+      dft_sign<N1>(v, s1);
+      twiddle<N1>(v, tw, t, s1);
+    }
+#pragma unroll
+    for (int i = 0; i < N1; ++i) A[(N2 * i + t) * LD + x] = v[i];
+  }
+}
+
+// Column pass that only reads natural samples (S4 optional) and does not store back.
+template <int N, class Op>
+__device__ __forceinline__ void pass_c4_out(const float2* __restrict__ A, int s4, Op op) {
+  using F = Field<N>;
+  constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD;
+  for (int tau = threadIdx.x; tau < N * N2; tau += F::NT) {
+    const int x = tau % N, t = tau / N;
+    float2 v[N1];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) v[i] = A[(N2 * i + t) * LD + x];
+    if (s4) dft_sign<N1>(v, s4);
+    op(v, x, t);
+  }
+}
+
+// Column pass that produces natural samples from op (no smem read), then S1 (optional) and stores.
+template <int N, class Op>
+__device__ __forceinline__ void pass_c1_in(float2* __restrict__ A, const float2* __restrict__ tw, int s1, Op op) {
+  using F = Field<N>;
+  constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD;
+  for (int tau = threadIdx.x; tau < N * N2; tau += F::NT) {
+    const int x = tau % N, t = tau / N;
+    float2 v[N1];
+    op(v, x, t);
+    if (s1) {
+      dft_sign<N1>(v, s1);
+      twiddle<N1>(v, tw, t, s1);
+    }
+#pragma unroll
+    for (int i = 0; i < N1; ++i) A[(N2 * i + t) * LD + x] = v[i];
+  }
+}
+
+// Column pass "2" (S2, forward second stage) or "3" (S3, inverse-side first stage), in place.
+template <int N, bool IS_S3>
+__device__ __forceinline__ void pass_c23(float2* __restrict__ A, const float2* __restrict__ tw, int sign) {
+  using F = Field<N>;
+  constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD;
+  for (int tau = threadIdx.x; tau < N * N1; tau += F::NT) {
+    const int x = tau % N, t = tau / N;
+    float2 v[N2];
+#pragma unroll
+    for (int i = 0; i < N2; ++i) v[i] = A[(N2 * t + i) * LD + x];
+    dft_sign<N2>(v, sign);
+    if (IS_S3) twiddle<N2>(v, tw, t, sign);
+#pragma unroll
+    for (int i = 0; i < N2; ++i) A[(N2 * t + i) * LD + x] = v[i];
+  }
+}
+
+// Row pass "1" (S1 forward first stage) or "4" (S4 inverse-side second stage), in place.
+template <int N, bool IS_S1>
+__device__ __forceinline__ void pass_r14(float2* __restrict__ A, const float2* __restrict__ tw, int sign) {
+  using F = Field<N>;
+  constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD;
+  for (int tau = threadIdx.x; tau < N * N2; tau += F::NT) {
+    const int r = tau % N, t = tau / N;
+    float2 v[N1];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) v[i] = A[r * LD + N2 * i + t];
+    dft_sign<N1>(v, sign);
+    if (IS_S1) twiddle<N1>(v, tw, t, sign);
+#pragma unroll
+    for (int i = 0; i < N1; ++i) A[r * LD + N2 * i + t] = v[i];
+  }
+}
+
+// Row pass "23": tasks (row r, t < N1).  Frequencies: ky = row_freq(r), kx = t + N1*i.
+//   s2:  0 = regs come from op_in (no smem read), else smem read + S2 with this sign
+//   op(v, ky, t): frequency-domain pointwise op
+//   s3:  0 = no store, else S3 with this sign and store in place
+template <int N, class Op>
+__device__ __forceinline__ void pass_r23(float2* __restrict__ A, const float2* __restrict__ tw, int s2, int s3, Op op) {
+  using F = Field<N>;
+  constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD;
+  for (int tau = threadIdx.x; tau < N * N1; tau += F::NT) {
+    const int r = tau % N, t = tau / N;
+    const int ky = F::row_freq(r);
+    float2 v[N2];
+    if (s2) {
+#pragma unroll
+      for (int i = 0; i < N2; ++i) v[i] = A[r * LD + N2 * t + i];
+      dft_sign<N2>(v, s2);
+    }
+    op(v, ky, t);
+    if (s3) {
+      dft_sign<N2>(v, s3);
+      twiddle<N2>(v, tw, t, s3);
+#pragma unroll
+      for (int i = 0; i < N2; ++i) A[r * LD + N2 * t + i] = v[i];
+    }
+  }
+}
+
+}  // namespace adorym

@@ -1,0 +1,679 @@
+// Fused multislice forward + loss + adjoint, one CTA per position (far field) or per problem
+// (near field), wavefield resident in shared memory (N <= 128).
+//
+// Forward (Algorithm 1, per probe mode):
+//   psi_0   = IDFT_-{ DFT_-[P] exp(-2 pi i dr.nu) }                 Eq. fourier_shift
+//   phi_j   = psi_j exp(-k dz beta_j) exp(i k dz delta_j)           Eq. ri_modulation
+//   psi_j+1 = IDFT_-{ DFT_-[phi_j] H },  H = exp(i pi lambda dz |nu|^2)   Eqs. fresnel_prop, paraxial_kernel
+//   far:  Psi = (1/N) DFT_+[phi_L-1]                                 Eq. fraunhofer (negative phase convention)
+//   near: Psi_d = IDFT_-{ DFT_-[phi_L-1] H_d exp(-2 pi i s_d.nu) }   Eq. fresnel_prop to the detector
+//   I = sum_modes |Psi|^2                                            Eq. multimode
+// Loss: mean over the batch's detector pixels of Eq. lsq_loss (amplitudes, I + eps) or
+// Eq. poisson_loss (log(I + eps)), summed in FP64.
+// Adjoint (chain rule; the paper obtains it by reverse-mode AD, Sec. 2.3.1):
+//   Psibar = 2 dL/dI Psi;  phibar_L-1 = (1/N) DFT_-[Psibar] (far) or IDFT_-{sum_d conj(G_d) DFT_-[Psibar_d]} (near)
+//   psibar_j = conj(T_j) phibar_j;  dL/ddelta_j += k dz Im(psibar_j conj psi_j);
+//   dL/dbeta_j += -k dz Re(psibar_j conj psi_j);  phibar_j-1 = IDFT_-{ DFT_-[psibar_j] conj H }
+//   far: Q = DFT_-[psibar_0];  dL/dP = IDFT_-{ sum_b Q conj(ramp) } (reduced later);
+//        dL/ddr_a = Re[(1/N^2) sum_nu conj(Q) (-2 pi i nu_a) P^ ramp]
+//   near: dL/dP = sum_b psibar_0;  dL/ds_d,a = Re[(1/N^2) sum_nu conj(Q_d) (-2 pi i nu_a) Phi G_d]
+// The psi_j needed by the adjoint are not kept: psi is checkpointed every cp slices
+// (cp = ceil(sqrt(L)) by default) and each segment is recomputed from its checkpoint
+// before it is reversed (the recompute-vs-store trade-off discussed in Sec. 4).
+#include "fft_block.cuh"
+#include "kernels.cuh"
+
+namespace adorym {
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NT / 32; ++i) s += red[i];   // fixed order: deterministic
+  }
+  __syncthreads();
+  return s;   // valid on thread 0
+}
+
+__device__ __forceinline__ double freqd(int k, int N) { return (double)(k <= (N - 1) / 2 ? k : k - N) / (double)N; }
+
+// exp(-2 pi i d f_k) for k < N into out (FP64 argument, rounded once)
+__device__ __forceinline__ void ramp_table(float2* out, double d, int N, int NT) {
+  for (int k = threadIdx.x; k < N; k += NT) {
+    double s, c;
+    sincospi(-2.0 * d * freqd(k, N), &s, &c);
+    out[k] = make_float2((float)c, (float)s);
+  }
+}
+
+template <int N, int FAR>
+__global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArgs a) {
+  using F = Field<N>;
+  constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD, NT = F::NT;
+  constexpr size_t NN = (size_t)N * N;
+  extern __shared__ float2 sm[];
+  float2* A = sm;
+  float2* tw = A + N * LD;
+  float2* hy = tw + N;
+  float2* hx = hy + N;
+  float2* ry = hx + N;
+  float2* rx = ry + N;
+  double* red = reinterpret_cast<double*>(rx + N);
+
+  const int b = blockIdx.x;
+  const int M = a.M, L = a.L, cp = a.cp, ncp = a.ncp;
+  for (int i = threadIdx.x; i < N; i += NT) {
+    tw[i] = a.tw[i];
+    hy[i] = a.hy[i];
+    hx[i] = a.hx[i];
+  }
+  int p0y = 0, p0x = 0;
+  if (FAR) {
+    // S1: integer corner p0 = floor(pos + 1/2), residual dr = pos - p0 (FP64, exact for float input)
+    const double py = a.pos[2 * b], px = a.pos[2 * b + 1];
+    const double fy = floor(py + 0.5), fx = floor(px + 0.5);
+    p0y = (int)fy;
+    p0x = (int)fx;
+    ramp_table(ry, py - fy, N, NT);
+    ramp_table(rx, px - fx, N, NT);
+  }
+  __syncthreads();
+
+  const int Ly = a.Ly, Lx = a.Lx;
+  const float kdz = a.kdz;
+  // transmission T_j at patch pixel (y, x); voxels outside the volume are vacuum
+  auto trans = [&](int j, int y, int x) -> float2 {
+    int gy = p0y + y, gx = p0x + x, gz = FAR ? j : b * L + j;
+    float d = 0.f, bb = 0.f;
+    if (gy >= 0 && gy < Ly && gx >= 0 && gx < Lx) {
+      size_t o = ((size_t)gz * Ly + gy) * Lx + gx;
+      d = __ldg(a.vd + o);
+      bb = __ldg(a.vb + o);
+    }
+    float s, c;
+    sincosf(kdz * d, &s, &c);
+    float e = expf(-kdz * bb);
+    return make_float2(e * c, e * s);
+  };
+  auto hop = [&](float2 (&v)[N2], int ky, int t) {
+    float2 h = hy[ky];
+#pragma unroll
+    for (int i = 0; i < N2; ++i) v[i] = cmul(cmul(v[i], h), hx[t + N1 * i]);
+  };
+  auto hop_conj = [&](float2 (&v)[N2], int ky, int t) {
+    float2 h = hy[ky];
+#pragma unroll
+    for (int i = 0; i < N2; ++i) v[i] = cmulc(cmulc(v[i], h), hx[t + N1 * i]);
+  };
+  // the rest of a propagation step after C14: C2, R1, R23(H), R4, C3
+  auto propagate_tail = [&](bool adjoint) {
+    pass_c23<N, false>(A, tw, -1);
+    __syncthreads();
+    pass_r14<N, true>(A, tw, -1);
+    __syncthreads();
+    if (adjoint) pass_r23<N>(A, tw, -1, +1, hop_conj);
+    else pass_r23<N>(A, tw, -1, +1, hop);
+    __syncthreads();
+    pass_r14<N, false>(A, tw, +1);
+    __syncthreads();
+    pass_c23<N, true>(A, tw, +1);
+    __syncthreads();
+  };
+
+  const bool adj = a.adj != 0;
+  const int nd = FAR ? 1 : a.n_dist;
+  const int j0_last = (ncp - 1) * cp;
+  const float invN = 1.0f / (float)N, invNN = 1.0f / (float)NN;
+  float2* ck_b = a.ckpt + (size_t)b * M * ncp * NN;
+  float2* seg_b = a.seg + (size_t)b * M * cp * NN;
+  float* gI_b = a.gI + (size_t)b * nd * NN;
+
+  // ------------------------------------------------------------------ forward
+  for (int m = 0; m < M; ++m) {
+    float2* ck = ck_b + (size_t)m * ncp * NN;
+    float2* sg = seg_b + (size_t)m * cp * NN;
+    // spatial op of slice j: store psi_j where the adjoint needs it, then modulate
+    auto fwd_op = [&](int j) {
+      return [&, j](float2 (&v)[N1], int x, int t) {
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+          const int y = N2 * k + t;
+          if (adj) {
+            if (j % cp == 0) ck[(size_t)(j / cp) * NN + y * N + x] = v[k];
+            else if (j > j0_last) sg[(size_t)(j - j0_last) * NN + y * N + x] = v[k];
+          }
+          v[k] = cmul(v[k], trans(j, y, x));
+        }
+      };
+    };
+    if (FAR) {
+      // psi_0 = IDFT_-(P^ ramp), built in Fourier space at the R23 layout
+      const float2* ph = a.phat + (size_t)m * NN;
+      pass_r23<N>(A, tw, 0, +1, [&](float2 (&v)[N2], int ky, int t) {
+        const float2 r = cscale(ry[ky], invNN);
+#pragma unroll
+        for (int i = 0; i < N2; ++i) {
+          const int kx = t + N1 * i;
+          v[i] = cmul(cmul(__ldg(&ph[ky * N + kx]), r), rx[kx]);
+        }
+      });
+      __syncthreads();
+      pass_r14<N, false>(A, tw, +1);
+      __syncthreads();
+      pass_c23<N, true>(A, tw, +1);
+      __syncthreads();
+    }
+    for (int j = 0; j < L; ++j) {
+      const bool last = (j == L - 1);
+      const int s1 = (FAR && last) ? +1 : -1;
+      if (!FAR && j == 0) {
+        const float2* pr = a.probe + (size_t)m * NN;
+        auto op = fwd_op(0);
+        pass_c1_in<N>(A, tw, s1, [&](float2 (&v)[N1], int x, int t) {
+#pragma unroll
+          for (int k = 0; k < N1; ++k) v[k] = __ldg(&pr[(N2 * k + t) * N + x]);
+          op(v, x, t);
+        });
+      } else {
+        pass_c14<N>(A, tw, +1, s1, fwd_op(j));
+      }
+      __syncthreads();
+      if (!last) {
+        propagate_tail(false);
+        continue;
+      }
+      pass_c23<N, false>(A, tw, s1);
+      __syncthreads();
+      pass_r14<N, true>(A, tw, s1);
+      __syncthreads();
+      if (FAR) {
+        // Psi = (1/N) DFT_+[phi]; keep Psi, accumulate I over modes
+        float2* fm = a.far + ((size_t)b * M + m) * NN;
+        pass_r23<N>(A, tw, +1, 0, [&](float2 (&v)[N2], int ky, int t) {
+#pragma unroll
+          for (int i = 0; i < N2; ++i) {
+            const int p = ky * N + t + N1 * i;
+            const float2 P = cscale(v[i], invN);
+            fm[p] = P;
+            const float I = fmaf(P.x, P.x, P.y * P.y);
+            gI_b[p] = (m == 0) ? I : gI_b[p] + I;
+          }
+        });
+        __syncthreads();
+      } else {
+        // Phi = DFT_-[phi] kept at slot n_dist; then Psi_d = IDFT_-{Phi G_d} per distance
+        float2* Phi = a.far + (((size_t)b * (nd + 1) + nd) * M + m) * NN;
+        pass_r23<N>(A, tw, -1, 0, [&](float2 (&v)[N2], int ky, int t) {
+#pragma unroll
+          for (int i = 0; i < N2; ++i) Phi[ky * N + t + N1 * i] = v[i];
+        });
+        __syncthreads();
+        for (int d = 0; d < nd; ++d) {
+          const float* sd = a.pos + ((size_t)b * nd + d) * 2;
+          ramp_table(ry, (double)sd[0], N, NT);
+          ramp_table(rx, (double)sd[1], N, NT);
+          __syncthreads();
+          const float2* hd = a.hd + (size_t)d * N;
+          pass_r23<N>(A, tw, 0, +1, [&](float2 (&v)[N2], int ky, int t) {
+            const float2 gy = cscale(cmul(__ldg(&hd[ky]), ry[ky]), invNN);
+#pragma unroll
+            for (int i = 0; i < N2; ++i) {
+              const int kx = t + N1 * i;
+              v[i] = cmul(cmul(Phi[ky * N + kx], gy), cmul(__ldg(&hd[kx]), rx[kx]));
+            }
+          });
+          __syncthreads();
+          pass_r14<N, false>(A, tw, +1);
+          __syncthreads();
+          pass_c23<N, true>(A, tw, +1);
+          __syncthreads();
+          float2* fd = a.far + (((size_t)b * (nd + 1) + d) * M + m) * NN;
+          float* gId = gI_b + (size_t)d * NN;
+          pass_c4_out<N>(A, +1, [&](float2 (&v)[N1], int x, int t) {
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+              const int p = (N2 * k + t) * N + x;
+              fd[p] = v[k];
+              const float I = fmaf(v[k].x, v[k].x, v[k].y * v[k].y);
+              gId[p] = (m == 0) ? I : gId[p] + I;
+            }
+          });
+          __syncthreads();
+        }
+      }
+    }
+  }
+
+  // ------------------------------------------------------------------ loss, dL/dI
+  {
+    const size_t npx = (size_t)nd * NN;
+    const float* Im = a.I_meas ? a.I_meas + (size_t)b * npx : nullptr;
+    float* Io = a.I_out ? a.I_out + (size_t)b * npx : nullptr;
+    const float eps = a.eps, sc = (float)a.inv_npix;
+    double acc = 0.0;
+    for (size_t p = threadIdx.x; p < npx; p += NT) {
+      const float I = gI_b[p];
+      if (Io) Io[p] = I;
+      if (!Im) continue;
+      const float im = Im[p];
+      float term, dI;
+      if (a.loss == 0) {
+        const float sI = sqrtf(I + eps), sM = sqrtf(im + eps);
+        const float df = sI - sM;
+        term = df * df;
+        dI = df / sI;
+      } else {
+        term = I - im * logf(I + eps);
+        dI = 1.0f - im / (I + eps);
+      }
+      acc += (double)term;
+      gI_b[p] = dI * sc;
+    }
+    const double s = block_sum<NT>(acc, red);
+    if (threadIdx.x == 0 && a.lossp) a.lossp[b] = s;
+  }
+  if (!adj) return;
+  __syncthreads();
+
+  // ------------------------------------------------------------------ adjoint
+  double gacc[2 * 4] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const bool want_obj = a.gd != nullptr;
+  for (int m = 0; m < M; ++m) {
+    float2* ck = ck_b + (size_t)m * ncp * NN;
+    float2* sg = seg_b + (size_t)m * cp * NN;
+    if (FAR) {
+      // phibar_{L-1} = (1/N) DFT_-[2 gI Psi]
+      const float2* fm = a.far + ((size_t)b * M + m) * NN;
+      const float sc = 2.0f * invN;
+      pass_r23<N>(A, tw, 0, -1, [&](float2 (&v)[N2], int ky, int t) {
+#pragma unroll
+        for (int i = 0; i < N2; ++i) {
+          const int p = ky * N + t + N1 * i;
+          v[i] = cscale(fm[p], sc * gI_b[p]);
+        }
+      });
+      __syncthreads();
+      pass_r14<N, false>(A, tw, -1);
+      __syncthreads();
+      pass_c23<N, true>(A, tw, -1);
+      __syncthreads();
+    } else {
+      const float2* Phi = a.far + (((size_t)b * (nd + 1) + nd) * M + m) * NN;
+      float2* fb = a.fbar + (size_t)b * NN;
+      for (int d = 0; d < nd; ++d) {
+        const float* sd = a.pos + ((size_t)b * nd + d) * 2;
+        ramp_table(ry, (double)sd[0], N, NT);
+        ramp_table(rx, (double)sd[1], N, NT);
+        const float2* fd = a.far + (((size_t)b * (nd + 1) + d) * M + m) * NN;
+        const float* gId = gI_b + (size_t)d * NN;
+        __syncthreads();
+        // Q_d = DFT_-[2 gI_d Psi_d]
+        pass_c1_in<N>(A, tw, -1, [&](float2 (&v)[N1], int x, int t) {
+#pragma unroll
+          for (int k = 0; k < N1; ++k) {
+            const int p = (N2 * k + t) * N + x;
+            v[k] = cscale(fd[p], 2.0f * gId[p]);
+          }
+        });
+        __syncthreads();
+        pass_c23<N, false>(A, tw, -1);
+        __syncthreads();
+        pass_r14<N, true>(A, tw, -1);
+        __syncthreads();
+        const float2* hd = a.hd + (size_t)d * N;
+        pass_r23<N>(A, tw, -1, 0, [&](float2 (&v)[N2], int ky, int t) {
+          const float2 gy = cmul(__ldg(&hd[ky]), ry[ky]);
+          const float fyk = (float)freqd(ky, N);
+          float ay = 0.f, ax = 0.f;
+#pragma unroll
+          for (int i = 0; i < N2; ++i) {
+            const int kx = t + N1 * i, p = ky * N + kx;
+            const float2 G = cmul(gy, cmul(__ldg(&hd[kx]), rx[kx]));
+            const float2 base = cmul(cconj(v[i]), cmul(Phi[p], G));
+            ay += fyk * base.y;
+            ax += (float)freqd(kx, N) * base.y;
+            const float2 c = cmulc(v[i], G);   // conj(G) Q
+            fb[p] = (d == 0) ? c : cadd(fb[p], c);
+          }
+          gacc[2 * d] += ay;
+          gacc[2 * d + 1] += ax;
+        });
+        __syncthreads();
+      }
+      // phibar_{L-1} = IDFT_-{sum_d conj(G_d) Q_d}
+      pass_r23<N>(A, tw, 0, +1, [&](float2 (&v)[N2], int ky, int t) {
+#pragma unroll
+        for (int i = 0; i < N2; ++i) v[i] = cscale(fb[ky * N + t + N1 * i], invNN);
+      });
+      __syncthreads();
+      pass_r14<N, false>(A, tw, +1);
+      __syncthreads();
+      pass_c23<N, true>(A, tw, +1);
+      __syncthreads();
+    }
+
+    for (int s = ncp - 1; s >= 0; --s) {
+      const int j0 = s * cp, j1 = min(j0 + cp, L) - 1;
+      if (s != ncp - 1 && j1 > j0) {
+        float2* pk = a.park + (size_t)b * N * LD;
+        for (int i = threadIdx.x; i < N * LD; i += NT) pk[i] = A[i];
+        __syncthreads();
+        // recompute psi_{j0+1..j1} from the checkpoint psi_{j0}
+        for (int j = j0; j < j1; ++j) {
+          auto op = [&, j](float2 (&v)[N1], int x, int t) {
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+              const int y = N2 * k + t;
+              if (j == j0) v[k] = ck[(size_t)s * NN + y * N + x];
+              else sg[(size_t)(j - j0) * NN + y * N + x] = v[k];
+              v[k] = cmul(v[k], trans(j, y, x));
+            }
+          };
+          if (j == j0) pass_c1_in<N>(A, tw, -1, op);
+          else pass_c14<N>(A, tw, +1, -1, op);
+          __syncthreads();
+          propagate_tail(false);
+        }
+        pass_c4_out<N>(A, +1, [&](float2 (&v)[N1], int x, int t) {
+#pragma unroll
+          for (int k = 0; k < N1; ++k) sg[(size_t)(j1 - j0) * NN + (N2 * k + t) * N + x] = v[k];
+        });
+        __syncthreads();
+        for (int i = threadIdx.x; i < N * LD; i += NT) A[i] = pk[i];
+        __syncthreads();
+      }
+      for (int j = j1; j >= j0; --j) {
+        const int s4 = (FAR && j == L - 1) ? -1 : +1;
+        const bool first = (j == 0);
+        auto op = [&, j](float2 (&v)[N1], int x, int t) {
+#pragma unroll
+          for (int k = 0; k < N1; ++k) {
+            const int y = N2 * k + t;
+            const float2 psi = (j == j0) ? ck[(size_t)s * NN + y * N + x] : sg[(size_t)(j - j0) * NN + y * N + x];
+            const float2 T = trans(j, y, x);
+            const float2 pb = cmulc(v[k], T);           // psibar_j = conj(T_j) phibar_j
+            if (want_obj) {
+              const int gy = p0y + y, gx = p0x + x, gz = FAR ? j : b * L + j;
+              if (gy >= 0 && gy < Ly && gx >= 0 && gx < Lx) {
+                const float2 z = cmulc(pb, psi);        // psibar conj(psi)
+                const size_t o = ((size_t)gz * Ly + gy) * Lx + gx;
+                atomicAdd(a.gd + o, kdz * z.y);
+                atomicAdd(a.gb + o, -kdz * z.x);
+              }
+            }
+            v[k] = pb;
+          }
+        };
+        if (!FAR && first) {
+          // illumination gradient (no shift in the near-field geometry): psibar_0 itself
+          float2* q = a.qacc ? a.qacc + ((size_t)b * M + m) * NN : nullptr;
+          pass_c4_out<N>(A, s4, [&](float2 (&v)[N1], int x, int t) {
+            op(v, x, t);
+            if (q) {
+#pragma unroll
+              for (int k = 0; k < N1; ++k) q[(N2 * k + t) * N + x] = v[k];
+            }
+          });
+          __syncthreads();
+          continue;
+        }
+        pass_c14<N>(A, tw, s4, -1, op);
+        __syncthreads();
+        if (!first) {
+          propagate_tail(true);
+          continue;
+        }
+        // far field, j = 0: Q = DFT_-[psibar_0] -> probe and position gradients
+        pass_c23<N, false>(A, tw, -1);
+        __syncthreads();
+        pass_r14<N, true>(A, tw, -1);
+        __syncthreads();
+        const float2* ph = a.phat + (size_t)m * NN;
+        float2* q = a.qacc ? a.qacc + ((size_t)b * M + m) * NN : nullptr;
+        pass_r23<N>(A, tw, -1, 0, [&](float2 (&v)[N2], int ky, int t) {
+          const float2 r_y = ry[ky];
+          const float fyk = (float)freqd(ky, N);
+          float ay = 0.f, ax = 0.f;
+#pragma unroll
+          for (int i = 0; i < N2; ++i) {
+            const int kx = t + N1 * i, p = ky * N + kx;
+            const float2 r = cmul(r_y, rx[kx]);
+            const float2 base = cmul(cconj(v[i]), cmul(__ldg(&ph[p]), r));
+            ay += fyk * base.y;
+            ax += (float)freqd(kx, N) * base.y;
+            if (q) q[p] = cmulc(v[i], r);
+          }
+          gacc[0] += ay;
+          gacc[1] += ax;
+        });
+        __syncthreads();
+      }
+    }
+  }
+  if (a.gpos) {
+    const double sc = 2.0 * 3.14159265358979323846 / (double)NN;
+    for (int d = 0; d < nd; ++d) {
+      const double gy = block_sum<NT>(gacc[2 * d], red);
+      const double gx = block_sum<NT>(gacc[2 * d + 1], red);
+      if (threadIdx.x == 0) {
+        a.gpos[((size_t)b * nd + d) * 2] = (float)(sc * gy);
+        a.gpos[((size_t)b * nd + d) * 2 + 1] = (float)(sc * gx);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------- probe DFT
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::NT) k_probe_hat(const float2* __restrict__ probe, float2* __restrict__ phat,
+                                                        const float2* __restrict__ twg) {
+  using F = Field<N>;
+  constexpr int N1 = F::N1, N2 = F::N2, NT = F::NT;
+  extern __shared__ float2 sm[];
+  float2* A = sm;
+  float2* tw = A + N * F::LD;
+  for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
+  __syncthreads();
+  const float2* p = probe + (size_t)blockIdx.x * N * N;
+  float2* o = phat + (size_t)blockIdx.x * N * N;
+  pass_c1_in<N>(A, tw, -1, [&](float2 (&v)[N1], int x, int t) {
+#pragma unroll
+    for (int k = 0; k < N1; ++k) v[k] = p[(N2 * k + t) * N + x];
+  });
+  __syncthreads();
+  pass_c23<N, false>(A, tw, -1);
+  __syncthreads();
+  pass_r14<N, true>(A, tw, -1);
+  __syncthreads();
+  pass_r23<N>(A, tw, -1, 0, [&](float2 (&v)[N2], int ky, int t) {
+#pragma unroll
+    for (int i = 0; i < N2; ++i) o[ky * N + t + N1 * i] = v[i];
+  });
+}
+
+// ---------------------------------------------------------------------------- probe gradient
+// qsum[m][p] = sum_b qacc[b][m][p] in FP64, fixed order
+__global__ void k_qsum(const float2* __restrict__ qacc, float2* __restrict__ qsum, int B, size_t MNN) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= MNN) return;
+  double sr = 0.0, si = 0.0;
+  for (int b = 0; b < B; ++b) {
+    const float2 v = qacc[(size_t)b * MNN + i];
+    sr += v.x;
+    si += v.y;
+  }
+  qsum[i] = make_float2((float)sr, (float)si);
+}
+
+// far field: g_probe[m] += IDFT_-{qsum[m]};  near field: g_probe[m] += qsum[m]
+template <int N, int FAR>
+__global__ void __launch_bounds__(Geo<N>::NT) k_probe_grad(const float2* __restrict__ qsum, float2* __restrict__ g,
+                                                         const float2* __restrict__ twg, const double* __restrict__ lossp,
+                                                         int B, double inv_npix, double* __restrict__ loss_out) {
+  using F = Field<N>;
+  constexpr int N1 = F::N1, N2 = F::N2, NT = F::NT;
+  constexpr size_t NN = (size_t)N * N;
+  extern __shared__ float2 sm[];
+  float2* A = sm;
+  float2* tw = A + N * F::LD;
+  if (loss_out && blockIdx.x == 0 && threadIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < B; ++b) s += lossp[b];
+    *loss_out = s * inv_npix;
+  }
+  if (!g) return;
+  const float2* q = qsum + blockIdx.x * NN;
+  float2* o = g + blockIdx.x * NN;
+  if (!FAR) {
+    for (size_t i = threadIdx.x; i < NN; i += NT) o[i] = cadd(o[i], q[i]);
+    return;
+  }
+  for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
+  __syncthreads();
+  const float invNN = 1.0f / (float)NN;
+  pass_r23<N>(A, tw, 0, +1, [&](float2 (&v)[N2], int ky, int t) {
+#pragma unroll
+    for (int i = 0; i < N2; ++i) v[i] = cscale(q[ky * N + t + N1 * i], invNN);
+  });
+  __syncthreads();
+  pass_r14<N, false>(A, tw, +1);
+  __syncthreads();
+  pass_c23<N, true>(A, tw, +1);
+  __syncthreads();
+  pass_c4_out<N>(A, +1, [&](float2 (&v)[N1], int x, int t) {
+#pragma unroll
+    for (int k = 0; k < N1; ++k) {
+      const int p = (N2 * k + t) * N + x;
+      o[p] = cadd(o[p], v[k]);
+    }
+  });
+}
+
+// ---------------------------------------------------------------------------- launchers
+int path_smem_bytes(int N) {
+  const int NT = N == 128 ? 512 : N == 64 ? 256 : N == 32 ? 128 : 64;
+  return (N * (N + 1) + 5 * N) * (int)sizeof(float2) + (NT / 32) * (int)sizeof(double);
+}
+
+template <int N, int FAR>
+static cudaError_t launch_path_t(const PathArgs& a, cudaStream_t s) {
+  const int smem = path_smem_bytes(N);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_path<N, FAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_path<N, FAR><<<a.B, Geo<N>::NT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_path(const PathArgs& a, int farfield, cudaStream_t s) {
+  switch (a.N) {
+#define ADORYM_CASE(n)                                                        \
+  case n:                                                                     \
+    return farfield ? launch_path_t<n, 1>(a, s) : launch_path_t<n, 0>(a, s);
+    ADORYM_CASE(8)
+    ADORYM_CASE(16)
+    ADORYM_CASE(32)
+    ADORYM_CASE(64)
+    ADORYM_CASE(128)
+#undef ADORYM_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+template <int N>
+static cudaError_t launch_probe_hat_t(int M, const float2* probe, float2* phat, const float2* tw, cudaStream_t s) {
+  const int smem = (N * (N + 1) + N) * (int)sizeof(float2);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_probe_hat<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_probe_hat<N><<<M, Geo<N>::NT, smem, s>>>(probe, phat, tw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe_hat(int N, int M, const float2* probe, float2* phat, const float2* tw, cudaStream_t s) {
+  switch (N) {
+    case 8: return launch_probe_hat_t<8>(M, probe, phat, tw, s);
+    case 16: return launch_probe_hat_t<16>(M, probe, phat, tw, s);
+    case 32: return launch_probe_hat_t<32>(M, probe, phat, tw, s);
+    case 64: return launch_probe_hat_t<64>(M, probe, phat, tw, s);
+    case 128: return launch_probe_hat_t<128>(M, probe, phat, tw, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int N, int FAR>
+static cudaError_t launch_probe_grad_t(int M, int B, const float2* qacc, float2* qsum, float2* g, const float2* tw,
+                                       const double* lossp, double inv_npix, double* loss_out, cudaStream_t s) {
+  const size_t MNN = (size_t)M * N * N;
+  if (g) {
+    k_qsum<<<(unsigned)((MNN + 255) / 256), 256, 0, s>>>(qacc, qsum, B, MNN);
+  }
+  const int smem = (N * (N + 1) + N) * (int)sizeof(float2);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_probe_grad<N, FAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_probe_grad<N, FAR><<<M, Geo<N>::NT, smem, s>>>(qsum, g, tw, lossp, B, inv_npix, loss_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe_grad(int N, int M, int B, int farfield, const float2* qacc, float2* qsum, float2* g_probe,
+                              const float2* tw, const double* lossp, double inv_npix, double* loss_out,
+                              cudaStream_t s) {
+  switch (N) {
+#define ADORYM_CASE(n)                                                                                     \
+  case n:                                                                                                  \
+    return farfield ? launch_probe_grad_t<n, 1>(M, B, qacc, qsum, g_probe, tw, lossp, inv_npix, loss_out, s) \
+                    : launch_probe_grad_t<n, 0>(M, B, qacc, qsum, g_probe, tw, lossp, inv_npix, loss_out, s);
+    ADORYM_CASE(8)
+    ADORYM_CASE(16)
+    ADORYM_CASE(32)
+    ADORYM_CASE(64)
+    ADORYM_CASE(128)
+#undef ADORYM_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+template <int N, int FAR>
+static cudaError_t prepare_t() {
+  cudaError_t e = cudaFuncSetAttribute(k_path<N, FAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, path_smem_bytes(N));
+  const int small = (N * (N + 1) + N) * (int)sizeof(float2);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_probe_hat<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, small);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_probe_grad<N, FAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, small);
+  return e;
+}
+
+cudaError_t prepare_path(int N, int farfield) {
+  switch (N) {
+#define ADORYM_CASE(n) \
+  case n:              \
+    return farfield ? prepare_t<n, 1>() : prepare_t<n, 0>();
+    ADORYM_CASE(8)
+    ADORYM_CASE(16)
+    ADORYM_CASE(32)
+    ADORYM_CASE(64)
+    ADORYM_CASE(128)
+#undef ADORYM_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace adorym

@@ -1,0 +1,57 @@
+// Device-side argument blocks and host launchers shared by the kernel files and the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace adorym {
+
+// One far-field (or near-field) loss/gradient launch over a batch, as seen by the fused kernel.
+struct PathArgs {
+  int N, L, M, B, Ly, Lx;
+  int cp, ncp;            // checkpoint spacing and count (ncp = ceil(L / cp))
+  int loss;               // 0 = LSQ (Eq. lsq_loss), 1 = Poisson (Eq. poisson_loss)
+  int adj;                // 1: run the adjoint (loss_grad); 0: forward only
+  int n_dist;             // near field: number of sample-detector distances
+  float eps, kdz;
+  double inv_npix;        // 1 / (number of detector pixels in the batch)
+  const float* vd;        // delta [Lz][Ly][Lx] (rotated frame for tomography)
+  const float* vb;        // beta
+  const float2* probe;    // near field: illumination [M][N][N]
+  const float2* phat;     // far field: DFT_-[probe] [M][N][N]
+  const float* pos;       // far field [B][2] (y, x); near field shifts [B][n_dist][2]
+  const float* I_meas;    // [B][N][N] or [B][n_dist][N][N]; null for forward-only
+  float* I_out;           // predicted intensities (same shape) or null
+  const float2* tw;       // W_N^m = exp(-2 pi i m / N), m < N
+  const float2* hy;       // slice-to-slice propagator factors exp(i pi c f^2) / N
+  const float2* hx;
+  const float2* hd;       // near field: [n_dist][N] factors exp(i pi f^2 / N_F) (unscaled)
+  float2* ckpt;           // [B][M][ncp][N*N] checkpoints psi_{j0}
+  float2* seg;            // [B][M][cp][N*N] recomputed psi_j of one segment
+  float2* park;           // [B][N*(N+1)] adjoint field parked during a recompute
+  float2* far;            // [B][M][N*N] detector field (far) or [B][n_dist][M][N*N] (near)
+  float* gI;              // [B][N*N] (or [B][n_dist][N*N]) intensity, then dL/dI
+  float2* fbar;           // near field: [B][N*N] accumulated Fourier-space adjoint
+  double* lossp;          // [B] per-problem loss sums
+  float2* qacc;           // [B][M][N*N] per-position probe-gradient partials (Fourier space)
+  float* gd;              // object gradient [Lz][Ly][Lx] (+=), or null
+  float* gb;
+  float* gpos;            // [B][2] or [B][n_dist][2] (overwritten), or null
+};
+
+// launchers (return cudaGetLastError())
+cudaError_t launch_probe_hat(int N, int M, const float2* probe, float2* phat, const float2* tw, cudaStream_t s);
+cudaError_t launch_path(const PathArgs& a, int farfield, cudaStream_t s);
+cudaError_t launch_probe_grad(int N, int M, int B, int farfield, const float2* qacc, float2* qsum, float2* g_probe,
+                              const float2* tw, const double* lossp, double inv_npix, double* loss_out,
+                              cudaStream_t s);
+cudaError_t launch_rotate(const float* vd, const float* vb, float* rd, float* rb, int Lz, int Ly, int Lx, float c,
+                          float sn, cudaStream_t s);
+cudaError_t launch_rotate_T(const float* gd_rot, const float* gb_rot, float* gd, float* gb, int Lz, int Ly, int Lx,
+                            float c, float sn, cudaStream_t s);
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s);
+int path_smem_bytes(int N);
+// set the dynamic shared-memory attributes of every kernel used for tile size N (call outside capture)
+cudaError_t prepare_path(int N, int farfield);
+
+}  // namespace adorym

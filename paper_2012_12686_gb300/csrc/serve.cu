@@ -1,0 +1,421 @@
+// Serving loop: continuous batching of loss/gradient requests over several CUDA streams.
+//
+// A request is queued by adorym_submit.  A worker thread admits queued requests in arrival
+// order whenever a slot (stream) is free and the request's workspace fits the footprint budget;
+// the workspace is carved from one device arena with a first-fit allocator.  Admitted requests
+// are recorded by stream capture into a CUDA graph and launched; the executable graph of each
+// (slot, problem shape) is kept and updated in place (cudaGraphExecUpdate) for the next
+// request of that shape, so steady-state launches cost one graph launch.  Completion is
+// detected with events; adorym_poll waits on a condition variable with a host-side timeout.
+// No device-side waiting is involved: a request that never completes shows up as ETIMEDOUT on
+// the host, never as a spinning kernel.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+
+#include "engine.h"
+
+namespace adorym {
+
+struct Arena {
+  // first-fit free list over [0, cap) of one device allocation
+  char* base = nullptr;
+  size_t cap = 0;
+  std::map<size_t, size_t> free_;   // offset -> size
+  size_t used = 0;
+  bool init(size_t bytes) {
+    if (cudaMalloc(&base, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      base = nullptr;
+      return false;
+    }
+    cap = bytes;
+    free_.clear();
+    free_[0] = bytes;
+    used = 0;
+    return true;
+  }
+  bool alloc(size_t bytes, size_t* off) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const size_t rest = it->second - bytes, o2 = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[o2] = rest;
+        used += bytes;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    used -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
+struct Ticket {
+  adorym_request req{};
+  Plan plan;
+  int state = 0;          // 0 queued, 1 running, 2 done
+  int rc = ADORYM_OK;
+  int slot = -1;
+  size_t ws_off = 0;
+  bool waited = false;
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  uint64_t ticket = 0;    // 0 = free
+  std::map<std::string, cudaGraphExec_t> graphs;
+};
+
+struct Serve {
+  int nslots = 4;
+  size_t budget = 0;      // bytes; 0 = arena default
+  Arena arena;
+  std::vector<Slot> slots;
+  std::deque<uint64_t> queue;
+  std::map<uint64_t, Ticket> tickets;
+  uint64_t next = 1;
+  uint64_t completed = 0, waits = 0;
+  bool stop = false;
+  std::thread worker;
+  std::condition_variable cv_work, cv_done;
+};
+
+static std::string shape_key(const Plan& pl, const adorym_request& r) {
+  char buf[320];
+  const adorym_problem& p = pl.p;
+  snprintf(buf, sizeof buf, "%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d%d%d%d|%d%d%d", p.N, p.L, p.M, p.B, p.Ly, p.Lx,
+           p.Lz, p.farfield, p.n_dist, p.loss, p.tomo, pl.cp, pl.ncp, r.g_delta != nullptr, r.g_probe != nullptr,
+           r.g_pos != nullptr, r.loss_out != nullptr, r.I_out != nullptr, 0, 0);
+  return std::string(buf);
+}
+
+// launch one admitted ticket on its slot (ctx->mu held)
+static int launch_ticket(adorym_ctx* ctx, Serve& S, uint64_t id) {
+  Ticket& t = S.tickets[id];
+  Slot& sl = S.slots[t.slot];
+  const adorym_request& r = t.req;
+  auto it = ctx->objects.find(r.obj_id);
+  if (it == ctx->objects.end()) {
+    ctx->err = "unknown object id";
+    return ADORYM_ENOENT;
+  }
+  Tables tab;
+  int rc = get_tables(ctx, r.problem, &tab);
+  if (rc) return rc;
+  CallPtrs c;
+  c.probe = reinterpret_cast<const float2*>(r.probe);
+  c.pos = r.pos;
+  c.I_meas = r.I_meas;
+  c.loss = r.loss_out;
+  c.gd = r.g_delta;
+  c.gb = r.g_beta;
+  c.g_probe = reinterpret_cast<float2*>(r.g_probe);
+  c.g_pos = r.g_pos;
+  c.I_out = r.I_out;
+  std::string err;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    ctx->err = std::string("begin capture: ") + cudaGetErrorString(e);
+    return ADORYM_EDEVICE;
+  }
+  rc = enqueue(t.plan, it->second, tab, c, S.arena.base + t.ws_off, sl.stream, &err);
+  e = cudaStreamEndCapture(sl.stream, &g);
+  if (rc || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    ctx->err = rc ? err : std::string("end capture: ") + cudaGetErrorString(e);
+    return rc ? rc : ADORYM_EDEVICE;
+  }
+  const std::string key = shape_key(t.plan, r);
+  auto git = sl.graphs.find(key);
+  bool ok = false;
+  if (git != sl.graphs.end()) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(git->second, g, &info) == cudaSuccess) ok = true;
+    else {
+      cudaGetLastError();
+      cudaGraphExecDestroy(git->second);
+      sl.graphs.erase(git);
+    }
+  }
+  if (!ok) {
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      ctx->err = std::string("graph instantiate: ") + cudaGetErrorString(e);
+      return ADORYM_EDEVICE;
+    }
+    sl.graphs[key] = ex;
+  }
+  cudaGraphDestroy(g);
+  e = cudaGraphLaunch(sl.graphs[key], sl.stream);
+  if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
+  if (e != cudaSuccess) {
+    ctx->err = std::string("graph launch: ") + cudaGetErrorString(e);
+    return ADORYM_EDEVICE;
+  }
+  return ADORYM_OK;
+}
+
+static void finish(Serve& S, uint64_t id, int rc) {
+  Ticket& t = S.tickets[id];
+  if (t.slot >= 0) {
+    S.slots[t.slot].ticket = 0;
+    S.arena.release(t.ws_off, t.plan.total);
+  }
+  t.state = 2;
+  t.rc = rc;
+  S.completed++;
+}
+
+static void worker_main(adorym_ctx* ctx) {
+  Serve& S = *ctx->serve;
+  cudaSetDevice(ctx->device);
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  while (!S.stop) {
+    bool progress = false;
+    // retire finished slots
+    for (auto& sl : S.slots) {
+      if (!sl.ticket) continue;
+      cudaError_t q = cudaEventQuery(sl.done);
+      if (q == cudaErrorNotReady) continue;
+      const uint64_t id = sl.ticket;
+      finish(S, id, q == cudaSuccess ? ADORYM_OK : ADORYM_EDEVICE);
+      if (q != cudaSuccess) ctx->err = std::string("request failed: ") + cudaGetErrorString(q);
+      progress = true;
+    }
+    // admit in arrival order while a slot and memory are free
+    while (!S.queue.empty()) {
+      const uint64_t id = S.queue.front();
+      Ticket& t = S.tickets[id];
+      int free_slot = -1;
+      for (int i = 0; i < (int)S.slots.size(); ++i)
+        if (!S.slots[i].ticket) {
+          free_slot = i;
+          break;
+        }
+      size_t off = 0;
+      if (free_slot < 0 || !S.arena.alloc(t.plan.total, &off)) {
+        if (!t.waited) S.waits++;
+        t.waited = true;
+        break;
+      }
+      S.queue.pop_front();
+      t.slot = free_slot;
+      t.ws_off = off;
+      t.state = 1;
+      S.slots[free_slot].ticket = id;
+      const int rc = launch_ticket(ctx, S, id);
+      if (rc) finish(S, id, rc);
+      progress = true;
+    }
+    if (progress) S.cv_done.notify_all();
+    bool busy = false;
+    for (auto& sl : S.slots) busy |= sl.ticket != 0;
+    if (busy) {
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      lk.lock();
+    } else {
+      S.cv_work.wait(lk, [&] { return S.stop || !S.queue.empty(); });
+    }
+  }
+}
+
+static int serve_start(adorym_ctx* ctx) {
+  if (ctx->serve) return ADORYM_OK;
+  auto S = std::make_unique<Serve>();
+  size_t freeb = 0, totalb = 0;
+  cudaSetDevice(ctx->device);
+  cudaMemGetInfo(&freeb, &totalb);
+  size_t budget = S->budget ? S->budget : std::min(freeb / 2, (size_t)8 << 30);
+  if (!S->arena.init(budget)) {
+    ctx->err = "serving arena allocation failed";
+    return ADORYM_ENOMEM;
+  }
+  S->slots.resize(S->nslots);
+  for (auto& sl : S->slots) {
+    cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+  }
+  ctx->serve = S.release();
+  ctx->serve->worker = std::thread(worker_main, ctx);
+  return ADORYM_OK;
+}
+
+void serve_shutdown(adorym_ctx* ctx) {
+  if (!ctx->serve) return;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->serve->stop = true;
+  }
+  ctx->serve->cv_work.notify_all();
+  if (ctx->serve->worker.joinable()) ctx->serve->worker.join();
+  Serve& S = *ctx->serve;
+  for (auto& sl : S.slots) {
+    cudaStreamSynchronize(sl.stream);
+    for (auto& kv : sl.graphs) cudaGraphExecDestroy(kv.second);
+    cudaStreamDestroy(sl.stream);
+    cudaEventDestroy(sl.done);
+  }
+  if (S.arena.base) cudaFree(S.arena.base);
+  delete ctx->serve;
+  ctx->serve = nullptr;
+}
+
+}  // namespace adorym
+
+using namespace adorym;
+
+extern "C" {
+
+int adorym_serve_config(adorym_ctx* ctx, int slots, uint64_t budget_bytes) {
+  if (!ctx) return ADORYM_EINVAL;
+  if (slots < 1 || slots > 16) {
+    ctx->err = "slots must be in 1..16";
+    return ADORYM_EINVAL;
+  }
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->serve) {
+      for (auto& kv : ctx->serve->tickets)
+        if (kv.second.state != 2) {
+          ctx->err = "requests in flight";
+          return ADORYM_EINVAL;
+        }
+    }
+  }
+  serve_shutdown(ctx);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto S = std::make_unique<Serve>();
+  S->nslots = slots;
+  S->budget = budget_bytes;
+  size_t freeb = 0, totalb = 0;
+  cudaSetDevice(ctx->device);
+  cudaMemGetInfo(&freeb, &totalb);
+  const size_t bytes = budget_bytes ? budget_bytes : std::min(freeb / 2, (size_t)8 << 30);
+  if (!S->arena.init(bytes)) {
+    ctx->err = "serving arena allocation failed";
+    return ADORYM_ENOMEM;
+  }
+  S->slots.resize(slots);
+  for (auto& sl : S->slots) {
+    cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+  }
+  ctx->serve = S.release();
+  ctx->serve->worker = std::thread(worker_main, ctx);
+  return ADORYM_OK;
+}
+
+int adorym_submit(adorym_ctx* ctx, const adorym_request* req, uint64_t* ticket) {
+  if (!ctx || !req || !ticket) return ADORYM_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!ctx->serve) {
+    int rc = serve_start(ctx);
+    if (rc) return rc;
+  }
+  Serve& S = *ctx->serve;
+  const adorym_request& r = *req;
+  if (!r.probe || !r.pos || !r.I_meas) {
+    ctx->err = "probe, pos and I_meas are required";
+    return ADORYM_EINVAL;
+  }
+  const void* ptrs[] = {r.probe, r.pos, r.I_meas, r.loss_out, r.g_delta, r.g_beta, r.g_probe, r.g_pos, r.I_out};
+  for (const void* q : ptrs) {
+    if (!q) continue;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, q) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+      cudaGetLastError();
+      ctx->err = "serving requests take device pointers only";
+      return ADORYM_EINVAL;
+    }
+  }
+  if ((r.g_delta == nullptr) != (r.g_beta == nullptr)) {
+    ctx->err = "g_delta and g_beta must both be given or both be NULL";
+    return ADORYM_EINVAL;
+  }
+  auto it = ctx->objects.find(r.obj_id);
+  if (it == ctx->objects.end()) {
+    ctx->err = "unknown object id";
+    return ADORYM_ENOENT;
+  }
+  const Object& obj = it->second;
+  if (obj.Lz != r.problem.Lz || obj.Ly != r.problem.Ly || obj.Lx != r.problem.Lx) {
+    ctx->err = "problem Lz/Ly/Lx differ from the registered object";
+    return ADORYM_EINVAL;
+  }
+  Ticket t;
+  t.req = r;
+  const int grads = (r.g_delta ? 1 : 0) | (r.g_probe ? 2 : 0) | (r.g_pos ? 4 : 0);
+  std::string err;
+  int rc = make_plan(r.problem, true, grads, r.loss_out != nullptr, &t.plan, &err);
+  if (rc) {
+    ctx->err = err;
+    return rc;
+  }
+  if (t.plan.total > S.arena.cap) {
+    ctx->err = "request workspace exceeds the serving footprint budget";
+    return ADORYM_ENOMEM;
+  }
+  // set kernel attributes and build tables outside of any capture
+  Tables tab;
+  if ((rc = get_tables(ctx, r.problem, &tab))) return rc;
+  if ((rc = prepare_kernels(r.problem, &err))) {
+    ctx->err = err;
+    return rc;
+  }
+  const uint64_t id = S.next++;
+  S.tickets[id] = t;
+  S.queue.push_back(id);
+  *ticket = id;
+  S.cv_work.notify_all();
+  return ADORYM_OK;
+}
+
+int adorym_poll(adorym_ctx* ctx, uint64_t ticket, int64_t timeout_us) {
+  if (!ctx) return ADORYM_EINVAL;
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  if (!ctx->serve) return ADORYM_ENOENT;
+  Serve& S = *ctx->serve;
+  auto it = S.tickets.find(ticket);
+  if (it == S.tickets.end()) return ADORYM_ENOENT;
+  auto ready = [&] { return S.tickets[ticket].state == 2; };
+  if (timeout_us < 0) S.cv_done.wait(lk, ready);
+  else if (timeout_us > 0) S.cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
+  if (!ready()) return ADORYM_ETIMEDOUT;
+  const int rc = S.tickets[ticket].rc;
+  S.tickets.erase(ticket);
+  return rc;
+}
+
+int adorym_serve_stats(adorym_ctx* ctx, uint64_t* completed, uint64_t* admission_waits) {
+  if (!ctx) return ADORYM_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (completed) *completed = ctx->serve ? ctx->serve->completed : 0;
+  if (admission_waits) *admission_waits = ctx->serve ? ctx->serve->waits : 0;
+  return ADORYM_OK;
+}
+
+}  // extern "C"
