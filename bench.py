@@ -317,12 +317,12 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clk.summary(), "wall_s_timed": wall}
     if not args.no_cpu_baseline and world == 1:
         cores = os.cpu_count() or 1
-        n_pos = 2 * cores
-        Im_np = I_meas[0, :n_pos].cpu().numpy()
-        ws = dict(w, pos=pos_b[0][:n_pos].cpu().numpy())
+        n_pos = min(8 * cores, len(all_pos))
+        Im_np = I_meas.reshape(-1, N, N)[:n_pos].cpu().numpy()
+        ws = dict(w, pos=all_pos[:n_pos])
         wall_c, npos = oracle_sample(ws, Im_np, n_pos, cores)
         line["cpu_baseline"] = {"value": npos * L / wall_c, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"{npos} positions x {L} slices of one minibatch, one position per "
+                                "sample": f"{npos} positions x {L} slices of the epoch, one position per "
                                           f"single-threaded process ({wall_c:.1f} s wall)"}
     print(json.dumps(line), flush=True)
 
@@ -342,8 +342,8 @@ def profiled_traffic(src_hash: str):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
