@@ -52,6 +52,8 @@ extern "C" {
 #define ADORYM_ETIMEDOUT 3   /* adorym_poll: the request did not finish within the timeout    */
 #define ADORYM_EDEVICE 4     /* a CUDA error was reported (message in adorym_last_error)      */
 #define ADORYM_ENOENT 5      /* unknown object id or ticket                                    */
+#define ADORYM_ETOOBIG 6     /* adorym_loss_grad_noalloc: the problem needs more scratch than
+                                ADORYM_NOALLOC_SCRATCH_BYTES                                   */
 
 #define ADORYM_LOSS_LSQ 0     /* Eq. lsq_loss: mean (sqrt(I+eps) - sqrt(I_meas+eps))^2        */
 #define ADORYM_LOSS_POISSON 1 /* Eq. poisson_loss: mean (I - I_meas log(I+eps))               */
@@ -169,6 +171,34 @@ int adorym_kernel_ms(adorym_ctx* ctx, float* path_ms);
 /* Device workspace (bytes) that adorym_loss_grad needs for this problem, for admission
  * planning by callers.  grads: bitmask 1 = object, 2 = probe, 4 = positions. */
 int adorym_workspace_bytes(const adorym_problem* p, int grads, uint64_t* bytes);
+
+/* Size of the fixed device scratch array used by adorym_loss_grad_noalloc. */
+#define ADORYM_NOALLOC_SCRATCH_BYTES ((uint64_t)64 << 20)
+
+/* adorym_loss_grad for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant of the same computation.
+ *
+ * Who needs it: code that runs where cudaMalloc is not allowed or not wanted -- inside a CUDA
+ * stream capture owned by someone else, in a plug-in whose host framework owns all device memory
+ * through its own pool, or in a latency-critical loop that must not allocate.  This call takes
+ * no context and allocates nothing (no cudaMalloc, cudaFree or allocating library routine):
+ * its workspace and tables live in one file-scope device array of ADORYM_NOALLOC_SCRATCH_BYTES
+ * (64 MiB), reserved on every GPU that loads the library until the process exits.
+ *
+ * Arguments are those of adorym_loss_grad (same layouts and accumulate/overwrite rules), except
+ * that the object volumes delta, beta ([Lz][Ly][Lx] FP32) are passed directly and every pointer
+ * must be device memory.  Work is enqueued on cuda_stream (a cudaStream_t) on the current device.
+ *
+ * Returns ADORYM_ETOOBIG when the problem's workspace exceeds the array (e.g. large batches of
+ * 128x128 tiles: use adorym_loss_grad there), EINVAL for invalid sizes or non-device pointers.
+ * The array's device address is looked up on the first call made on each device, so make that
+ * first call before any stream capture.  All calls share the array and it keeps the previous
+ * call's contents (each call clears on its stream what must start at zero); calls that overlap
+ * on the GPU -- on different streams or from several host threads -- race on it, so the caller
+ * must serialise them (e.g. one stream). */
+int adorym_loss_grad_noalloc(void* cuda_stream, const adorym_problem* p, const float* delta, const float* beta,
+                             const float* probe, const float* pos, const float* I_meas, double* loss_out,
+                             float* g_delta, float* g_beta, float* g_probe, float* g_pos, float* I_out);
 
 #ifdef __cplusplus
 }

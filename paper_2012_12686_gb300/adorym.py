@@ -14,13 +14,14 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libadorym.so")
 
-OK, EINVAL, ENOMEM, ETIMEDOUT, EDEVICE, ENOENT = 0, 1, 2, 3, 4, 5
+OK, EINVAL, ENOMEM, ETIMEDOUT, EDEVICE, ENOENT, ETOOBIG = 0, 1, 2, 3, 4, 5, 6
+NOALLOC_SCRATCH_BYTES = 64 << 20
 LOSS = {"lsq": 0, "poisson": 1}
 
 EXPORTS = ["adorym_create", "adorym_destroy", "adorym_last_error", "adorym_register_object",
            "adorym_unregister_object", "adorym_forward", "adorym_loss_grad", "adorym_submit", "adorym_poll",
            "adorym_serve_config", "adorym_serve_stats", "adorym_workspace_bytes", "adorym_enable_kernel_timing",
-           "adorym_kernel_ms"]
+           "adorym_kernel_ms", "adorym_loss_grad_noalloc"]
 
 
 class Problem(ctypes.Structure):
@@ -86,6 +87,7 @@ def lib() -> ctypes.CDLL:
         L.adorym_workspace_bytes.argtypes = [ctypes.POINTER(Problem), i32, ctypes.POINTER(u64)]
         L.adorym_enable_kernel_timing.argtypes = [vp, i32]
         L.adorym_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+        L.adorym_loss_grad_noalloc.argtypes = [vp, ctypes.POINTER(Problem), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("adorym_destroy", "adorym_last_error"):
                 getattr(L, name).restype = ctypes.c_int
@@ -203,6 +205,16 @@ class Engine:
         c, w = ctypes.c_uint64(), ctypes.c_uint64()
         self._check(lib().adorym_serve_stats(self._ctx, ctypes.byref(c), ctypes.byref(w)))
         return c.value, w.value
+
+
+def loss_grad_noalloc(stream, problem, delta, beta, probe, pos, I_meas, loss_out=None, g_delta=None, g_beta=None,
+                      g_probe=None, g_pos=None, I_out=None) -> int:
+    """adorym_loss_grad_noalloc: same computation as Engine.loss_grad with no device allocation
+    (fixed 64 MiB scratch); all arrays must be device memory.  Returns the library's code."""
+    p = problem if isinstance(problem, Problem) else Problem.of(problem)
+    return lib().adorym_loss_grad_noalloc(ctypes.c_void_p(stream), ctypes.byref(p), _ptr(delta), _ptr(beta),
+                                          _ptr(probe), _ptr(pos), _ptr(I_meas), _ptr(loss_out), _ptr(g_delta),
+                                          _ptr(g_beta), _ptr(g_probe), _ptr(g_pos), _ptr(I_out))
 
 
 def workspace_bytes(problem, grads: int = 7) -> int:

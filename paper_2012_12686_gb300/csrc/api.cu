@@ -12,7 +12,7 @@ static const double kPi = 3.14159265358979323846;
 
 static bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
 
-int validate(const adorym_problem& p, std::string* err) {
+int validate(const adorym_problem& p, const char** err) {
   auto bad = [&](const char* m) {
     *err = m;
     return ADORYM_EINVAL;
@@ -43,7 +43,7 @@ int validate(const adorym_problem& p, std::string* err) {
 
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan* pl, std::string* err) {
+int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan* pl, const char** err) {
   int rc = validate(p, err);
   if (rc) return rc;
   Plan q;
@@ -110,15 +110,10 @@ static std::string table_key(const adorym_problem& p) {
 
 static double freq(int k, int N) { return (double)(k <= (N - 1) / 2 ? k : k - N) / (double)N; }
 
-int get_tables(adorym_ctx* ctx, const adorym_problem& p, Tables* out) {
-  const std::string key = table_key(p);
-  auto it = ctx->tables.find(key);
-  if (it != ctx->tables.end()) {
-    *out = it->second;
-    return ADORYM_OK;
-  }
+size_t table_count(const adorym_problem& p) { return (size_t)(3 + (p.farfield ? 0 : p.n_dist)) * p.N; }
+
+void fill_tables(const adorym_problem& p, float2* h) {
   const int N = p.N, nd = p.farfield ? 0 : p.n_dist;
-  std::vector<float2> h((size_t)(3 + nd) * N);
   for (int m = 0; m < N; ++m) {   // W_N^m = exp(-2 pi i m / N), FP64 argument
     const double a = 2.0 * kPi * (double)m / (double)N;
     h[m] = make_float2((float)std::cos(a), (float)-std::sin(a));
@@ -135,6 +130,18 @@ int get_tables(adorym_ctx* ctx, const adorym_problem& p, Tables* out) {
       h[(size_t)(3 + d) * N + k] = make_float2((float)std::cos(ph), (float)std::sin(ph));
     }
   }
+}
+
+int get_tables(adorym_ctx* ctx, const adorym_problem& p, Tables* out) {
+  const std::string key = table_key(p);
+  auto it = ctx->tables.find(key);
+  if (it != ctx->tables.end()) {
+    *out = it->second;
+    return ADORYM_OK;
+  }
+  const int N = p.N, nd = p.farfield ? 0 : p.n_dist;
+  std::vector<float2> h(table_count(p));
+  fill_tables(p, h.data());
   Tables t;
   t.N = N;
   t.nd = nd;
@@ -240,11 +247,11 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
   return ADORYM_OK;
 }
 
-int prepare_kernels(const adorym_problem& p, std::string* err) {
+int prepare_kernels(const adorym_problem& p, const char** err) {
   cudaError_t e = prepare_path(p.N, p.farfield ? 1 : 0);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    *err = std::string("kernel attributes: ") + cudaGetErrorString(e);
+    *err = "kernel attributes could not be set";
     return ADORYM_EDEVICE;
   }
   return ADORYM_OK;
@@ -353,7 +360,7 @@ int adorym_unregister_object(adorym_ctx* ctx, int obj_id) {
 int adorym_workspace_bytes(const adorym_problem* p, int grads, uint64_t* bytes) {
   if (!p || !bytes) return ADORYM_EINVAL;
   Plan pl;
-  std::string err;
+  const char* err = "";
   int rc = make_plan(*p, true, grads, true, &pl, &err);
   if (rc) return rc;
   *bytes = pl.total;
@@ -380,13 +387,14 @@ static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const 
     return fail(ctx, ADORYM_EINVAL, "g_delta / g_beta must be device memory");
   const int grads = (g_delta ? 1 : 0) | (g_probe ? 2 : 0) | (g_pos ? 4 : 0);
   Plan pl;
+  const char* msg = "";
+  int rc = make_plan(*p, adj, grads, loss_out != nullptr, &pl, &msg);
+  if (rc) return fail(ctx, rc, msg);
   std::string err;
-  int rc = make_plan(*p, adj, grads, loss_out != nullptr, &pl, &err);
-  if (rc) return fail(ctx, rc, err);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "set device");
   Tables tab;
   if ((rc = get_tables(ctx, *p, &tab))) return rc;
-  if ((rc = prepare_kernels(*p, &err))) return fail(ctx, rc, err);
+  if ((rc = prepare_kernels(*p, &msg))) return fail(ctx, rc, msg);
   if ((rc = ensure_ws(ctx, pl.total))) return rc;
   char* ws = ctx->ws;
   cudaStream_t s = ctx->stream;

@@ -51,8 +51,11 @@ struct CallPtrs {
   float* I_out = nullptr;
 };
 
-int validate(const adorym_problem& p, std::string* err);
-int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan* plan, std::string* err);
+int validate(const adorym_problem& p, const char** err);
+int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan* plan, const char** err);
+// FP64-built tables (twiddles, propagator factors) of a problem: table_count(p) float2 values
+size_t table_count(const adorym_problem& p);
+void fill_tables(const adorym_problem& p, float2* out);
 
 struct Tables {
   float2* dev = nullptr;   // [tw N][hy N][hx N][hd n_dist*N]
@@ -90,6 +93,6 @@ struct adorym_ctx {
 
 namespace adorym {
 int get_tables(adorym_ctx* ctx, const adorym_problem& p, Tables* out);   // ctx->mu held
-int prepare_kernels(const adorym_problem& p, std::string* err);         // attributes, outside capture
+int prepare_kernels(const adorym_problem& p, const char** err);         // attributes, outside capture
 void serve_shutdown(adorym_ctx* ctx);
 }  // namespace adorym

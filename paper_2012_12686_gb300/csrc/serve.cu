@@ -369,10 +369,10 @@ int adorym_submit(adorym_ctx* ctx, const adorym_request* req, uint64_t* ticket) 
   Ticket t;
   t.req = r;
   const int grads = (r.g_delta ? 1 : 0) | (r.g_probe ? 2 : 0) | (r.g_pos ? 4 : 0);
-  std::string err;
-  int rc = make_plan(r.problem, true, grads, r.loss_out != nullptr, &t.plan, &err);
+  const char* msg = "";
+  int rc = make_plan(r.problem, true, grads, r.loss_out != nullptr, &t.plan, &msg);
   if (rc) {
-    ctx->err = err;
+    ctx->err = msg;
     return rc;
   }
   if (t.plan.total > S.arena.cap) {
@@ -382,8 +382,8 @@ int adorym_submit(adorym_ctx* ctx, const adorym_request* req, uint64_t* ticket) 
   // set kernel attributes and build tables outside of any capture
   Tables tab;
   if ((rc = get_tables(ctx, r.problem, &tab))) return rc;
-  if ((rc = prepare_kernels(r.problem, &err))) {
-    ctx->err = err;
+  if ((rc = prepare_kernels(r.problem, &msg))) {
+    ctx->err = msg;
     return rc;
   }
   const uint64_t id = S.next++;
