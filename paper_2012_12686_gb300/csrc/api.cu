@@ -80,10 +80,10 @@ int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan
   q.off_gI = take(B * q.nd * NN * sizeof(float));
   q.off_lossp = take(B * sizeof(double));
   q.off_loss = take(sizeof(double));
-  if (q.tomo) {
-    const size_t V = (size_t)p.Lz * p.Ly * p.Lx * sizeof(float);
-    q.off_rot = take(2 * V);
-    if (q.want_obj) q.off_grot = take(2 * V);
+  {
+    const size_t V = (size_t)p.Lz * p.Ly * p.Lx;
+    q.off_T = take(V * f2);
+    if (q.tomo && q.want_obj) q.off_grot = take(2 * V * sizeof(float));
   }
   q.bytes_probe = M * NN * f2;
   q.bytes_pos = B * q.nd * 2 * sizeof(float);
@@ -170,23 +170,20 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
     *err = std::string(what) + ": " + cudaGetErrorString(e);
     return ADORYM_EDEVICE;
   };
-  const float *vd = obj.d, *vb = obj.b;
   float *gd = c.gd, *gb = c.gb;
   const size_t V = (size_t)p.Lz * p.Ly * p.Lx;
   const double cth = std::cos(p.theta), sth = std::sin(p.theta);
   int rc;
-  if (pl.tomo) {
-    float* rot = reinterpret_cast<float*>(W(pl.off_rot));
-    if ((rc = chk(launch_rotate(obj.d, obj.b, rot, rot + V, p.Lz, p.Ly, p.Lx, (float)cth, (float)sth, s), "rotate")))
-      return rc;
-    vd = rot;
-    vb = rot + V;
-    if (pl.want_obj) {
-      float* grot = reinterpret_cast<float*>(W(pl.off_grot));
-      if ((rc = chk(cudaMemsetAsync(grot, 0, 2 * V * sizeof(float), s), "memset"))) return rc;
-      gd = grot;
-      gb = grot + V;
-    }
+  float2* T = reinterpret_cast<float2*>(W(pl.off_T));
+  if ((rc = chk(launch_transmission(obj.d, obj.b, T, p.Lz, p.Ly, p.Lx, (float)p.kdz, pl.tomo ? 1 : 0, (float)cth,
+                                    (float)sth, s),
+                "transmission")))
+    return rc;
+  if (pl.tomo && pl.want_obj) {
+    float* grot = reinterpret_cast<float*>(W(pl.off_grot));
+    if ((rc = chk(cudaMemsetAsync(grot, 0, 2 * V * sizeof(float), s), "memset"))) return rc;
+    gd = grot;
+    gb = grot + V;
   }
   float2* phat = reinterpret_cast<float2*>(W(pl.off_phat));
   if (pl.far) {
@@ -207,8 +204,7 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
   a.eps = (float)p.eps;
   a.kdz = (float)p.kdz;
   a.inv_npix = 1.0 / ((double)p.B * pl.nd * (double)pl.NN);
-  a.vd = vd;
-  a.vb = vb;
+  a.T = T;
   a.probe = c.probe;
   a.phat = phat;
   a.pos = c.pos;
@@ -241,7 +237,7 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
       return rc;
   }
   if (pl.tomo && pl.want_obj) {
-    if ((rc = chk(launch_rotate_T(gd, gb, c.gd, c.gb, p.Lz, p.Ly, p.Lx, (float)cth, (float)sth, s), "rotate_T")))
+    if ((rc = chk(launch_rotate_adj(gd, gb, c.gd, c.gb, p.Lz, p.Ly, p.Lx, (float)cth, (float)sth, s), "rotate_adj")))
       return rc;
   }
   return ADORYM_OK;

@@ -31,7 +31,7 @@ struct Plan {
   bool want_obj = false, want_probe = false, want_pos = false, want_loss = false;
   size_t NN = 0;
   size_t off_phat = 0, off_ckpt = 0, off_seg = 0, off_park = 0, off_far = 0, off_gI = 0, off_fbar = 0,
-         off_lossp = 0, off_qacc = 0, off_qsum = 0, off_rot = 0, off_grot = 0, off_loss = 0;
+         off_lossp = 0, off_qacc = 0, off_qsum = 0, off_T = 0, off_grot = 0, off_loss = 0;
   // staging for host-memory arguments
   size_t off_s_probe = 0, off_s_pos = 0, off_s_meas = 0, off_s_gprobe = 0, off_s_gpos = 0, off_s_iout = 0;
   size_t bytes_probe = 0, bytes_pos = 0, bytes_meas = 0, bytes_iout = 0;

@@ -106,32 +106,29 @@ __device__ __forceinline__ void dft(float2 (&v)[R]) {
   }
 }
 
+// twiddle multiply v[k] *= W_N^(S t k) from the FP64-built table tw[m] = exp(-2 pi i m / N)
 template <int S, int R>
-__device__ __forceinline__ void dft_s(float2 (&v)[R]) { dft<R, S>(v); }
-
-template <int R>
-__device__ __forceinline__ void dft_sign(float2 (&v)[R], int sign) {
-  if (sign < 0) dft<R, -1>(v); else dft<R, +1>(v);
-}
-
-// twiddle multiply v[k] *= W_N^(sign t k) from the FP64-built table tw[m] = exp(-2 pi i m / N)
-template <int R>
-__device__ __forceinline__ void twiddle(float2 (&v)[R], const float2* __restrict__ tw, int t, int sign) {
+__device__ __forceinline__ void twiddle(float2 (&v)[R], const float2* __restrict__ tw, int t) {
 #pragma unroll
   for (int k = 1; k < R; ++k) {
-    float2 w = tw[t * k];
-    v[k] = sign < 0 ? cmul(v[k], w) : cmulc(v[k], w);
+    const float2 w = tw[t * k];
+    v[k] = S < 0 ? cmul(v[k], w) : cmulc(v[k], w);
   }
 }
 
 template <int N_>
 struct Geo;
 // NT threads per CTA; MINB resident CTAs per SM the register budget is sized for (128 regs/thread)
-template <> struct Geo<8>   { static constexpr int N1 = 4,  N2 = 2, NT = 64,  MINB = 8; };
-template <> struct Geo<16>  { static constexpr int N1 = 4,  N2 = 4, NT = 64,  MINB = 8; };
-template <> struct Geo<32>  { static constexpr int N1 = 8,  N2 = 4, NT = 128, MINB = 4; };
-template <> struct Geo<64>  { static constexpr int N1 = 8,  N2 = 8, NT = 256, MINB = 2; };
-template <> struct Geo<128> { static constexpr int N1 = 16, N2 = 8, NT = 512, MINB = 1; };
+// The spatial passes (S4/S1, radix N1) carry the global-memory traffic of the pointwise ops, so
+// N1 is the smaller radix where the two differ.
+#ifndef ADORYM_NT128
+#define ADORYM_NT128 512
+#endif
+template <> struct Geo<8>   { static constexpr int N1 = 4, N2 = 2,  NT = 64,  MINB = 8; };
+template <> struct Geo<16>  { static constexpr int N1 = 4, N2 = 4,  NT = 64,  MINB = 8; };
+template <> struct Geo<32>  { static constexpr int N1 = 4, N2 = 8,  NT = 128, MINB = 4; };
+template <> struct Geo<64>  { static constexpr int N1 = 8, N2 = 8,  NT = 256, MINB = 2; };
+template <> struct Geo<128> { static constexpr int N1 = 8, N2 = 16, NT = ADORYM_NT128, MINB = 1; };
 
 template <int N>
 struct Field {
@@ -142,68 +139,47 @@ struct Field {
 };
 
 // ---------------------------------------------------------------------------
+// Passes.  Signs are compile-time: S = -1 (DFT_-), +1 (DFT_+), 0 (stage skipped).
+//
 // Column pass "14": tasks (x, t < N2); v[k] <-> sample y = N2*k + t.
-//   load:  regs from smem (always)
-//   s4:    0 = no S4 (slots already natural), else S4 with this sign
-//   op(v, x, t): spatial pointwise op on natural samples (may read/write global)
-//   s1:    0 = store natural, else S1 with this sign, then store
+//   pre(pa, pb, x, t): issues the task's global loads before the smem loads and S4
+//   op(v, pa, pb, x, t): spatial pointwise op on natural samples
+//   S1 != 0: S1 then store; S1 == 0: store natural samples; STORE = false: no store
+// LOAD = false: the samples come from op (no smem read, no S4).
 // ---------------------------------------------------------------------------
-template <int N, class Op>
-__device__ __forceinline__ void pass_c14(float2* __restrict__ A, const float2* __restrict__ tw, int s4, int s1, Op op) {
-  using F = Field<N>;
-  constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD;
-  for (int tau = threadIdx.x; tau < N * N2; tau += F::NT) {
-    const int x = tau % N, t = tau / N;
-    float2 v[N1];
-#pragma unroll
-    for (int i = 0; i < N1; ++i) v[i] = A[(N2 * i + t) * LD + x];
-    if (s4) dft_sign<N1>(v, s4);
-    op(v, x, t);
-    if (s1) {
-      dft_sign<N1>(v, s1);
-      twiddle<N1>(v, tw, t, s1);
-    }
-#pragma unroll
-    for (int i = 0; i < N1; ++i) A[(N2 * i + t) * LD + x] = v[i];
-  }
-}
+struct NoPre {
+  template <int R>
+  __device__ __forceinline__ void operator()(float2 (&)[R], float2 (&)[R], int, int) const {}
+};
 
-// Column pass that only reads natural samples (S4 optional) and does not store back.
-template <int N, class Op>
-__device__ __forceinline__ void pass_c4_out(const float2* __restrict__ A, int s4, Op op) {
+template <int N, int S4, int S1, bool LOAD, bool STORE, class Pre, class Op>
+__device__ __forceinline__ void pass_c14(float2* __restrict__ A, const float2* __restrict__ tw, Pre pre, Op op) {
   using F = Field<N>;
   constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD;
   for (int tau = threadIdx.x; tau < N * N2; tau += F::NT) {
     const int x = tau % N, t = tau / N;
-    float2 v[N1];
+    float2 pa[N1], pb[N1], v[N1];
+    pre(pa, pb, x, t);
+    if (LOAD) {
 #pragma unroll
-    for (int i = 0; i < N1; ++i) v[i] = A[(N2 * i + t) * LD + x];
-    if (s4) dft_sign<N1>(v, s4);
-    op(v, x, t);
-  }
-}
-
-// Column pass that produces natural samples from op (no smem read), then S1 (optional) and stores.
-template <int N, class Op>
-__device__ __forceinline__ void pass_c1_in(float2* __restrict__ A, const float2* __restrict__ tw, int s1, Op op) {
-  using F = Field<N>;
-  constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD;
-  for (int tau = threadIdx.x; tau < N * N2; tau += F::NT) {
-    const int x = tau % N, t = tau / N;
-    float2 v[N1];
-    op(v, x, t);
-    if (s1) {
-      dft_sign<N1>(v, s1);
-      twiddle<N1>(v, tw, t, s1);
+      for (int i = 0; i < N1; ++i) v[i] = A[(N2 * i + t) * LD + x];
+      if (S4) dft<N1, S4>(v);
     }
+    op(v, pa, pb, x, t);
+    if (STORE) {
+      if (S1) {
+        dft<N1, S1>(v);
+        twiddle<S1>(v, tw, t);
+      }
 #pragma unroll
-    for (int i = 0; i < N1; ++i) A[(N2 * i + t) * LD + x] = v[i];
+      for (int i = 0; i < N1; ++i) A[(N2 * i + t) * LD + x] = v[i];
+    }
   }
 }
 
 // Column pass "2" (S2, forward second stage) or "3" (S3, inverse-side first stage), in place.
-template <int N, bool IS_S3>
-__device__ __forceinline__ void pass_c23(float2* __restrict__ A, const float2* __restrict__ tw, int sign) {
+template <int N, bool IS_S3, int S>
+__device__ __noinline__ void pass_c23(float2* __restrict__ A, const float2* __restrict__ tw) {
   using F = Field<N>;
   constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD;
   for (int tau = threadIdx.x; tau < N * N1; tau += F::NT) {
@@ -211,16 +187,16 @@ __device__ __forceinline__ void pass_c23(float2* __restrict__ A, const float2* _
     float2 v[N2];
 #pragma unroll
     for (int i = 0; i < N2; ++i) v[i] = A[(N2 * t + i) * LD + x];
-    dft_sign<N2>(v, sign);
-    if (IS_S3) twiddle<N2>(v, tw, t, sign);
+    dft<N2, S>(v);
+    if (IS_S3) twiddle<S>(v, tw, t);
 #pragma unroll
     for (int i = 0; i < N2; ++i) A[(N2 * t + i) * LD + x] = v[i];
   }
 }
 
 // Row pass "1" (S1 forward first stage) or "4" (S4 inverse-side second stage), in place.
-template <int N, bool IS_S1>
-__device__ __forceinline__ void pass_r14(float2* __restrict__ A, const float2* __restrict__ tw, int sign) {
+template <int N, bool IS_S1, int S>
+__device__ __noinline__ void pass_r14(float2* __restrict__ A, const float2* __restrict__ tw) {
   using F = Field<N>;
   constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD;
   for (int tau = threadIdx.x; tau < N * N2; tau += F::NT) {
@@ -228,34 +204,34 @@ __device__ __forceinline__ void pass_r14(float2* __restrict__ A, const float2* _
     float2 v[N1];
 #pragma unroll
     for (int i = 0; i < N1; ++i) v[i] = A[r * LD + N2 * i + t];
-    dft_sign<N1>(v, sign);
-    if (IS_S1) twiddle<N1>(v, tw, t, sign);
+    dft<N1, S>(v);
+    if (IS_S1) twiddle<S>(v, tw, t);
 #pragma unroll
     for (int i = 0; i < N1; ++i) A[r * LD + N2 * i + t] = v[i];
   }
 }
 
 // Row pass "23": tasks (row r, t < N1).  Frequencies: ky = row_freq(r), kx = t + N1*i.
-//   s2:  0 = regs come from op_in (no smem read), else smem read + S2 with this sign
+//   S2 != 0: smem read + S2; S2 == 0: the values come from op
 //   op(v, ky, t): frequency-domain pointwise op
-//   s3:  0 = no store, else S3 with this sign and store in place
-template <int N, class Op>
-__device__ __forceinline__ void pass_r23(float2* __restrict__ A, const float2* __restrict__ tw, int s2, int s3, Op op) {
+//   S3 != 0: S3 and store in place; S3 == 0: no store
+template <int N, int S2, int S3, class Op>
+__device__ __forceinline__ void pass_r23(float2* __restrict__ A, const float2* __restrict__ tw, Op op) {
   using F = Field<N>;
   constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD;
   for (int tau = threadIdx.x; tau < N * N1; tau += F::NT) {
     const int r = tau % N, t = tau / N;
     const int ky = F::row_freq(r);
     float2 v[N2];
-    if (s2) {
+    if (S2) {
 #pragma unroll
       for (int i = 0; i < N2; ++i) v[i] = A[r * LD + N2 * t + i];
-      dft_sign<N2>(v, s2);
+      dft<N2, S2>(v);
     }
     op(v, ky, t);
-    if (s3) {
-      dft_sign<N2>(v, s3);
-      twiddle<N2>(v, tw, t, s3);
+    if (S3) {
+      dft<N2, S3>(v);
+      twiddle<S3>(v, tw, t);
 #pragma unroll
       for (int i = 0; i < N2; ++i) A[r * LD + N2 * t + i] = v[i];
     }

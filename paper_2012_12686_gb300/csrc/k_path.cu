@@ -57,6 +57,8 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
   using F = Field<N>;
   constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD, NT = F::NT;
   constexpr size_t NN = (size_t)N * N;
+  using V1 = float2[N1];
+  using V2 = float2[N2];
   extern __shared__ float2 sm[];
   float2* A = sm;
   float2* tw = A + N * LD;
@@ -87,42 +89,40 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
 
   const int Ly = a.Ly, Lx = a.Lx;
   const float kdz = a.kdz;
-  // transmission T_j at patch pixel (y, x); voxels outside the volume are vacuum
-  auto trans = [&](int j, int y, int x) -> float2 {
-    int gy = p0y + y, gx = p0x + x, gz = FAR ? j : b * L + j;
-    float d = 0.f, bb = 0.f;
-    if (gy >= 0 && gy < Ly && gx >= 0 && gx < Lx) {
-      size_t o = ((size_t)gz * Ly + gy) * Lx + gx;
-      d = __ldg(a.vd + o);
-      bb = __ldg(a.vb + o);
-    }
-    float s, c;
-    sincosf(kdz * d, &s, &c);
-    float e = expf(-kdz * bb);
-    return make_float2(e * c, e * s);
+  // transmission T_j at patch pixel (y, x); voxels outside the volume are vacuum (T = 1)
+  auto tload = [&](int j, int y, int x) -> float2 {
+    const int gy = p0y + y, gx = p0x + x, gz = FAR ? j : b * L + j;
+    if (gy >= 0 && gy < Ly && gx >= 0 && gx < Lx) return __ldg(a.T + ((size_t)gz * Ly + gy) * Lx + gx);
+    return make_float2(1.f, 0.f);
   };
-  auto hop = [&](float2 (&v)[N2], int ky, int t) {
-    float2 h = hy[ky];
+  auto pre_T = [&](int j) {
+    return [&, j](V1& pa, V1&, int x, int t) {
+#pragma unroll
+      for (int k = 0; k < N1; ++k) pa[k] = tload(j, N2 * k + t, x);
+    };
+  };
+  auto hop = [&](V2& v, int ky, int t) {
+    const float2 h = hy[ky];
 #pragma unroll
     for (int i = 0; i < N2; ++i) v[i] = cmul(cmul(v[i], h), hx[t + N1 * i]);
   };
-  auto hop_conj = [&](float2 (&v)[N2], int ky, int t) {
-    float2 h = hy[ky];
+  auto hop_conj = [&](V2& v, int ky, int t) {
+    const float2 h = hy[ky];
 #pragma unroll
     for (int i = 0; i < N2; ++i) v[i] = cmulc(cmulc(v[i], h), hx[t + N1 * i]);
   };
-  // the rest of a propagation step after C14: C2, R1, R23(H), R4, C3
+  // the rest of a propagation step after C14: C2, R1, R23(H or conj H), R4, C3
   auto propagate_tail = [&](bool adjoint) {
-    pass_c23<N, false>(A, tw, -1);
+    pass_c23<N, false, -1>(A, tw);
     __syncthreads();
-    pass_r14<N, true>(A, tw, -1);
+    pass_r14<N, true, -1>(A, tw);
     __syncthreads();
-    if (adjoint) pass_r23<N>(A, tw, -1, +1, hop_conj);
-    else pass_r23<N>(A, tw, -1, +1, hop);
+    if (adjoint) pass_r23<N, -1, +1>(A, tw, hop_conj);
+    else pass_r23<N, -1, +1>(A, tw, hop);
     __syncthreads();
-    pass_r14<N, false>(A, tw, +1);
+    pass_r14<N, false, +1>(A, tw);
     __syncthreads();
-    pass_c23<N, true>(A, tw, +1);
+    pass_c23<N, true, +1>(A, tw);
     __syncthreads();
   };
 
@@ -139,23 +139,24 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
     float2* ck = ck_b + (size_t)m * ncp * NN;
     float2* sg = seg_b + (size_t)m * cp * NN;
     // spatial op of slice j: store psi_j where the adjoint needs it, then modulate
-    auto fwd_op = [&](int j) {
-      return [&, j](float2 (&v)[N1], int x, int t) {
+    auto fwd_op = [&](int j, bool from_pb) {
+      return [&, j, from_pb](V1& v, V1& pa, V1& pb, int x, int t) {
 #pragma unroll
         for (int k = 0; k < N1; ++k) {
           const int y = N2 * k + t;
+          if (from_pb) v[k] = pb[k];
           if (adj) {
             if (j % cp == 0) ck[(size_t)(j / cp) * NN + y * N + x] = v[k];
             else if (j > j0_last) sg[(size_t)(j - j0_last) * NN + y * N + x] = v[k];
           }
-          v[k] = cmul(v[k], trans(j, y, x));
+          v[k] = cmul(v[k], pa[k]);
         }
       };
     };
     if (FAR) {
       // psi_0 = IDFT_-(P^ ramp), built in Fourier space at the R23 layout
       const float2* ph = a.phat + (size_t)m * NN;
-      pass_r23<N>(A, tw, 0, +1, [&](float2 (&v)[N2], int ky, int t) {
+      pass_r23<N, 0, +1>(A, tw, [&](V2& v, int ky, int t) {
         const float2 r = cscale(ry[ky], invNN);
 #pragma unroll
         for (int i = 0; i < N2; ++i) {
@@ -164,38 +165,40 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
         }
       });
       __syncthreads();
-      pass_r14<N, false>(A, tw, +1);
+      pass_r14<N, false, +1>(A, tw);
       __syncthreads();
-      pass_c23<N, true>(A, tw, +1);
+      pass_c23<N, true, +1>(A, tw);
       __syncthreads();
     }
     for (int j = 0; j < L; ++j) {
       const bool last = (j == L - 1);
-      const int s1 = (FAR && last) ? +1 : -1;
       if (!FAR && j == 0) {
+        // the illumination enters through pb; near field always starts its last transform with DFT_-
         const float2* pr = a.probe + (size_t)m * NN;
-        auto op = fwd_op(0);
-        pass_c1_in<N>(A, tw, s1, [&](float2 (&v)[N1], int x, int t) {
+        auto T0 = pre_T(0);
+        pass_c14<N, 0, -1, false, true>(A, tw, [&](V1& pa, V1& pb, int x, int t) {
+          T0(pa, pb, x, t);
 #pragma unroll
-          for (int k = 0; k < N1; ++k) v[k] = __ldg(&pr[(N2 * k + t) * N + x]);
-          op(v, x, t);
-        });
+          for (int k = 0; k < N1; ++k) pb[k] = __ldg(&pr[(N2 * k + t) * N + x]);
+        }, fwd_op(0, true));
+      } else if (FAR && last) {
+        pass_c14<N, +1, +1, true, true>(A, tw, pre_T(j), fwd_op(j, false));
       } else {
-        pass_c14<N>(A, tw, +1, s1, fwd_op(j));
+        pass_c14<N, +1, -1, true, true>(A, tw, pre_T(j), fwd_op(j, false));
       }
       __syncthreads();
       if (!last) {
         propagate_tail(false);
         continue;
       }
-      pass_c23<N, false>(A, tw, s1);
-      __syncthreads();
-      pass_r14<N, true>(A, tw, s1);
-      __syncthreads();
       if (FAR) {
         // Psi = (1/N) DFT_+[phi]; keep Psi, accumulate I over modes
+        pass_c23<N, false, +1>(A, tw);
+        __syncthreads();
+        pass_r14<N, true, +1>(A, tw);
+        __syncthreads();
         float2* fm = a.far + ((size_t)b * M + m) * NN;
-        pass_r23<N>(A, tw, +1, 0, [&](float2 (&v)[N2], int ky, int t) {
+        pass_r23<N, +1, 0>(A, tw, [&](V2& v, int ky, int t) {
 #pragma unroll
           for (int i = 0; i < N2; ++i) {
             const int p = ky * N + t + N1 * i;
@@ -208,8 +211,12 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
         __syncthreads();
       } else {
         // Phi = DFT_-[phi] kept at slot n_dist; then Psi_d = IDFT_-{Phi G_d} per distance
+        pass_c23<N, false, -1>(A, tw);
+        __syncthreads();
+        pass_r14<N, true, -1>(A, tw);
+        __syncthreads();
         float2* Phi = a.far + (((size_t)b * (nd + 1) + nd) * M + m) * NN;
-        pass_r23<N>(A, tw, -1, 0, [&](float2 (&v)[N2], int ky, int t) {
+        pass_r23<N, -1, 0>(A, tw, [&](V2& v, int ky, int t) {
 #pragma unroll
           for (int i = 0; i < N2; ++i) Phi[ky * N + t + N1 * i] = v[i];
         });
@@ -220,7 +227,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
           ramp_table(rx, (double)sd[1], N, NT);
           __syncthreads();
           const float2* hd = a.hd + (size_t)d * N;
-          pass_r23<N>(A, tw, 0, +1, [&](float2 (&v)[N2], int ky, int t) {
+          pass_r23<N, 0, +1>(A, tw, [&](V2& v, int ky, int t) {
             const float2 gy = cscale(cmul(__ldg(&hd[ky]), ry[ky]), invNN);
 #pragma unroll
             for (int i = 0; i < N2; ++i) {
@@ -229,13 +236,13 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
             }
           });
           __syncthreads();
-          pass_r14<N, false>(A, tw, +1);
+          pass_r14<N, false, +1>(A, tw);
           __syncthreads();
-          pass_c23<N, true>(A, tw, +1);
+          pass_c23<N, true, +1>(A, tw);
           __syncthreads();
           float2* fd = a.far + (((size_t)b * (nd + 1) + d) * M + m) * NN;
           float* gId = gI_b + (size_t)d * NN;
-          pass_c4_out<N>(A, +1, [&](float2 (&v)[N1], int x, int t) {
+          pass_c14<N, +1, 0, true, false>(A, tw, NoPre(), [&](V1& v, V1&, V1&, int x, int t) {
 #pragma unroll
             for (int k = 0; k < N1; ++k) {
               const int p = (N2 * k + t) * N + x;
@@ -291,7 +298,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
       // phibar_{L-1} = (1/N) DFT_-[2 gI Psi]
       const float2* fm = a.far + ((size_t)b * M + m) * NN;
       const float sc = 2.0f * invN;
-      pass_r23<N>(A, tw, 0, -1, [&](float2 (&v)[N2], int ky, int t) {
+      pass_r23<N, 0, -1>(A, tw, [&](V2& v, int ky, int t) {
 #pragma unroll
         for (int i = 0; i < N2; ++i) {
           const int p = ky * N + t + N1 * i;
@@ -299,9 +306,9 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
         }
       });
       __syncthreads();
-      pass_r14<N, false>(A, tw, -1);
+      pass_r14<N, false, -1>(A, tw);
       __syncthreads();
-      pass_c23<N, true>(A, tw, -1);
+      pass_c23<N, true, -1>(A, tw);
       __syncthreads();
     } else {
       const float2* Phi = a.far + (((size_t)b * (nd + 1) + nd) * M + m) * NN;
@@ -314,20 +321,24 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
         const float* gId = gI_b + (size_t)d * NN;
         __syncthreads();
         // Q_d = DFT_-[2 gI_d Psi_d]
-        pass_c1_in<N>(A, tw, -1, [&](float2 (&v)[N1], int x, int t) {
+        pass_c14<N, 0, -1, false, true>(A, tw, [&](V1& pa, V1& pb, int x, int t) {
 #pragma unroll
           for (int k = 0; k < N1; ++k) {
             const int p = (N2 * k + t) * N + x;
-            v[k] = cscale(fd[p], 2.0f * gId[p]);
+            pa[k] = fd[p];
+            pb[k].x = gId[p];
           }
+        }, [&](V1& v, V1& pa, V1& pb, int, int) {
+#pragma unroll
+          for (int k = 0; k < N1; ++k) v[k] = cscale(pa[k], 2.0f * pb[k].x);
         });
         __syncthreads();
-        pass_c23<N, false>(A, tw, -1);
+        pass_c23<N, false, -1>(A, tw);
         __syncthreads();
-        pass_r14<N, true>(A, tw, -1);
+        pass_r14<N, true, -1>(A, tw);
         __syncthreads();
         const float2* hd = a.hd + (size_t)d * N;
-        pass_r23<N>(A, tw, -1, 0, [&](float2 (&v)[N2], int ky, int t) {
+        pass_r23<N, -1, 0>(A, tw, [&](V2& v, int ky, int t) {
           const float2 gy = cmul(__ldg(&hd[ky]), ry[ky]);
           const float fyk = (float)freqd(ky, N);
           float ay = 0.f, ax = 0.f;
@@ -347,14 +358,14 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
         __syncthreads();
       }
       // phibar_{L-1} = IDFT_-{sum_d conj(G_d) Q_d}
-      pass_r23<N>(A, tw, 0, +1, [&](float2 (&v)[N2], int ky, int t) {
+      pass_r23<N, 0, +1>(A, tw, [&](V2& v, int ky, int t) {
 #pragma unroll
         for (int i = 0; i < N2; ++i) v[i] = cscale(fb[ky * N + t + N1 * i], invNN);
       });
       __syncthreads();
-      pass_r14<N, false>(A, tw, +1);
+      pass_r14<N, false, +1>(A, tw);
       __syncthreads();
-      pass_c23<N, true>(A, tw, +1);
+      pass_c23<N, true, +1>(A, tw);
       __syncthreads();
     }
 
@@ -366,21 +377,29 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
         __syncthreads();
         // recompute psi_{j0+1..j1} from the checkpoint psi_{j0}
         for (int j = j0; j < j1; ++j) {
-          auto op = [&, j](float2 (&v)[N1], int x, int t) {
+          if (j == j0) {
+            auto T0 = pre_T(j);
+            pass_c14<N, 0, -1, false, true>(A, tw, [&](V1& pa, V1& pb, int x, int t) {
+              T0(pa, pb, x, t);
 #pragma unroll
-            for (int k = 0; k < N1; ++k) {
-              const int y = N2 * k + t;
-              if (j == j0) v[k] = ck[(size_t)s * NN + y * N + x];
-              else sg[(size_t)(j - j0) * NN + y * N + x] = v[k];
-              v[k] = cmul(v[k], trans(j, y, x));
-            }
-          };
-          if (j == j0) pass_c1_in<N>(A, tw, -1, op);
-          else pass_c14<N>(A, tw, +1, -1, op);
+              for (int k = 0; k < N1; ++k) pb[k] = ck[(size_t)s * NN + (N2 * k + t) * N + x];
+            }, [&](V1& v, V1& pa, V1& pb, int, int) {
+#pragma unroll
+              for (int k = 0; k < N1; ++k) v[k] = cmul(pb[k], pa[k]);
+            });
+          } else {
+            pass_c14<N, +1, -1, true, true>(A, tw, pre_T(j), [&, j](V1& v, V1& pa, V1&, int x, int t) {
+#pragma unroll
+              for (int k = 0; k < N1; ++k) {
+                sg[(size_t)(j - j0) * NN + (N2 * k + t) * N + x] = v[k];
+                v[k] = cmul(v[k], pa[k]);
+              }
+            });
+          }
           __syncthreads();
           propagate_tail(false);
         }
-        pass_c4_out<N>(A, +1, [&](float2 (&v)[N1], int x, int t) {
+        pass_c14<N, +1, 0, true, false>(A, tw, NoPre(), [&](V1& v, V1&, V1&, int x, int t) {
 #pragma unroll
           for (int k = 0; k < N1; ++k) sg[(size_t)(j1 - j0) * NN + (N2 * k + t) * N + x] = v[k];
         });
@@ -389,54 +408,52 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
         __syncthreads();
       }
       for (int j = j1; j >= j0; --j) {
-        const int s4 = (FAR && j == L - 1) ? -1 : +1;
         const bool first = (j == 0);
-        auto op = [&, j](float2 (&v)[N1], int x, int t) {
+        // prefetch T_j and psi_j (checkpoint or recomputed segment)
+        auto pre = [&, j](V1& pa, V1& pb, int x, int t) {
+          const float2* src = (j == j0) ? ck + (size_t)s * NN : sg + (size_t)(j - j0) * NN;
+#pragma unroll
+          for (int k = 0; k < N1; ++k) {
+            pa[k] = tload(j, N2 * k + t, x);
+            pb[k] = src[(N2 * k + t) * N + x];
+          }
+        };
+        float2* q0 = (!FAR && first && a.qacc) ? a.qacc + ((size_t)b * M + m) * NN : nullptr;
+        auto op = [&, j, q0](V1& v, V1& pa, V1& pb, int x, int t) {
 #pragma unroll
           for (int k = 0; k < N1; ++k) {
             const int y = N2 * k + t;
-            const float2 psi = (j == j0) ? ck[(size_t)s * NN + y * N + x] : sg[(size_t)(j - j0) * NN + y * N + x];
-            const float2 T = trans(j, y, x);
-            const float2 pb = cmulc(v[k], T);           // psibar_j = conj(T_j) phibar_j
+            const float2 pbar = cmulc(v[k], pa[k]);     // psibar_j = conj(T_j) phibar_j
             if (want_obj) {
               const int gy = p0y + y, gx = p0x + x, gz = FAR ? j : b * L + j;
               if (gy >= 0 && gy < Ly && gx >= 0 && gx < Lx) {
-                const float2 z = cmulc(pb, psi);        // psibar conj(psi)
+                const float2 z = cmulc(pbar, pb[k]);    // psibar conj(psi)
                 const size_t o = ((size_t)gz * Ly + gy) * Lx + gx;
                 atomicAdd(a.gd + o, kdz * z.y);
                 atomicAdd(a.gb + o, -kdz * z.x);
               }
             }
-            v[k] = pb;
+            v[k] = pbar;
+            if (q0) q0[y * N + x] = pbar;               // near field: illumination gradient
           }
         };
-        if (!FAR && first) {
-          // illumination gradient (no shift in the near-field geometry): psibar_0 itself
-          float2* q = a.qacc ? a.qacc + ((size_t)b * M + m) * NN : nullptr;
-          pass_c4_out<N>(A, s4, [&](float2 (&v)[N1], int x, int t) {
-            op(v, x, t);
-            if (q) {
-#pragma unroll
-              for (int k = 0; k < N1; ++k) q[(N2 * k + t) * N + x] = v[k];
-            }
-          });
-          __syncthreads();
-          continue;
-        }
-        pass_c14<N>(A, tw, s4, -1, op);
+        if (FAR && j == L - 1) pass_c14<N, -1, -1, true, true>(A, tw, pre, op);
+        else if (!FAR && first) pass_c14<N, +1, 0, true, false>(A, tw, pre, op);
+        else pass_c14<N, +1, -1, true, true>(A, tw, pre, op);
         __syncthreads();
         if (!first) {
           propagate_tail(true);
           continue;
         }
+        if (!FAR) continue;
         // far field, j = 0: Q = DFT_-[psibar_0] -> probe and position gradients
-        pass_c23<N, false>(A, tw, -1);
+        pass_c23<N, false, -1>(A, tw);
         __syncthreads();
-        pass_r14<N, true>(A, tw, -1);
+        pass_r14<N, true, -1>(A, tw);
         __syncthreads();
         const float2* ph = a.phat + (size_t)m * NN;
         float2* q = a.qacc ? a.qacc + ((size_t)b * M + m) * NN : nullptr;
-        pass_r23<N>(A, tw, -1, 0, [&](float2 (&v)[N2], int ky, int t) {
+        pass_r23<N, -1, 0>(A, tw, [&](V2& v, int ky, int t) {
           const float2 r_y = ry[ky];
           const float fyk = (float)freqd(ky, N);
           float ay = 0.f, ax = 0.f;
@@ -482,16 +499,18 @@ __global__ void __launch_bounds__(Geo<N>::NT) k_probe_hat(const float2* __restri
   __syncthreads();
   const float2* p = probe + (size_t)blockIdx.x * N * N;
   float2* o = phat + (size_t)blockIdx.x * N * N;
-  pass_c1_in<N>(A, tw, -1, [&](float2 (&v)[N1], int x, int t) {
+  using V1 = float2[N1];
+  using V2 = float2[N2];
+  pass_c14<N, 0, -1, false, true>(A, tw, NoPre(), [&](V1& v, V1&, V1&, int x, int t) {
 #pragma unroll
     for (int k = 0; k < N1; ++k) v[k] = p[(N2 * k + t) * N + x];
   });
   __syncthreads();
-  pass_c23<N, false>(A, tw, -1);
+  pass_c23<N, false, -1>(A, tw);
   __syncthreads();
-  pass_r14<N, true>(A, tw, -1);
+  pass_r14<N, true, -1>(A, tw);
   __syncthreads();
-  pass_r23<N>(A, tw, -1, 0, [&](float2 (&v)[N2], int ky, int t) {
+  pass_r23<N, -1, 0>(A, tw, [&](V2& v, int ky, int t) {
 #pragma unroll
     for (int i = 0; i < N2; ++i) o[ky * N + t + N1 * i] = v[i];
   });
@@ -537,16 +556,18 @@ __global__ void __launch_bounds__(Geo<N>::NT) k_probe_grad(const float2* __restr
   for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
   __syncthreads();
   const float invNN = 1.0f / (float)NN;
-  pass_r23<N>(A, tw, 0, +1, [&](float2 (&v)[N2], int ky, int t) {
+  using V1 = float2[N1];
+  using V2 = float2[N2];
+  pass_r23<N, 0, +1>(A, tw, [&](V2& v, int ky, int t) {
 #pragma unroll
     for (int i = 0; i < N2; ++i) v[i] = cscale(q[ky * N + t + N1 * i], invNN);
   });
   __syncthreads();
-  pass_r14<N, false>(A, tw, +1);
+  pass_r14<N, false, +1>(A, tw);
   __syncthreads();
-  pass_c23<N, true>(A, tw, +1);
+  pass_c23<N, true, +1>(A, tw);
   __syncthreads();
-  pass_c4_out<N>(A, +1, [&](float2 (&v)[N1], int x, int t) {
+  pass_c14<N, +1, 0, true, false>(A, tw, NoPre(), [&](V1& v, V1&, V1&, int x, int t) {
 #pragma unroll
     for (int k = 0; k < N1; ++k) {
       const int p = (N2 * k + t) * N + x;
@@ -556,9 +577,21 @@ __global__ void __launch_bounds__(Geo<N>::NT) k_probe_grad(const float2* __restr
 }
 
 // ---------------------------------------------------------------------------- launchers
+// field + tw, hy, hx, ry, rx tables + one double per warp for block reductions
+template <int N>
+static constexpr int path_smem_bytes_t() {
+  return (N * (N + 1) + 5 * N) * (int)sizeof(float2) + (Geo<N>::NT / 32) * (int)sizeof(double);
+}
+
 int path_smem_bytes(int N) {
-  const int NT = N == 128 ? 512 : N == 64 ? 256 : N == 32 ? 128 : 64;
-  return (N * (N + 1) + 5 * N) * (int)sizeof(float2) + (NT / 32) * (int)sizeof(double);
+  switch (N) {
+    case 8: return path_smem_bytes_t<8>();
+    case 16: return path_smem_bytes_t<16>();
+    case 32: return path_smem_bytes_t<32>();
+    case 64: return path_smem_bytes_t<64>();
+    case 128: return path_smem_bytes_t<128>();
+    default: return 0;
+  }
 }
 
 template <int N, int FAR>

@@ -1,5 +1,5 @@
-// Rotation of the object for ptychographic tomography (Eq. rotation_transform) and its exact
-// transpose.  The plane perpendicular to the rotation axis (y) is the x-z plane; a rotated-frame
+// Transmission volume (Eq. ri_modulation), with the rotation of the object for ptychographic
+// tomography (Eq. rotation_transform) fused in, and the rotation's exact transpose.  The plane perpendicular to the rotation axis (y) is the x-z plane; a rotated-frame
 // voxel (z_t, y, x_t) samples the unrotated volume at
 //   x0 = c (x_t - cx) - s (z_t - cz) + cx,   z0 = s (x_t - cx) + c (z_t - cz) + cz
 // with bilinear weights; nodes outside the volume contribute nothing.  The transpose is computed
@@ -31,33 +31,46 @@ __device__ __forceinline__ Tap tap(int zt, int xt, int Lz, int Lx, float c, floa
   return t;
 }
 
-__global__ void k_rotate(const float* __restrict__ vd, const float* __restrict__ vb, float* __restrict__ rd,
-                         float* __restrict__ rb, int Lz, int Ly, int Lx, float c, float s) {
+// T = exp(-kdz beta) exp(i kdz delta) of the (optionally rotated) volume, Eq. ri_modulation.
+// Computed once per call so the fused kernel gathers a complex64 per voxel instead of
+// evaluating sincos/exp for every (position, slice, pixel) it touches.
+template <bool ROT>
+__global__ void k_transmission(const float* __restrict__ vd, const float* __restrict__ vb, float2* __restrict__ T,
+                               int Lz, int Ly, int Lx, float kdz, float c, float s) {
   const size_t n = (size_t)Lz * Ly * Lx;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const int xt = (int)(i % Lx);
-    const int y = (int)((i / Lx) % Ly);
-    const int zt = (int)(i / ((size_t)Lx * Ly));
-    const Tap t = tap(zt, xt, Lz, Lx, c, s);
-    float sd = 0.f, sb = 0.f;
+    float sd, sb;
+    if (ROT) {
+      const int xt = (int)(i % Lx);
+      const int y = (int)((i / Lx) % Ly);
+      const int zt = (int)(i / ((size_t)Lx * Ly));
+      const Tap t = tap(zt, xt, Lz, Lx, c, s);
+      sd = 0.f;
+      sb = 0.f;
 #pragma unroll
-    for (int dz = 0; dz < 2; ++dz) {
+      for (int dz = 0; dz < 2; ++dz) {
 #pragma unroll
-      for (int dx = 0; dx < 2; ++dx) {
-        const int z = t.fz + dz, x = t.fx + dx;
-        if (z < 0 || z >= Lz || x < 0 || x >= Lx) continue;
-        const float w = (dz ? t.az : 1.f - t.az) * (dx ? t.ax : 1.f - t.ax);
-        const size_t o = ((size_t)z * Ly + y) * Lx + x;
-        sd = fmaf(w, __ldg(vd + o), sd);
-        sb = fmaf(w, __ldg(vb + o), sb);
+        for (int dx = 0; dx < 2; ++dx) {
+          const int z = t.fz + dz, x = t.fx + dx;
+          if (z < 0 || z >= Lz || x < 0 || x >= Lx) continue;
+          const float w = (dz ? t.az : 1.f - t.az) * (dx ? t.ax : 1.f - t.ax);
+          const size_t o = ((size_t)z * Ly + y) * Lx + x;
+          sd = fmaf(w, __ldg(vd + o), sd);
+          sb = fmaf(w, __ldg(vb + o), sb);
+        }
       }
+    } else {
+      sd = __ldg(vd + i);
+      sb = __ldg(vb + i);
     }
-    rd[i] = sd;
-    rb[i] = sb;
+    float sn, cs;
+    sincosf(kdz * sd, &sn, &cs);
+    const float e = expf(-kdz * sb);
+    T[i] = make_float2(e * cs, e * sn);
   }
 }
 
-__global__ void k_rotate_T(const float* __restrict__ gdr, const float* __restrict__ gbr, float* __restrict__ gd,
+__global__ void k_rotate_adj(const float* __restrict__ gdr, const float* __restrict__ gbr, float* __restrict__ gd,
                            float* __restrict__ gb, int Lz, int Ly, int Lx, float c, float s) {
   const size_t n = (size_t)Lz * Ly * Lx;
   const float cx = 0.5f * (float)(Lx - 1), cz = 0.5f * (float)(Lz - 1);
@@ -92,19 +105,20 @@ __global__ void k_rotate_T(const float* __restrict__ gdr, const float* __restric
   }
 }
 
-cudaError_t launch_rotate(const float* vd, const float* vb, float* rd, float* rb, int Lz, int Ly, int Lx, float c,
-                          float sn, cudaStream_t s) {
+cudaError_t launch_transmission(const float* vd, const float* vb, float2* T, int Lz, int Ly, int Lx, float kdz,
+                                int rotate, float c, float sn, cudaStream_t s) {
   const size_t n = (size_t)Lz * Ly * Lx;
   const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
-  k_rotate<<<grid, 256, 0, s>>>(vd, vb, rd, rb, Lz, Ly, Lx, c, sn);
+  if (rotate) k_transmission<true><<<grid, 256, 0, s>>>(vd, vb, T, Lz, Ly, Lx, kdz, c, sn);
+  else k_transmission<false><<<grid, 256, 0, s>>>(vd, vb, T, Lz, Ly, Lx, kdz, c, sn);
   return cudaGetLastError();
 }
 
-cudaError_t launch_rotate_T(const float* gdr, const float* gbr, float* gd, float* gb, int Lz, int Ly, int Lx, float c,
-                            float sn, cudaStream_t s) {
+cudaError_t launch_rotate_adj(const float* gdr, const float* gbr, float* gd, float* gb, int Lz, int Ly, int Lx,
+                              float c, float sn, cudaStream_t s) {
   const size_t n = (size_t)Lz * Ly * Lx;
   const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
-  k_rotate_T<<<grid, 256, 0, s>>>(gdr, gbr, gd, gb, Lz, Ly, Lx, c, sn);
+  k_rotate_adj<<<grid, 256, 0, s>>>(gdr, gbr, gd, gb, Lz, Ly, Lx, c, sn);
   return cudaGetLastError();
 }
 

@@ -15,8 +15,7 @@ struct PathArgs {
   int n_dist;             // near field: number of sample-detector distances
   float eps, kdz;
   double inv_npix;        // 1 / (number of detector pixels in the batch)
-  const float* vd;        // delta [Lz][Ly][Lx] (rotated frame for tomography)
-  const float* vb;        // beta
+  const float2* T;        // transmission exp(i kdz (delta + i beta)) [Lz][Ly][Lx] (rotated frame for tomography)
   const float2* probe;    // near field: illumination [M][N][N]
   const float2* phat;     // far field: DFT_-[probe] [M][N][N]
   const float* pos;       // far field [B][2] (y, x); near field shifts [B][n_dist][2]
@@ -45,10 +44,13 @@ cudaError_t launch_path(const PathArgs& a, int farfield, cudaStream_t s);
 cudaError_t launch_probe_grad(int N, int M, int B, int farfield, const float2* qacc, float2* qsum, float2* g_probe,
                               const float2* tw, const double* lossp, double inv_npix, double* loss_out,
                               cudaStream_t s);
-cudaError_t launch_rotate(const float* vd, const float* vb, float* rd, float* rb, int Lz, int Ly, int Lx, float c,
-                          float sn, cudaStream_t s);
-cudaError_t launch_rotate_T(const float* gd_rot, const float* gb_rot, float* gd, float* gb, int Lz, int Ly, int Lx,
-                            float c, float sn, cudaStream_t s);
+// T = exp(-kdz beta) exp(i kdz delta) over a volume (Eq. ri_modulation), optionally after the
+// bilinear rotation of Eq. rotation_transform (rotate = 1)
+cudaError_t launch_transmission(const float* vd, const float* vb, float2* T, int Lz, int Ly, int Lx, float kdz,
+                                int rotate, float c, float sn, cudaStream_t s);
+// transpose of the rotation, added into gd/gb
+cudaError_t launch_rotate_adj(const float* gd_rot, const float* gb_rot, float* gd, float* gb, int Lz, int Ly, int Lx,
+                              float c, float sn, cudaStream_t s);
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s);
 int path_smem_bytes(int N);
 // set the dynamic shared-memory attributes of every kernel used for tile size N (call outside capture)

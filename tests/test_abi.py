@@ -43,8 +43,10 @@ def _problem(**kw):
 def test_workspace_planning_and_validation(lib):
     from paper_2012_12686_gb300.adorym import workspace_bytes, AdorymError
     ws = workspace_bytes(_problem())
-    # checkpoints (6) + segment (6) + park + far field + probe partials dominate: ~15 fields of 128 KB per position
-    assert 128 * 14 * 128 * 1024 < ws < 128 * 20 * 128 * 1024
+    # checkpoints (6) + segment (6) + park + far field + probe partials: ~15 fields of 128 KB per
+    # position, plus the complex64 transmission volume (512 x 512 x 32)
+    T = 512 * 512 * 32 * 8
+    assert T + 128 * 14 * 128 * 1024 < ws < T + 128 * 20 * 128 * 1024
     ws1 = workspace_bytes(_problem(checkpoint_every=1))
     assert ws1 > ws
     for bad in (dict(N=100), dict(N=256), dict(Lz=31), dict(B=0), dict(M=0), dict(loss=7), dict(eps=-1.0),
