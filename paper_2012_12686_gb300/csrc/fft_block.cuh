@@ -122,7 +122,7 @@ struct Geo;
 // The spatial passes (S4/S1, radix N1) carry the global-memory traffic of the pointwise ops, so
 // N1 is the smaller radix where the two differ.
 #ifndef ADORYM_NT128
-#define ADORYM_NT128 512
+#define ADORYM_NT128 1024
 #endif
 template <> struct Geo<8>   { static constexpr int N1 = 4, N2 = 2,  NT = 64,  MINB = 8; };
 template <> struct Geo<16>  { static constexpr int N1 = 4, N2 = 4,  NT = 64,  MINB = 8; };

@@ -518,16 +518,33 @@ __global__ void __launch_bounds__(Geo<N>::NT) k_probe_hat(const float2* __restri
 
 // ---------------------------------------------------------------------------- probe gradient
 // qsum[m][p] = sum_b qacc[b][m][p] in FP64, fixed order
-__global__ void k_qsum(const float2* __restrict__ qacc, float2* __restrict__ qsum, int B, size_t MNN) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= MNN) return;
+// Block of 256 threads = 32 consecutive elements x 8 batch chunks; each thread sums its chunk
+// in FP64, then the 8 partials of an element are added in chunk order (deterministic).
+__global__ void __launch_bounds__(256) k_qsum(const float2* __restrict__ qacc, float2* __restrict__ qsum, int B,
+                                              size_t MNN) {
+  __shared__ double2 part[8][32];
+  const int e = threadIdx.x & 31, c = threadIdx.x >> 5;
+  const size_t i = (size_t)blockIdx.x * 32 + e;
+  const int b0 = (B * c) / 8, b1 = (B * (c + 1)) / 8;
   double sr = 0.0, si = 0.0;
-  for (int b = 0; b < B; ++b) {
-    const float2 v = qacc[(size_t)b * MNN + i];
-    sr += v.x;
-    si += v.y;
+  if (i < MNN) {
+    for (int b = b0; b < b1; ++b) {
+      const float2 v = qacc[(size_t)b * MNN + i];
+      sr += v.x;
+      si += v.y;
+    }
   }
-  qsum[i] = make_float2((float)sr, (float)si);
+  part[c][e] = make_double2(sr, si);
+  __syncthreads();
+  if (c == 0 && i < MNN) {
+    double r = 0.0, im = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      r += part[k][e].x;
+      im += part[k][e].y;
+    }
+    qsum[i] = make_float2((float)r, (float)im);
+  }
 }
 
 // far field: g_probe[m] += IDFT_-{qsum[m]};  near field: g_probe[m] += qsum[m]
@@ -652,7 +669,7 @@ static cudaError_t launch_probe_grad_t(int M, int B, const float2* qacc, float2*
                                        const double* lossp, double inv_npix, double* loss_out, cudaStream_t s) {
   const size_t MNN = (size_t)M * N * N;
   if (g) {
-    k_qsum<<<(unsigned)((MNN + 255) / 256), 256, 0, s>>>(qacc, qsum, B, MNN);
+    k_qsum<<<(unsigned)((MNN + 31) / 32), 256, 0, s>>>(qacc, qsum, B, MNN);
   }
   const int smem = (N * (N + 1) + N) * (int)sizeof(float2);
   static bool attr = false;
