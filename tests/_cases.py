@@ -72,8 +72,64 @@ def measured(case, seed=99):
 
 def _oracle_chunk(args):
     import oracle
-    problem, d, b, probe, pos, Im = args
+    kind, problem, d, b, probe, pos, Im = args
+    if kind == "forward":
+        return oracle.forward(problem, d, b, probe, pos)
     return oracle.loss_grad(problem, d, b, probe, pos, Im)
+
+
+def _chunks(case, workers):
+    """Split a batch into per-worker sub-problems.  Far field: positions (whole object each).
+    Near field: problems, each chunk with its own slab of the volume."""
+    p = dict(case["problem"])
+    B = p["B"]
+    idx = np.array_split(np.arange(B), min(workers, B))
+    out = []
+    for c in idx:
+        q = dict(p, B=len(c))
+        if p["farfield"]:
+            out.append((q, case["delta"], case["beta"], case["pos"][c], c))
+        else:
+            L = p["L"]
+            q["Lz"] = len(c) * L
+            sl = slice(c[0] * L, (c[-1] + 1) * L)
+            out.append((q, case["delta"][sl], case["beta"][sl], case["pos"][c], c))
+    return out
+
+
+def _pool_map(jobs):
+    """Spawn pool of single-threaded workers (one BLAS thread each, so they do not oversubscribe)."""
+    import os
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(len(jobs)) as pool:
+            return pool.map(_oracle_chunk, jobs)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def oracle_forward(case, which="", workers=1):
+    """Oracle intensities of the case's object (which="") or of its second object (which="_meas")."""
+    import oracle
+    d, b = case["delta" + which], case["beta" + which]
+    if workers <= 1 or case["problem"]["B"] < 2:
+        return oracle.forward(case["problem"], d, b, case["probe"], case["pos"])
+    c2 = dict(case, delta=d, beta=b)
+    ch = _chunks(c2, workers)
+    res = _pool_map([("forward", q, dd, bb, case["probe"], pp, None) for q, dd, bb, pp, _ in ch])
+    return np.concatenate(res, 0)
+
+
+def measured_par(case, workers, seed=99):
+    return synth.poisson(oracle_forward(case, "_meas", workers), seed, case.get("photons", 1.0))
 
 
 def oracle_loss_grad(case, I_meas, workers=1):
@@ -84,22 +140,18 @@ def oracle_loss_grad(case, I_meas, workers=1):
     B = p["B"]
     if workers <= 1 or B < 2:
         return oracle.loss_grad(p, case["delta"], case["beta"], case["probe"], case["pos"], I_meas)
-    chunks = np.array_split(np.arange(B), min(workers, B))
-    jobs = []
-    for c in chunks:
-        q = dict(p, B=len(c))
-        if not p["farfield"]:
-            raise ValueError("parallel oracle supports the far-field geometry")
-        jobs.append((q, case["delta"], case["beta"], case["probe"], case["pos"][c], I_meas[c]))
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(len(jobs)) as pool:
-        res = pool.map(_oracle_chunk, jobs)
-    w = [len(c) / B for c in chunks]
+    ch = _chunks(case, workers)
+    res = _pool_map([("loss_grad", q, dd, bb, case["probe"], pp, I_meas[c]) for q, dd, bb, pp, c in ch])
+    w = [len(c) / B for *_, c in ch]
     L = sum(wi * r[0] for wi, r in zip(w, res))
-    gd = sum(wi * r[1] for wi, r in zip(w, res))
-    gb = sum(wi * r[2] for wi, r in zip(w, res))
     gp = sum(wi * r[3] for wi, r in zip(w, res))
     gpos = np.concatenate([wi * r[4] for wi, r in zip(w, res)], 0)
+    if p["farfield"]:
+        gd = sum(wi * r[1] for wi, r in zip(w, res))
+        gb = sum(wi * r[2] for wi, r in zip(w, res))
+    else:   # disjoint slabs
+        gd = np.concatenate([wi * r[1] for wi, r in zip(w, res)], 0)
+        gb = np.concatenate([wi * r[2] for wi, r in zip(w, res)], 0)
     return L, gd, gb, gp, gpos
 
 

@@ -76,3 +76,40 @@ def test_only_some_gradients_and_determinism():
     # no atomics on the probe / loss path: bitwise reproducible
     assert r1["loss"] == r2["loss"]
     np.testing.assert_array_equal(r1["gp"], r2["gp"])
+
+
+def _full(name, **over):
+    """A workload at its full size, oracle on every CPU core (spawn pool)."""
+    import os
+    from paper_2012_12686_gb300 import synth
+    import oracle
+    w = synth.workload(name, seed=0, **over)
+    workers = os.cpu_count() or 1
+    Im = C.measured_par(w, workers)
+    I_ref = C.oracle_forward(w, "", workers)
+    ref = C.oracle_loss_grad(w, Im, workers)
+    r = C.cuda_run(w, Im)
+    errs = {"I": C.rel(r["I"], I_ref), "loss": abs(r["loss"] - ref[0]) / abs(ref[0]),
+            "gd": C.rel(r["gd"], ref[1]), "gb": C.rel(r["gb"], ref[2]), "gp": C.rel(r["gp"], ref[3]),
+            "gpos": C.rel(r["gpos"], ref[4])}
+    assert errs["I"] <= C.TOL_I and errs["loss"] <= C.TOL_I, errs
+    assert max(errs["gd"], errs["gb"], errs["gp"], errs["gpos"]) <= C.TOL_G, errs
+    return errs
+
+
+def test_multislice_full_workload():
+    """512x512x32 object, 128x128 probe, one minibatch of 128 positions, 32 slices, Poisson --
+    the benchmark's own launch configuration, every output compared with the FP64 oracle."""
+    _full("multislice")
+
+
+def test_tomo_full_workload():
+    """128^3 volume rotated by 30 degrees, 8x8 positions (patches leave the volume), N = 64,
+    128 slices, LSQ; gradients through the rotation's transpose."""
+    _full("tomo")
+
+
+def test_multimode_probe():
+    """Five incoherent probe modes (the paper's fly-scan / ptychotomography setting)."""
+    case = C.small_case(N=64, L=6, M=5, B=6, loss="lsq", seed=31)
+    _compare(case)
