@@ -11,6 +11,7 @@ namespace adorym {
 static const double kPi = 3.14159265358979323846;
 
 static bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+bool two_pass(int N) { return N >= 256; }
 
 int validate(const adorym_problem& p, const char** err) {
   auto bad = [&](const char* m) {
@@ -25,12 +26,12 @@ int validate(const adorym_problem& p, const char** err) {
   if (!std::isfinite(p.kdz) || !std::isfinite(p.lambda_dz_over_px2)) return bad("kdz / lambda_dz_over_px2 not finite");
   if (p.checkpoint_every < 0 || p.checkpoint_every > p.L) return bad("checkpoint_every must be in 0..L");
   if (p.farfield) {
-    if (!pow2_in(p.N, 8, 128)) return bad("far field: N must be a power of two in 8..128");
+    if (!pow2_in(p.N, 8, 1024)) return bad("far field: N must be a power of two in 8..1024");
     if (p.Lz != p.L) return bad("far field: Lz must equal L (the wave crosses every slice)");
     if (p.Ly < 1 || p.Lx < 1) return bad("object dims must be >= 1");
     if (p.tomo && !std::isfinite(p.theta)) return bad("theta not finite");
   } else {
-    if (!pow2_in(p.N, 8, 128)) return bad("near field: N must be a power of two in 8..128");
+    if (!pow2_in(p.N, 8, 1024)) return bad("near field: N must be a power of two in 8..1024");
     if (p.tomo) return bad("tomography is defined for the far-field geometry only");
     if (p.Ly != p.N || p.Lx != p.N) return bad("near field: Ly == Lx == N (full-field tiles)");
     if ((long long)p.Lz != (long long)p.B * p.L) return bad("near field: Lz must equal B * L");
@@ -68,17 +69,33 @@ int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan
     return r;
   };
   q.off_phat = take(M * NN * f2);
-  if (adj) {
-    q.off_ckpt = take(B * M * q.ncp * NN * f2);
-    q.off_seg = take(B * M * q.cp * NN * f2);
-    q.off_park = take(B * N * (N + 1) * f2);
-    if (!q.far) q.off_fbar = take(B * NN * f2);
-    q.off_qacc = take(B * M * NN * f2);
-    q.off_qsum = take(M * NN * f2);
+  if (two_pass(p.N)) {
+    q.off_FA = take(B * M * NN * f2);
+    if (adj) {
+      q.off_FR = take(B * M * NN * f2);
+      q.off_ckpt = take(B * M * q.ncp * NN * f2);
+      q.off_seg = take(B * M * q.cp * NN * f2);
+      q.off_qacc = take(B * M * NN * f2);
+      q.off_qsum = take(M * NN * f2);
+      q.off_posp = take(B * q.nd * (N / (N == 256 ? 64 : N == 512 ? 32 : 16)) * 2 * sizeof(double));
+    }
+    q.off_tmp = take(M * NN * f2);
+    q.off_far = take(B * (q.far ? 1 : q.nd + 1) * M * NN * f2);
+    q.off_gI = take(B * q.nd * NN * sizeof(float));
+    q.off_lossp = take(B * q.nd * (NN / 1024) * sizeof(double));
+  } else {
+    if (adj) {
+      q.off_ckpt = take(B * M * q.ncp * NN * f2);
+      q.off_seg = take(B * M * q.cp * NN * f2);
+      q.off_park = take(B * N * (N + 1) * f2);
+      if (!q.far) q.off_fbar = take(B * NN * f2);
+      q.off_qacc = take(B * M * NN * f2);
+      q.off_qsum = take(M * NN * f2);
+    }
+    q.off_far = take(B * (q.far ? 1 : q.nd + 1) * M * NN * f2);
+    q.off_gI = take(B * q.nd * NN * sizeof(float));
+    q.off_lossp = take(B * sizeof(double));
   }
-  q.off_far = take(B * (q.far ? 1 : q.nd + 1) * M * NN * f2);
-  q.off_gI = take(B * q.nd * NN * sizeof(float));
-  q.off_lossp = take(B * sizeof(double));
   q.off_loss = take(sizeof(double));
   {
     const size_t V = (size_t)p.Lz * p.Ly * p.Lx;
@@ -186,55 +203,104 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
     gb = grot + V;
   }
   float2* phat = reinterpret_cast<float2*>(W(pl.off_phat));
-  if (pl.far) {
-    if ((rc = chk(launch_probe_hat(p.N, p.M, c.probe, phat, tab.tw(), s), "probe_hat"))) return rc;
-  }
-  PathArgs a{};
-  a.N = p.N;
-  a.L = p.L;
-  a.M = p.M;
-  a.B = p.B;
-  a.Ly = p.Ly;
-  a.Lx = p.Lx;
-  a.cp = pl.cp;
-  a.ncp = pl.ncp;
-  a.loss = p.loss;
-  a.adj = pl.adj ? 1 : 0;
-  a.n_dist = pl.nd;
-  a.eps = (float)p.eps;
-  a.kdz = (float)p.kdz;
-  a.inv_npix = 1.0 / ((double)p.B * pl.nd * (double)pl.NN);
-  a.T = T;
-  a.probe = c.probe;
-  a.phat = phat;
-  a.pos = c.pos;
-  a.I_meas = c.I_meas;
-  a.I_out = c.I_out;
-  a.tw = tab.tw();
-  a.hy = tab.hy();
-  a.hx = tab.hx();
-  a.hd = pl.far ? nullptr : tab.hd();
-  if (pl.adj) {
-    a.ckpt = reinterpret_cast<float2*>(W(pl.off_ckpt));
-    a.seg = reinterpret_cast<float2*>(W(pl.off_seg));
-    a.park = reinterpret_cast<float2*>(W(pl.off_park));
-    a.fbar = pl.far ? nullptr : reinterpret_cast<float2*>(W(pl.off_fbar));
-    a.qacc = pl.want_probe ? reinterpret_cast<float2*>(W(pl.off_qacc)) : nullptr;
-    a.gd = pl.want_obj ? gd : nullptr;
-    a.gb = pl.want_obj ? gb : nullptr;
-    a.gpos = pl.want_pos ? c.g_pos : nullptr;
-  }
-  a.far = reinterpret_cast<float2*>(W(pl.off_far));
-  a.gI = reinterpret_cast<float*>(W(pl.off_gI));
-  a.lossp = reinterpret_cast<double*>(W(pl.off_lossp));
-  if (ev_start) cudaEventRecord(ev_start, s);
-  if ((rc = chk(launch_path(a, pl.far ? 1 : 0, s), "path"))) return rc;
-  if (ev_stop) cudaEventRecord(ev_stop, s);
-  if (pl.adj && (pl.want_probe || c.loss)) {
-    if ((rc = chk(launch_probe_grad(p.N, p.M, p.B, pl.far ? 1 : 0, a.qacc, reinterpret_cast<float2*>(W(pl.off_qsum)),
-                                    pl.want_probe ? c.g_probe : nullptr, tab.tw(), a.lossp, a.inv_npix, c.loss, s),
-                  "probe_grad")))
-      return rc;
+  if (two_pass(p.N)) {
+    TPArgs t{};
+    t.N = p.N;
+    t.L = p.L;
+    t.M = p.M;
+    t.B = p.B;
+    t.Ly = p.Ly;
+    t.Lx = p.Lx;
+    t.cp = pl.cp;
+    t.ncp = pl.ncp;
+    t.nd = pl.nd;
+    t.loss = p.loss;
+    t.farfield = pl.far ? 1 : 0;
+    t.adj = pl.adj ? 1 : 0;
+    t.eps = (float)p.eps;
+    t.kdz = (float)p.kdz;
+    t.inv_npix = 1.0 / ((double)p.B * pl.nd * (double)pl.NN);
+    t.T = T;
+    t.probe = c.probe;
+    t.phat = phat;
+    t.phat_w = phat;
+    t.pos = c.pos;
+    t.I_meas = c.I_meas;
+    t.I_out = c.I_out;
+    t.tw = tab.tw();
+    t.hy = tab.hy();
+    t.hx = tab.hx();
+    t.hd = pl.far ? nullptr : tab.hd();
+    t.FA = reinterpret_cast<float2*>(W(pl.off_FA));
+    t.far = reinterpret_cast<float2*>(W(pl.off_far));
+    t.gI = reinterpret_cast<float*>(W(pl.off_gI));
+    t.lossp = reinterpret_cast<double*>(W(pl.off_lossp));
+    t.tmp = reinterpret_cast<float2*>(W(pl.off_tmp));
+    if (pl.adj) {
+      t.FR = reinterpret_cast<float2*>(W(pl.off_FR));
+      t.ckpt = reinterpret_cast<float2*>(W(pl.off_ckpt));
+      t.seg = reinterpret_cast<float2*>(W(pl.off_seg));
+      t.qacc = pl.want_probe ? reinterpret_cast<float2*>(W(pl.off_qacc)) : nullptr;
+      t.qsum = reinterpret_cast<float2*>(W(pl.off_qsum));
+      t.posp = pl.want_pos ? reinterpret_cast<double*>(W(pl.off_posp)) : nullptr;
+      t.gd = pl.want_obj ? gd : nullptr;
+      t.gb = pl.want_obj ? gb : nullptr;
+      t.gpos = pl.want_pos ? c.g_pos : nullptr;
+      t.g_probe = pl.want_probe ? c.g_probe : nullptr;
+      t.loss_out = c.loss;
+    }
+    if ((rc = chk(launch_twopass(t, s, ev_start, ev_stop), "two-pass"))) return rc;
+  } else {
+    if (pl.far) {
+      if ((rc = chk(launch_probe_hat(p.N, p.M, c.probe, phat, tab.tw(), s), "probe_hat"))) return rc;
+    }
+    PathArgs a{};
+    a.N = p.N;
+    a.L = p.L;
+    a.M = p.M;
+    a.B = p.B;
+    a.Ly = p.Ly;
+    a.Lx = p.Lx;
+    a.cp = pl.cp;
+    a.ncp = pl.ncp;
+    a.loss = p.loss;
+    a.adj = pl.adj ? 1 : 0;
+    a.n_dist = pl.nd;
+    a.eps = (float)p.eps;
+    a.kdz = (float)p.kdz;
+    a.inv_npix = 1.0 / ((double)p.B * pl.nd * (double)pl.NN);
+    a.T = T;
+    a.probe = c.probe;
+    a.phat = phat;
+    a.pos = c.pos;
+    a.I_meas = c.I_meas;
+    a.I_out = c.I_out;
+    a.tw = tab.tw();
+    a.hy = tab.hy();
+    a.hx = tab.hx();
+    a.hd = pl.far ? nullptr : tab.hd();
+    if (pl.adj) {
+      a.ckpt = reinterpret_cast<float2*>(W(pl.off_ckpt));
+      a.seg = reinterpret_cast<float2*>(W(pl.off_seg));
+      a.park = reinterpret_cast<float2*>(W(pl.off_park));
+      a.fbar = pl.far ? nullptr : reinterpret_cast<float2*>(W(pl.off_fbar));
+      a.qacc = pl.want_probe ? reinterpret_cast<float2*>(W(pl.off_qacc)) : nullptr;
+      a.gd = pl.want_obj ? gd : nullptr;
+      a.gb = pl.want_obj ? gb : nullptr;
+      a.gpos = pl.want_pos ? c.g_pos : nullptr;
+    }
+    a.far = reinterpret_cast<float2*>(W(pl.off_far));
+    a.gI = reinterpret_cast<float*>(W(pl.off_gI));
+    a.lossp = reinterpret_cast<double*>(W(pl.off_lossp));
+    if (ev_start) cudaEventRecord(ev_start, s);
+    if ((rc = chk(launch_path(a, pl.far ? 1 : 0, s), "path"))) return rc;
+    if (ev_stop) cudaEventRecord(ev_stop, s);
+    if (pl.adj && (pl.want_probe || c.loss)) {
+      if ((rc = chk(launch_probe_grad(p.N, p.M, p.B, pl.far ? 1 : 0, a.qacc, reinterpret_cast<float2*>(W(pl.off_qsum)),
+                                      pl.want_probe ? c.g_probe : nullptr, tab.tw(), a.lossp, a.inv_npix, c.loss, s),
+                    "probe_grad")))
+        return rc;
+    }
   }
   if (pl.tomo && pl.want_obj) {
     if ((rc = chk(launch_rotate_adj(gd, gb, c.gd, c.gb, p.Lz, p.Ly, p.Lx, (float)cth, (float)sth, s), "rotate_adj")))
@@ -244,7 +310,7 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
 }
 
 int prepare_kernels(const adorym_problem& p, const char** err) {
-  cudaError_t e = prepare_path(p.N, p.farfield ? 1 : 0);
+  cudaError_t e = two_pass(p.N) ? prepare_twopass(p.N) : prepare_path(p.N, p.farfield ? 1 : 0);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *err = "kernel attributes could not be set";

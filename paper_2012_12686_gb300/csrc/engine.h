@@ -32,6 +32,8 @@ struct Plan {
   size_t NN = 0;
   size_t off_phat = 0, off_ckpt = 0, off_seg = 0, off_park = 0, off_far = 0, off_gI = 0, off_fbar = 0,
          off_lossp = 0, off_qacc = 0, off_qsum = 0, off_T = 0, off_grot = 0, off_loss = 0;
+  // two-pass path (N >= 256)
+  size_t off_FA = 0, off_FR = 0, off_tmp = 0, off_posp = 0;
   // staging for host-memory arguments
   size_t off_s_probe = 0, off_s_pos = 0, off_s_meas = 0, off_s_gprobe = 0, off_s_gpos = 0, off_s_iout = 0;
   size_t bytes_probe = 0, bytes_pos = 0, bytes_meas = 0, bytes_iout = 0;
@@ -52,6 +54,7 @@ struct CallPtrs {
 };
 
 int validate(const adorym_problem& p, const char** err);
+bool two_pass(int N);   // N >= 256: fields in HBM, row/column kernels per slice step
 int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan* plan, const char** err);
 // FP64-built tables (twiddles, propagator factors) of a problem: table_count(p) float2 values
 size_t table_count(const adorym_problem& p);

@@ -45,19 +45,18 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 
-// cos / sin of 2 pi k / 16, k = 0..15 (exact values rounded to float)
-struct Unit16 {
-  static constexpr float c[16] = {1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
-                                  0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
-                                  -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
-                                  0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f};
-  static constexpr float s[16] = {0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f,
-                                  1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
-                                  0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
-                                  -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f};
+// cos / sin of 2 pi q / 32 from the first-octant values cos(2 pi j / 32), j = 0..8, by symmetry
+struct Unit32 {
+  static constexpr double base[9] = {1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708,
+                                     0.70710678118654752440, 0.55557023301960222474, 0.38268343236508977173,
+                                     0.19509032201612826785, 0.0};
+  static constexpr double cosq(int q) {   // q in [0, 32)
+    return q <= 8 ? base[q] : q <= 16 ? -base[16 - q] : q <= 24 ? -base[q - 16] : base[32 - q];
+  }
+  static constexpr double sinq(int q) { return cosq((q + 24) % 32); }   // sin x = cos(x - pi/2)
 };
 
-// a * exp(S * 2 pi i K / R), K, R compile-time, R | 16
+// a * exp(S * 2 pi i K / R), K, R compile-time, R | 32
 template <int R, int K, int S>
 __device__ __forceinline__ float2 rot_const(float2 a) {
   constexpr int k = K % R;
@@ -70,9 +69,9 @@ __device__ __forceinline__ float2 rot_const(float2 a) {
   } else if constexpr (4 * k == 3 * R) {  // exp(S i 3pi/2) = -S i
     return S > 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
   } else {
-    constexpr int q = k * (16 / R);
-    constexpr float c = Unit16::c[q];
-    constexpr float s = S > 0 ? Unit16::s[q] : -Unit16::s[q];
+    constexpr int q = k * (32 / R);
+    constexpr float c = (float)Unit32::cosq(q);
+    constexpr float s = S > 0 ? (float)Unit32::sinq(q) : -(float)Unit32::sinq(q);
     return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
   }
 }
@@ -83,7 +82,7 @@ __device__ __forceinline__ void butterflies(float2 (&v)[R], const float2 (&e)[R 
   ((v[K] = cadd(e[K], rot_const<R, K, S>(o[K])), v[K + R / 2] = csub(e[K], rot_const<R, K, S>(o[K]))), ...);
 }
 
-// In-register DFT of size R (1, 2, 4, 8, 16): v[k] <- sum_n v[n] exp(S 2 pi i n k / R)
+// In-register DFT of size R (1, 2, 4, 8, 16, 32): v[k] <- sum_n v[n] exp(S 2 pi i n k / R)
 template <int R, int S>
 __device__ __forceinline__ void dft(float2 (&v)[R]) {
   if constexpr (R == 1) {

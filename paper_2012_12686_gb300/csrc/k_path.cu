@@ -547,6 +547,11 @@ __global__ void __launch_bounds__(256) k_qsum(const float2* __restrict__ qacc, f
   }
 }
 
+cudaError_t launch_qsum(const float2* qacc, float2* qsum, int B, size_t MNN, cudaStream_t s) {
+  k_qsum<<<(unsigned)((MNN + 31) / 32), 256, 0, s>>>(qacc, qsum, B, MNN);
+  return cudaGetLastError();
+}
+
 // far field: g_probe[m] += IDFT_-{qsum[m]};  near field: g_probe[m] += qsum[m]
 template <int N, int FAR>
 __global__ void __launch_bounds__(Geo<N>::NT) k_probe_grad(const float2* __restrict__ qsum, float2* __restrict__ g,

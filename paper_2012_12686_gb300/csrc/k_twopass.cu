@@ -1,0 +1,711 @@
+// Two-pass path for tiles of 256, 512 and 1024 pixels: the wavefields live in HBM and each
+// propagation step is one row kernel and one column kernel.
+//
+// A 1-D transform of length N = N1 * N2 uses the same two in-place stages as the shared-memory
+// kernel (S1/S2 forward, S3/S4 inverse side, see fft_block.cuh), so a field in global memory is
+// always in natural order: spatial (y, x), or "x-transformed" (y, kx) between a row kernel and
+// a column kernel.
+//
+//   row kernel  (RB rows per CTA):   [S3 S4 from global]  -> spatial op ->  [S1 S2 to global]
+//   column kernel (CW columns/CTA):  [S1 S2 from global]  -> frequency op -> [S3 S4 to global]
+//
+// so one slice step (modulation by T_j, Eq. ri_modulation; Fresnel step, Eq. fresnel_prop)
+// is: row kernel (finish the previous inverse x-transform, store/modulate, start the forward
+// x-transform) + column kernel (forward y-transform, propagator, inverse y-transform).  The
+// row tile uses a skewed shared-memory layout (one pad element after every N2 elements), which
+// keeps both the strided and the contiguous stage accesses free of bank conflicts with the
+// lane index on the x digit, so every global access is coalesced.  Loss and position-gradient
+// reductions write per-CTA FP64 partials that a final kernel adds in a fixed order.
+#include "fft_block.cuh"
+#include "kernels.cuh"
+
+namespace adorym {
+
+template <int N>
+struct Geo2;
+template <> struct Geo2<256>  { static constexpr int N1 = 16, N2 = 16, RB = 32, CW = 64; };
+template <> struct Geo2<512>  { static constexpr int N1 = 16, N2 = 32, RB = 32, CW = 32; };
+template <> struct Geo2<1024> { static constexpr int N1 = 32, N2 = 32, RB = 16, CW = 16; };
+constexpr int NT2 = 512;
+
+template <int N>
+constexpr int row_smem_bytes() {
+  return Geo2<N>::RB * (N + Geo2<N>::N1) * (int)sizeof(float2) + N * (int)sizeof(float2) + 64 * 8;
+}
+template <int N>
+constexpr int col_smem_bytes() {
+  return N * Geo2<N>::CW * (int)sizeof(float2) + 3 * N * (int)sizeof(float2) + 64 * 8;
+}
+
+enum RowMode { R_FWD, R_RC_FIRST, R_RC, R_ADJ, R_NEAR_DET, R_NEAR_SEED, R_PHAT, R_PG_OUT };
+enum ColMode { C_PROP, C_PROP_ADJ, C_PSI0, C_FAR, C_SEED, C_Q, C_PHAT, C_PG, C_NEAR_PHI, C_NEAR_Q };
+
+__device__ __forceinline__ float freqf(int k, int N) { return (float)(k <= (N - 1) / 2 ? k : k - N) / (float)N; }
+__device__ __forceinline__ double freq2(int k, int N) { return (double)(k <= (N - 1) / 2 ? k : k - N) / (double)N; }
+
+__device__ __forceinline__ float2 ramp1(double d, int k, int N) {
+  double s, c;
+  sincospi(-2.0 * d * freq2(k, N), &s, &c);
+  return make_float2((float)c, (float)s);
+}
+
+__device__ __forceinline__ double block_sum2(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+
+// ============================================================================ row kernel
+template <int N, int MODE>
+__global__ void __launch_bounds__(NT2) k_row(const TPArgs a) {
+  constexpr int N1 = Geo2<N>::N1, N2 = Geo2<N>::N2, RB = Geo2<N>::RB, LDR = N + N1;
+  constexpr size_t NN = (size_t)N * N;
+  extern __shared__ float2 sm[];
+  float2* A = sm;
+  float2* tw = A + RB * LDR;
+  auto idx = [](int r, int p) { return r * LDR + p + p / N2; };
+  for (int i = threadIdx.x; i < N; i += NT2) tw[i] = a.tw[i];
+
+  const int r0 = blockIdx.x * RB;
+  const int f = blockIdx.y;                         // position / problem b (or probe mode m)
+  const bool FAR = a.farfield != 0;
+  const int b = f, m = a.m, j = a.j;
+  // input / output fields and stage configuration
+  const float2* src = nullptr;
+  float2* dst = nullptr;
+  bool in_freq = true;     // S3/S4 from global (else natural spatial from global)
+  int out = 1;             // 1: S1/S2 to global (x-transformed), 2: natural to global, 0: none
+  int si = +1, so = -1;    // signs of the inverse-side (in) and forward (out) transforms
+  const size_t fo = ((size_t)b * a.M + m) * NN;
+  if (MODE == R_FWD) {
+    src = (!FAR && j == 0) ? a.probe + (size_t)m * NN : a.FA + fo;
+    in_freq = !((!FAR) && j == 0);
+    dst = a.FA + fo;
+    so = (FAR && j == a.L - 1) ? +1 : -1;
+  } else if (MODE == R_RC_FIRST) {
+    src = a.ckpt + (((size_t)b * a.M + m) * a.ncp + a.s) * NN;
+    in_freq = false;
+    dst = a.FR + fo;
+  } else if (MODE == R_RC) {
+    src = a.FR + fo;
+    dst = a.FR + fo;
+    out = (j < a.j1) ? 1 : 0;
+  } else if (MODE == R_ADJ) {
+    src = a.FA + fo;
+    dst = a.FA + fo;
+    si = (FAR && j == a.L - 1) ? -1 : +1;
+    out = (!FAR && j == 0) ? 0 : 1;
+  } else if (MODE == R_NEAR_DET || MODE == R_NEAR_SEED) {
+    const size_t fd = (((size_t)b * (a.nd + 1) + a.d) * a.M + m) * NN;
+    src = a.far + fd;
+    dst = a.far + fd;
+    in_freq = (MODE == R_NEAR_DET);
+    out = (MODE == R_NEAR_DET) ? 2 : 1;
+  } else if (MODE == R_PHAT) {
+    src = a.probe + (size_t)f * NN;
+    dst = a.tmp + (size_t)f * NN;
+    in_freq = false;
+  } else if (MODE == R_PG_OUT) {
+    src = a.tmp + (size_t)f * NN;
+    out = 0;
+  }
+  __syncthreads();
+
+  // ---- stage IN: S3 from global (natural kx = t + N1 i)
+  if (in_freq) {
+    for (int tau = threadIdx.x; tau < RB * N1; tau += NT2) {
+      const int t = tau % N1, r = tau / N1;
+      const float2* row = src + (size_t)(r0 + r) * N;
+      float2 v[N2];
+#pragma unroll
+      for (int i = 0; i < N2; ++i) v[i] = row[t + N1 * i];
+      if (si < 0) { dft<N2, -1>(v); twiddle<-1>(v, tw, t); }
+      else { dft<N2, +1>(v); twiddle<+1>(v, tw, t); }
+#pragma unroll
+      for (int k = 0; k < N2; ++k) A[idx(r, N2 * t + k)] = v[k];
+    }
+    __syncthreads();
+  }
+  // ---- stage MID: S4 -> natural x = N2 k + t -> op -> S1
+  for (int tau = threadIdx.x; tau < RB * N2; tau += NT2) {
+    const int t = tau % N2, r = tau / N2;
+    const int y = r0 + r;
+    float2 v[N1];
+    if (in_freq) {
+#pragma unroll
+      for (int k = 0; k < N1; ++k) v[k] = A[idx(r, N2 * k + t)];
+      if (si < 0) dft<N1, -1>(v);
+      else dft<N1, +1>(v);
+    } else {
+#pragma unroll
+      for (int k = 0; k < N1; ++k) v[k] = src[(size_t)y * N + N2 * k + t];
+    }
+    // spatial ops; x = N2 k + t
+    if (MODE == R_FWD || MODE == R_RC_FIRST || MODE == R_RC || MODE == R_ADJ) {
+      int p0y = 0, p0x = 0, gz = FAR ? j : b * a.L + j;
+      if (FAR) {
+        p0y = (int)floor((double)a.pos[2 * b] + 0.5);
+        p0x = (int)floor((double)a.pos[2 * b + 1] + 0.5);
+      }
+      const int gy = p0y + y;
+      const bool row_in = gy >= 0 && gy < a.Ly;
+      float2* ck = a.ckpt + ((size_t)b * a.M + m) * a.ncp * NN;
+      float2* sg = a.seg + ((size_t)b * a.M + m) * a.cp * NN;
+#pragma unroll
+      for (int k = 0; k < N1; ++k) {
+        const int x = N2 * k + t, gx = p0x + x;
+        const bool inb = row_in && gx >= 0 && gx < a.Lx;
+        const size_t o = ((size_t)gz * a.Ly + gy) * a.Lx + gx;
+        const float2 T = inb ? __ldg(a.T + o) : make_float2(1.f, 0.f);
+        const size_t px = (size_t)y * N + x;
+        if (MODE == R_FWD) {
+          if (a.adj) {
+            if (j % a.cp == 0) ck[(size_t)(j / a.cp) * NN + px] = v[k];
+            else if (j > (a.ncp - 1) * a.cp) sg[(size_t)(j - (a.ncp - 1) * a.cp) * NN + px] = v[k];
+          }
+          v[k] = cmul(v[k], T);
+        } else if (MODE == R_RC_FIRST) {
+          v[k] = cmul(v[k], T);
+        } else if (MODE == R_RC) {
+          sg[(size_t)(j - a.j0) * NN + px] = v[k];
+          v[k] = cmul(v[k], T);
+        } else {   // R_ADJ
+          const float2 psi = (j == a.j0) ? ck[(size_t)a.s * NN + px] : sg[(size_t)(j - a.j0) * NN + px];
+          const float2 pbar = cmulc(v[k], T);
+          if (a.gd && inb) {
+            const float2 z = cmulc(pbar, psi);
+            atomicAdd(a.gd + o, a.kdz * z.y);
+            atomicAdd(a.gb + o, -a.kdz * z.x);
+          }
+          v[k] = pbar;
+          if (!FAR && j == 0 && a.qacc) a.qacc[fo + px] = pbar;
+        }
+      }
+    } else if (MODE == R_NEAR_DET) {
+      float* g = a.gI + ((size_t)b * a.nd + a.d) * NN;
+#pragma unroll
+      for (int k = 0; k < N1; ++k) {
+        const size_t px = (size_t)y * N + N2 * k + t;
+        const float I = fmaf(v[k].x, v[k].x, v[k].y * v[k].y);
+        g[px] = (m == 0) ? I : g[px] + I;
+      }
+    } else if (MODE == R_NEAR_SEED) {
+      const float* g = a.gI + ((size_t)b * a.nd + a.d) * NN;
+#pragma unroll
+      for (int k = 0; k < N1; ++k) v[k] = cscale(v[k], 2.0f * g[(size_t)y * N + N2 * k + t]);
+    } else if (MODE == R_PG_OUT) {
+      float2* g = a.g_probe + (size_t)f * NN;
+#pragma unroll
+      for (int k = 0; k < N1; ++k) {
+        const size_t px = (size_t)y * N + N2 * k + t;
+        g[px] = cadd(g[px], v[k]);
+      }
+    }
+    if (out == 1) {
+      if (so < 0) { dft<N1, -1>(v); twiddle<-1>(v, tw, t); }
+      else { dft<N1, +1>(v); twiddle<+1>(v, tw, t); }
+#pragma unroll
+      for (int k = 0; k < N1; ++k) A[idx(r, N2 * k + t)] = v[k];
+    } else if (out == 2) {
+#pragma unroll
+      for (int k = 0; k < N1; ++k) dst[(size_t)y * N + N2 * k + t] = v[k];
+    }
+  }
+  if (out != 1) return;
+  __syncthreads();
+  // ---- stage OUT: S2 to global (natural kx = t + N1 i)
+  for (int tau = threadIdx.x; tau < RB * N1; tau += NT2) {
+    const int t = tau % N1, r = tau / N1;
+    float2 v[N2];
+#pragma unroll
+    for (int i = 0; i < N2; ++i) v[i] = A[idx(r, N2 * t + i)];
+    if (so < 0) dft<N2, -1>(v);
+    else dft<N2, +1>(v);
+    float2* row = dst + (size_t)(r0 + r) * N;
+#pragma unroll
+    for (int i = 0; i < N2; ++i) row[t + N1 * i] = v[i];
+  }
+}
+
+// ============================================================================ column kernel
+template <int N, int MODE>
+__global__ void __launch_bounds__(NT2) k_col(const TPArgs a) {
+  constexpr int N1 = Geo2<N>::N1, N2 = Geo2<N>::N2, CW = Geo2<N>::CW;
+  constexpr size_t NN = (size_t)N * N;
+  extern __shared__ float2 sm[];
+  float2* C = sm;
+  float2* tw = C + N * CW;
+  float2* ry = tw + N;
+  float2* hy = ry + N;                // hy (far: propagator / near: detector factor of distance d)
+  double* red = reinterpret_cast<double*>(hy + N);
+  const int p0 = blockIdx.x * CW;
+  const int f = blockIdx.y;
+  const bool FAR = a.farfield != 0;
+  const int b = f, m = a.m;
+  const size_t fo = ((size_t)b * a.M + m) * NN;
+  for (int i = threadIdx.x; i < N; i += NT2) {
+    tw[i] = a.tw[i];
+    hy[i] = a.hy[i];
+  }
+  double dry = 0.0, drx = 0.0;
+  if (FAR && (MODE == C_PSI0 || MODE == C_Q)) {
+    const double py = a.pos[2 * b], px = a.pos[2 * b + 1];
+    dry = py - floor(py + 0.5);
+    drx = px - floor(px + 0.5);
+    for (int i = threadIdx.x; i < N; i += NT2) ry[i] = ramp1(dry, i, N);
+  }
+  __syncthreads();
+
+  // S1 from global column tile -> smem
+  auto stage_in = [&](const float2* src, int sgn) {
+    for (int tau = threadIdx.x; tau < CW * N2; tau += NT2) {
+      const int c = tau % CW, t = tau / CW;
+      float2 v[N1];
+#pragma unroll
+      for (int i = 0; i < N1; ++i) v[i] = src[(size_t)(N2 * i + t) * N + p0 + c];
+      if (sgn < 0) { dft<N1, -1>(v); twiddle<-1>(v, tw, t); }
+      else { dft<N1, +1>(v); twiddle<+1>(v, tw, t); }
+#pragma unroll
+      for (int k = 0; k < N1; ++k) C[(N2 * k + t) * CW + c] = v[k];
+    }
+  };
+  // S4 from smem -> global column tile (natural y)
+  auto stage_out = [&](float2* dst, int sgn) {
+    for (int tau = threadIdx.x; tau < CW * N2; tau += NT2) {
+      const int c = tau % CW, t = tau / CW;
+      float2 v[N1];
+#pragma unroll
+      for (int i = 0; i < N1; ++i) v[i] = C[(N2 * i + t) * CW + c];
+      if (sgn < 0) dft<N1, -1>(v);
+      else dft<N1, +1>(v);
+#pragma unroll
+      for (int k = 0; k < N1; ++k) dst[(size_t)(N2 * k + t) * N + p0 + c] = v[k];
+    }
+  };
+  // S3 of registers -> smem
+  auto s3_store = [&](float2 (&v)[N2], int c, int t, int sgn) {
+    if (sgn < 0) { dft<N2, -1>(v); twiddle<-1>(v, tw, t); }
+    else { dft<N2, +1>(v); twiddle<+1>(v, tw, t); }
+#pragma unroll
+    for (int k = 0; k < N2; ++k) C[(N2 * t + k) * CW + c] = v[k];
+  };
+  auto s2_load = [&](float2 (&v)[N2], int c, int t, int sgn) {
+#pragma unroll
+    for (int i = 0; i < N2; ++i) v[i] = C[(N2 * t + i) * CW + c];
+    if (sgn < 0) dft<N2, -1>(v);
+    else dft<N2, +1>(v);
+  };
+
+  if (MODE == C_PROP || MODE == C_PROP_ADJ) {
+    float2* F = (a.buf == 1 ? a.FR : a.FA) + fo;
+    stage_in(F, -1);
+    __syncthreads();
+    for (int tau = threadIdx.x; tau < CW * N1; tau += NT2) {
+      const int c = tau % CW, t = tau / CW;
+      float2 v[N2];
+      s2_load(v, c, t, -1);
+      const float2 hx = a.hx[p0 + c];
+#pragma unroll
+      for (int i = 0; i < N2; ++i) {
+        const float2 h = cmul(hy[t + N1 * i], hx);
+        v[i] = (MODE == C_PROP) ? cmul(v[i], h) : cmulc(v[i], h);
+      }
+      s3_store(v, c, t, +1);
+    }
+    __syncthreads();
+    stage_out(F, +1);
+  } else if (MODE == C_PSI0 || MODE == C_SEED || MODE == C_PG) {
+    // Fourier-space input from op, inverse y-transform to global
+    for (int tau = threadIdx.x; tau < CW * N1; tau += NT2) {
+      const int c = tau % CW, t = tau / CW;
+      const int kx = p0 + c;
+      float2 v[N2];
+      if (MODE == C_PSI0) {
+        const float2* ph = a.phat + (size_t)m * NN;
+        const float2 rx = cscale(ramp1(drx, kx, N), 1.0f / (float)NN);
+#pragma unroll
+        for (int i = 0; i < N2; ++i) {
+          const int ky = t + N1 * i;
+          v[i] = cmul(cmul(ph[(size_t)ky * N + kx], ry[ky]), rx);
+        }
+      } else if (MODE == C_SEED) {
+        const float2* fm = a.far + fo;
+        const float* g = a.gI + (size_t)b * NN;
+        const float sc = 2.0f / (float)N;
+#pragma unroll
+        for (int i = 0; i < N2; ++i) {
+          const size_t p = (size_t)(t + N1 * i) * N + kx;
+          v[i] = cscale(fm[p], sc * g[p]);
+        }
+      } else {   // C_PG: qsum / N^2
+        const float2* q = a.qsum + (size_t)f * NN;
+#pragma unroll
+        for (int i = 0; i < N2; ++i) v[i] = cscale(q[(size_t)(t + N1 * i) * N + kx], 1.0f / (float)NN);
+      }
+      s3_store(v, c, t, MODE == C_SEED ? -1 : +1);
+    }
+    __syncthreads();
+    float2* dst = (MODE == C_PG) ? a.tmp + (size_t)f * NN : a.FA + fo;
+    stage_out(dst, MODE == C_SEED ? -1 : +1);
+  } else if (MODE == C_FAR || MODE == C_Q || MODE == C_PHAT) {
+    const int sg = (MODE == C_FAR) ? +1 : -1;
+    const float2* F = (MODE == C_PHAT) ? a.tmp + (size_t)f * NN : a.FA + fo;
+    stage_in(F, sg);
+    __syncthreads();
+    float ay = 0.f, ax = 0.f;
+    for (int tau = threadIdx.x; tau < CW * N1; tau += NT2) {
+      const int c = tau % CW, t = tau / CW;
+      const int kx = p0 + c;
+      float2 v[N2];
+      s2_load(v, c, t, sg);
+      if (MODE == C_FAR) {
+        float2* fm = a.far + fo;
+        float* g = a.gI + (size_t)b * NN;
+        const float invN = 1.0f / (float)N;
+#pragma unroll
+        for (int i = 0; i < N2; ++i) {
+          const size_t p = (size_t)(t + N1 * i) * N + kx;
+          const float2 P = cscale(v[i], invN);
+          fm[p] = P;
+          const float I = fmaf(P.x, P.x, P.y * P.y);
+          g[p] = (m == 0) ? I : g[p] + I;
+        }
+      } else if (MODE == C_PHAT) {
+        float2* o = a.phat_w + (size_t)f * NN;
+#pragma unroll
+        for (int i = 0; i < N2; ++i) o[(size_t)(t + N1 * i) * N + kx] = v[i];
+      } else {   // C_Q
+        const float2* ph = a.phat + (size_t)m * NN;
+        float2* q = a.qacc ? a.qacc + fo : nullptr;
+        const float2 rx = ramp1(drx, kx, N);
+        const float fx = freqf(kx, N);
+#pragma unroll
+        for (int i = 0; i < N2; ++i) {
+          const int ky = t + N1 * i;
+          const size_t p = (size_t)ky * N + kx;
+          const float2 r = cmul(ry[ky], rx);
+          const float2 base = cmul(cconj(v[i]), cmul(ph[p], r));
+          ay += freqf(ky, N) * base.y;
+          ax += fx * base.y;
+          if (q) q[p] = cmulc(v[i], r);
+        }
+      }
+    }
+    if (MODE == C_Q && a.posp) {
+      const double sy = block_sum2(ay, red), sx = block_sum2(ax, red);
+      if (threadIdx.x == 0) {
+        double* pp = a.posp + ((size_t)b * gridDim.x + blockIdx.x) * 2;
+        pp[0] = (m == 0) ? sy : pp[0] + sy;
+        pp[1] = (m == 0) ? sx : pp[1] + sx;
+      }
+    }
+  } else if (MODE == C_NEAR_PHI) {
+    // Phi = DFT_-[phi] (kept in registers and stored for the shift gradients); then for each
+    // distance Psi_d = IDFT_-{Phi G_d}: y-inverse here, x-inverse in the row kernel
+    constexpr int NTASK = (CW * N1 + NT2 - 1) / NT2;
+    stage_in(a.FA + fo, -1);
+    __syncthreads();
+    float2* Phi = a.far + (((size_t)b * (a.nd + 1) + a.nd) * a.M + m) * NN;
+    float2 keep[NTASK][N2];
+#pragma unroll
+    for (int it = 0; it < NTASK; ++it) {
+      const int tau = threadIdx.x + it * NT2;
+      if (tau >= CW * N1) break;
+      const int c = tau % CW, t = tau / CW;
+      s2_load(keep[it], c, t, -1);
+#pragma unroll
+      for (int i = 0; i < N2; ++i) Phi[(size_t)(t + N1 * i) * N + p0 + c] = keep[it][i];
+    }
+    for (int d = 0; d < a.nd; ++d) {
+      const double sy = a.pos[((size_t)b * a.nd + d) * 2], sx = a.pos[((size_t)b * a.nd + d) * 2 + 1];
+      __syncthreads();   // every S2 read (d = 0) / S4 read (d > 0) of the tile is done
+      for (int i = threadIdx.x; i < N; i += NT2) ry[i] = cmul(ramp1(sy, i, N), a.hd[(size_t)d * N + i]);
+      __syncthreads();
+#pragma unroll
+      for (int it = 0; it < NTASK; ++it) {
+        const int tau = threadIdx.x + it * NT2;
+        if (tau >= CW * N1) break;
+        const int c = tau % CW, t = tau / CW, kx = p0 + c;
+        const float2 gx = cscale(cmul(ramp1(sx, kx, N), a.hd[(size_t)d * N + kx]), 1.0f / (float)NN);
+        float2 v[N2];
+#pragma unroll
+        for (int i = 0; i < N2; ++i) v[i] = cmul(cmul(keep[it][i], ry[t + N1 * i]), gx);
+        s3_store(v, c, t, +1);
+      }
+      __syncthreads();
+      stage_out(a.far + (((size_t)b * (a.nd + 1) + d) * a.M + m) * NN, +1);
+    }
+  } else if (MODE == C_NEAR_Q) {
+    // Q_d = DFT_-[seed_d]; shift-gradient partials; phibar = IDFT_-{sum_d conj(G_d) Q_d}
+    constexpr int NTASK = (CW * N1 + NT2 - 1) / NT2;
+    const float2* Phi = a.far + (((size_t)b * (a.nd + 1) + a.nd) * a.M + m) * NN;
+    float2 acc[NTASK][N2];
+#pragma unroll
+    for (int it = 0; it < NTASK; ++it)
+#pragma unroll
+      for (int i = 0; i < N2; ++i) acc[it][i] = make_float2(0.f, 0.f);
+    for (int d = 0; d < a.nd; ++d) {
+      const double sy = a.pos[((size_t)b * a.nd + d) * 2], sx = a.pos[((size_t)b * a.nd + d) * 2 + 1];
+      __syncthreads();
+      stage_in(a.far + (((size_t)b * (a.nd + 1) + d) * a.M + m) * NN, -1);
+      for (int i = threadIdx.x; i < N; i += NT2) ry[i] = cmul(ramp1(sy, i, N), a.hd[(size_t)d * N + i]);
+      __syncthreads();
+      float ay = 0.f, ax = 0.f;
+#pragma unroll
+      for (int it = 0; it < NTASK; ++it) {
+        const int tau = threadIdx.x + it * NT2;
+        if (tau >= CW * N1) break;
+        const int c = tau % CW, t = tau / CW, kx = p0 + c;
+        const float2 gx = cmul(ramp1(sx, kx, N), a.hd[(size_t)d * N + kx]);
+        const float fx = freqf(kx, N);
+        float2 v[N2];
+        s2_load(v, c, t, -1);
+#pragma unroll
+        for (int i = 0; i < N2; ++i) {
+          const int ky = t + N1 * i;
+          const float2 G = cmul(ry[ky], gx);
+          const float2 base = cmul(cconj(v[i]), cmul(Phi[(size_t)ky * N + kx], G));
+          ay += freqf(ky, N) * base.y;
+          ax += fx * base.y;
+          acc[it][i] = cadd(acc[it][i], cmulc(v[i], G));
+        }
+      }
+      if (a.posp) {
+        const double s_y = block_sum2(ay, red), s_x = block_sum2(ax, red);
+        if (threadIdx.x == 0) {
+          double* pp = a.posp + (((size_t)b * a.nd + d) * gridDim.x + blockIdx.x) * 2;
+          pp[0] = (m == 0) ? s_y : pp[0] + s_y;
+          pp[1] = (m == 0) ? s_x : pp[1] + s_x;
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < NTASK; ++it) {
+      const int tau = threadIdx.x + it * NT2;
+      if (tau >= CW * N1) break;
+      const int c = tau % CW, t = tau / CW;
+      float2 v[N2];
+#pragma unroll
+      for (int i = 0; i < N2; ++i) v[i] = cscale(acc[it][i], 1.0f / (float)NN);
+      s3_store(v, c, t, +1);
+    }
+    __syncthreads();
+    stage_out(a.FA + fo, +1);
+  }
+}
+
+// ============================================================================ loss, final reductions
+constexpr int LOSS_PX = 1024;   // pixels per loss CTA (256 threads x 4)
+
+__global__ void __launch_bounds__(256) k_loss2(const TPArgs a) {
+  __shared__ double red[8];
+  const size_t NN = (size_t)a.N * a.N;
+  const size_t base = (size_t)blockIdx.y * NN;
+  double acc = 0.0;
+  for (int e = 0; e < 4; ++e) {
+    const size_t p = base + (size_t)blockIdx.x * LOSS_PX + e * 256 + threadIdx.x;
+    const float I = a.gI[p];
+    if (a.I_out) a.I_out[p] = I;
+    if (!a.I_meas) continue;
+    const float im = a.I_meas[p];
+    float term, dI;
+    if (a.loss == 0) {
+      const float sI = sqrtf(I + a.eps), sM = sqrtf(im + a.eps);
+      const float df = sI - sM;
+      term = df * df;
+      dI = df / sI;
+    } else {
+      term = I - im * logf(I + a.eps);
+      dI = 1.0f - im / (I + a.eps);
+    }
+    acc += (double)term;
+    a.gI[p] = dI * (float)a.inv_npix;
+  }
+  const double s = block_sum2(acc, red);
+  if (threadIdx.x == 0) a.lossp[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(256) k_final2(const TPArgs a, int nloss, int ncolblk) {
+  __shared__ double red[8];
+  if (a.loss_out) {
+    const int chunk = (nloss + 255) / 256;
+    double acc = 0.0;
+    for (int i = threadIdx.x * chunk; i < min(nloss, (int)(threadIdx.x + 1) * chunk); ++i) acc += a.lossp[i];
+    const double s = block_sum2(acc, red);
+    if (threadIdx.x == 0) *a.loss_out = s * a.inv_npix;
+  }
+  if (a.gpos) {
+    const double sc = 2.0 * 3.14159265358979323846 / ((double)a.N * a.N);
+    for (int q = threadIdx.x; q < a.B * a.nd; q += 256) {
+      double sy = 0.0, sx = 0.0;
+      for (int k = 0; k < ncolblk; ++k) {
+        sy += a.posp[((size_t)q * ncolblk + k) * 2];
+        sx += a.posp[((size_t)q * ncolblk + k) * 2 + 1];
+      }
+      a.gpos[2 * q] = (float)(sc * sy);
+      a.gpos[2 * q + 1] = (float)(sc * sx);
+    }
+  }
+}
+
+__global__ void k_add2(float2* __restrict__ g, const float2* __restrict__ q, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    g[i] = cadd(g[i], q[i]);
+}
+
+// ============================================================================ launch sequence
+template <int N, int MODE>
+static void row(const TPArgs& a, int gy, cudaStream_t s) {
+  k_row<N, MODE><<<dim3(N / Geo2<N>::RB, gy), NT2, row_smem_bytes<N>(), s>>>(a);
+}
+template <int N, int MODE>
+static void col(const TPArgs& a, int gy, cudaStream_t s) {
+  k_col<N, MODE><<<dim3(N / Geo2<N>::CW, gy), NT2, col_smem_bytes<N>(), s>>>(a);
+}
+
+template <int N, class F>
+static cudaError_t set_attr(F* k, int bytes) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <int N>
+static cudaError_t prepare_t2() {
+  cudaError_t e = cudaSuccess;
+  const int rb = row_smem_bytes<N>(), cb = col_smem_bytes<N>();
+#define ROWA(M_) if (e == cudaSuccess) e = set_attr<N>(k_row<N, M_>, rb);
+#define COLA(M_) if (e == cudaSuccess) e = set_attr<N>(k_col<N, M_>, cb);
+  ROWA(R_FWD) ROWA(R_RC_FIRST) ROWA(R_RC) ROWA(R_ADJ) ROWA(R_NEAR_DET) ROWA(R_NEAR_SEED) ROWA(R_PHAT) ROWA(R_PG_OUT)
+  COLA(C_PROP) COLA(C_PROP_ADJ) COLA(C_PSI0) COLA(C_FAR) COLA(C_SEED) COLA(C_Q) COLA(C_PHAT) COLA(C_PG)
+  COLA(C_NEAR_PHI) COLA(C_NEAR_Q)
+#undef ROWA
+#undef COLA
+  return e;
+}
+
+cudaError_t prepare_twopass(int N) {
+  switch (N) {
+    case 256: return prepare_t2<256>();
+    case 512: return prepare_t2<512>();
+    case 1024: return prepare_t2<1024>();
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int N>
+static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+  static bool prepared = false;
+  if (!prepared) {
+    cudaError_t e = prepare_t2<N>();
+    if (e != cudaSuccess) return e;
+    prepared = true;
+  }
+  const bool far = a.farfield != 0;
+  const int B = a.B, M = a.M, L = a.L;
+  const size_t NN = (size_t)N * N;
+  const int nloss = (int)(B * a.nd * (NN / LOSS_PX));
+  const int ncol = N / Geo2<N>::CW;
+  if (ev0) cudaEventRecord(ev0, s);
+  if (far) {
+    row<N, R_PHAT>(a, M, s);
+    col<N, C_PHAT>(a, M, s);
+  }
+  // ---------------- forward
+  for (int m = 0; m < M; ++m) {
+    a.m = m;
+    if (far) col<N, C_PSI0>(a, B, s);
+    for (int j = 0; j < L; ++j) {
+      a.j = j;
+      row<N, R_FWD>(a, B, s);
+      if (j < L - 1) {
+        a.buf = 0;
+        col<N, C_PROP>(a, B, s);
+      } else if (far) {
+        col<N, C_FAR>(a, B, s);
+      } else {
+        col<N, C_NEAR_PHI>(a, B, s);
+        for (int d = 0; d < a.nd; ++d) {
+          a.d = d;
+          row<N, R_NEAR_DET>(a, B, s);
+        }
+      }
+    }
+  }
+  k_loss2<<<dim3((unsigned)(NN / LOSS_PX), B * a.nd), 256, 0, s>>>(a);
+  if (a.adj) {
+    // ---------------- adjoint
+    for (int m = 0; m < M; ++m) {
+      a.m = m;
+      if (far) {
+        col<N, C_SEED>(a, B, s);
+      } else {
+        for (int d = 0; d < a.nd; ++d) {
+          a.d = d;
+          row<N, R_NEAR_SEED>(a, B, s);
+        }
+        col<N, C_NEAR_Q>(a, B, s);
+      }
+      for (int sg = a.ncp - 1; sg >= 0; --sg) {
+        const int j0 = sg * a.cp, j1 = min(j0 + a.cp, L) - 1;
+        a.s = sg;
+        a.j0 = j0;
+        a.j1 = j1;
+        if (sg != a.ncp - 1 && j1 > j0) {
+          a.j = j0;
+          row<N, R_RC_FIRST>(a, B, s);
+          for (int j = j0 + 1; j <= j1; ++j) {
+            a.buf = 1;
+            col<N, C_PROP>(a, B, s);
+            a.j = j;
+            row<N, R_RC>(a, B, s);
+          }
+        }
+        for (int j = j1; j >= j0; --j) {
+          a.j = j;
+          row<N, R_ADJ>(a, B, s);
+          if (j > 0) {
+            a.buf = 0;
+            col<N, C_PROP_ADJ>(a, B, s);
+          } else if (far) {
+            col<N, C_Q>(a, B, s);
+          }
+        }
+      }
+    }
+  }
+  if (ev1) cudaEventRecord(ev1, s);
+  if (a.adj) {
+    k_final2<<<1, 256, 0, s>>>(a, nloss, ncol);
+    if (a.g_probe) {
+      const size_t MNN = (size_t)M * NN;
+      // per-element FP64 sum over the batch (deterministic), then back to real space
+      launch_qsum(a.qacc, a.qsum, B, MNN, s);
+      if (far) {
+        col<N, C_PG>(a, M, s);
+        row<N, R_PG_OUT>(a, M, s);
+      } else {
+        k_add2<<<1024, 256, 0, s>>>(a.g_probe, a.qsum, MNN);
+      }
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_twopass(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+  switch (a.N) {
+    case 256: return twopass_t<256>(a, s, ev0, ev1);
+    case 512: return twopass_t<512>(a, s, ev0, ev1);
+    case 1024: return twopass_t<1024>(a, s, ev0, ev1);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace adorym

@@ -38,6 +38,42 @@ struct PathArgs {
   float* gpos;            // [B][2] or [B][n_dist][2] (overwritten), or null
 };
 
+// Arguments of the two-pass path (N >= 256): fields in HBM, one row and one column kernel per
+// slice step.  The per-launch fields (m, j, s, j0, j1, d, buf) select the step.
+struct TPArgs {
+  int N, L, M, B, Ly, Lx, cp, ncp, nd, loss, farfield, adj;
+  float eps, kdz;
+  double inv_npix;
+  const float2* T;         // transmission volume [Lz][Ly][Lx]
+  const float2* probe;     // [M][N][N]
+  const float2* phat;      // [M][N][N] DFT_-[probe] (natural frequency order)
+  float2* phat_w;          // same buffer, written by the probe transform
+  const float* pos;
+  const float* I_meas;
+  float* I_out;
+  const float2* tw;
+  const float2* hy;        // exp(i pi c f^2) / N
+  const float2* hx;
+  const float2* hd;        // near field [n_dist][N] exp(i pi f^2 / N_F)
+  float2* FA;              // [B][M][N*N] forward / adjoint field
+  float2* FR;              // [B][M][N*N] recompute field
+  float2* ckpt;            // [B][M][ncp][N*N]
+  float2* seg;             // [B][M][cp][N*N]
+  float2* far;             // far [B][M][N*N]; near [B][n_dist + 1][M][N*N] (Psi_d, then Phi)
+  float* gI;               // [B][n_dist][N*N]
+  double* lossp;           // [B * n_dist][N*N / 1024] loss partials
+  double* posp;            // [B][n_dist][N / CW][2] position / shift gradient partials
+  float2* qacc;            // [B][M][N*N]
+  float2* qsum;            // [M][N*N]
+  float2* tmp;             // [M][N*N]
+  float* gd;
+  float* gb;
+  float* gpos;
+  float2* g_probe;
+  double* loss_out;
+  int m, j, s, j0, j1, d, buf;
+};
+
 // launchers (return cudaGetLastError())
 cudaError_t launch_probe_hat(int N, int M, const float2* probe, float2* phat, const float2* tw, cudaStream_t s);
 cudaError_t launch_path(const PathArgs& a, int farfield, cudaStream_t s);
@@ -52,7 +88,12 @@ cudaError_t launch_transmission(const float* vd, const float* vb, float2* T, int
 cudaError_t launch_rotate_adj(const float* gd_rot, const float* gb_rot, float* gd, float* gb, int Lz, int Ly, int Lx,
                               float c, float sn, cudaStream_t s);
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s);
+// qsum[i] = sum_b qacc[b][i] in FP64, fixed order
+cudaError_t launch_qsum(const float2* qacc, float2* qsum, int B, size_t MNN, cudaStream_t s);
 int path_smem_bytes(int N);
+// whole two-pass loss/gradient (adj = 1) or forward (adj = 0) sequence for N in {256, 512, 1024}
+cudaError_t launch_twopass(TPArgs a, cudaStream_t s, cudaEvent_t ev_start, cudaEvent_t ev_stop);
+cudaError_t prepare_twopass(int N);
 // set the dynamic shared-memory attributes of every kernel used for tile size N (call outside capture)
 cudaError_t prepare_path(int N, int farfield);
 

@@ -49,7 +49,7 @@ def test_workspace_planning_and_validation(lib):
     assert T + 128 * 14 * 128 * 1024 < ws < T + 128 * 20 * 128 * 1024
     ws1 = workspace_bytes(_problem(checkpoint_every=1))
     assert ws1 > ws
-    for bad in (dict(N=100), dict(N=256), dict(Lz=31), dict(B=0), dict(M=0), dict(loss=7), dict(eps=-1.0),
+    for bad in (dict(N=100), dict(N=2048), dict(Lz=31), dict(B=0), dict(M=0), dict(loss=7), dict(eps=-1.0),
                 dict(checkpoint_every=33), dict(farfield=0, nf=[0.1], Ly=128, Lx=128, Lz=128 * 32 + 1),
                 dict(farfield=0, nf=[], Ly=128, Lx=128, Lz=128 * 32), dict(tomo=1, theta=float("nan"))):
         with pytest.raises(AdorymError):

@@ -13,6 +13,7 @@ def test_autograd_matches_oracle_and_finite_difference():
     from paper_2012_12686_gb300.autograd import multislice_loss
     dev = torch.device("cuda:0")
     case = C.small_case(N=32, L=4, M=1, B=5, loss="lsq", seed=41)
+    case["problem"]["eps"] = 1.0      # smooth amplitude loss, so an FP32 central difference resolves it
     Im = C.measured(case)
     L, gd, gb, gp, gpos = C.oracle_loss_grad(case, Im)
     t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).to(dev)
@@ -28,10 +29,11 @@ def test_autograd_matches_oracle_and_finite_difference():
     assert C.rel(b.grad.cpu().numpy() / 2, gb) < C.TOL_G
     assert C.rel(probe.grad.cpu().numpy() / 2, gp) < C.TOL_G
     assert C.rel(pos.grad.cpu().numpy() / 2, gpos) < C.TOL_G
-    # directional derivative along a random delta perturbation (FP32 central difference)
+    # directional derivative along a random delta perturbation (FP32 central difference; the step
+    # keeps the loss difference far above FP32 rounding while O(h^2) stays below 1 %)
     g = np.random.default_rng(1)
     v = torch.from_numpy(g.uniform(-1, 1, case["delta"].shape).astype(np.float32)).to(dev)
-    h = 2e-5
+    h = 5e-5
     with torch.no_grad():
         lp = multislice_loss(d + h * v, b, probe, pos, Imt, case["problem"]).item()
         lm = multislice_loss(d - h * v, b, probe, pos, Imt, case["problem"]).item()
