@@ -148,6 +148,108 @@ def oracle_sample(w, I_meas_np, n_pos: int, workers: int):
     return wall, n_pos
 
 
+# ----------------------------------------------------------------------------- multi-rank host logic
+def rank_batches(rank: int, world: int, start: int, count: int, nb: int):
+    """Minibatch indices a rank evaluates at steps start..start+count-1: at every step the ranks
+    take distinct minibatches of the epoch (positions are independent units, no collective)."""
+    return [(rank + (start + k) * world) % nb for k in range(count)]
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """Max of a per-rank number over the process group (identity without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- plain GPU path
+def plain_loss(delta, beta, probe, pos, I_meas, p):
+    """The plain, unfused GPU formulation the fused engine is compared with: the same far-field
+    multislice model written with torch.fft and elementwise tensor ops, differentiated by torch
+    autograd (every slice's intermediates kept), one request at a time.  Measurement baseline
+    only; it is not part of the engine."""
+    import torch
+    N, L, kdz, c = p["N"], p["L"], p["kdz"], p["lambda_dz_over_px2"]
+    dev = delta.device
+    p0 = torch.floor(pos.detach() + 0.5)
+    dr = pos - p0
+    f = torch.fft.fftfreq(N, device=dev)
+    ramp = torch.exp(-2j * math.pi * (dr[:, 0, None, None] * f[None, :, None] + dr[:, 1, None, None] * f[None, None, :]))
+    psi = torch.fft.ifft2(torch.fft.fft2(probe)[None] * ramp[:, None])            # [B, M, N, N]
+    if p.get("tomo"):
+        delta, beta = plain_rotate(delta, p["theta"]), plain_rotate(beta, p["theta"])
+    pad = N
+    dp = torch.nn.functional.pad(delta, (pad, pad, pad, pad))
+    bp = torch.nn.functional.pad(beta, (pad, pad, pad, pad))
+    iy = (p0[:, 0].long() + pad)[:, None] + torch.arange(N, device=dev)[None]
+    ix = (p0[:, 1].long() + pad)[:, None] + torch.arange(N, device=dev)[None]
+    H = torch.exp(1j * math.pi * c * (f[:, None] ** 2 + f[None, :] ** 2))
+    for j in range(L):
+        od = dp[j][iy[:, :, None], ix[:, None, :]]
+        ob = bp[j][iy[:, :, None], ix[:, None, :]]
+        phi = psi * torch.exp(-kdz * ob + 1j * kdz * od)[:, None]
+        if j < L - 1:
+            psi = torch.fft.ifft2(torch.fft.fft2(phi) * H)
+    Psi = torch.fft.ifft2(phi) * N
+    I = (Psi.real ** 2 + Psi.imag ** 2).sum(1)
+    eps = p["eps"]
+    if p["loss"] == "lsq":
+        terms = (torch.sqrt(I + eps) - torch.sqrt(I_meas + eps)) ** 2
+    else:
+        terms = I - I_meas * torch.log(I + eps)
+    return terms.mean(), I
+
+
+def plain_rotate(vol, theta):
+    """Bilinear rotation about y in the x-z plane with torch indexing (differentiable by autograd)."""
+    import torch
+    Lz, Ly, Lx = vol.shape
+    dev = vol.device
+    zt, xt = torch.meshgrid(torch.arange(Lz, device=dev, dtype=torch.float64),
+                            torch.arange(Lx, device=dev, dtype=torch.float64), indexing="ij")
+    cz, cx = (Lz - 1) / 2.0, (Lx - 1) / 2.0
+    c, s = math.cos(theta), math.sin(theta)
+    x0 = c * (xt - cx) - s * (zt - cz) + cx
+    z0 = s * (xt - cx) + c * (zt - cz) + cz
+    fx, fz = torch.floor(x0), torch.floor(z0)
+    ax, az = (x0 - fx).float(), (z0 - fz).float()
+    out = torch.zeros_like(vol)
+    for dz, wz in ((0, 1 - az), (1, az)):
+        for dx, wx in ((0, 1 - ax), (1, ax)):
+            zi, xi = (fz + dz).long(), (fx + dx).long()
+            ok = (zi >= 0) & (zi < Lz) & (xi >= 0) & (xi < Lx)
+            g = vol[zi.clamp(0, Lz - 1), :, xi.clamp(0, Lx - 1)]            # [Lz, Lx, Ly]
+            out = out + (g * (wz * wx * ok)[:, :, None]).permute(0, 2, 1)
+    return out
+
+
+def time_plain(w, dev, pos_b, I_meas_b, steps, warmup):
+    """Per-step device time of the plain path (loss + autograd backward) on the same minibatches."""
+    import torch
+    p = w["problem"]
+    d = torch.from_numpy(w["delta"]).to(dev).requires_grad_()
+    b = torch.from_numpy(w["beta"]).to(dev).requires_grad_()
+    probe = torch.from_numpy(w["probe"]).to(dev).requires_grad_()
+    nb = len(pos_b)
+    times = []
+    for k in range(warmup + steps):
+        pos = pos_b[k % nb].clone().requires_grad_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        loss, _ = plain_loss(d, b, probe, pos, I_meas_b[k % nb], p)
+        loss.backward()
+        e.record()
+        torch.cuda.synchronize(dev)
+        if k >= warmup:
+            times.append(s.elapsed_time(e))
+        d.grad = b.grad = probe.grad = None
+    return times
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args, rank):
     if rank != 0:
@@ -234,8 +336,8 @@ def run_ours(args, rank, world, local_rank):
         def step(k):
             eng.loss_grad(prob, oid, probe, pos_b[k % nb], I_meas[k % nb], loss, gd, gb, gp, gpos)
 
-        for k in range(args.warmup):
-            step(rank + k * world)
+        for k in rank_batches(rank, world, 0, args.warmup, nb):
+            step(k)
         stream.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -244,24 +346,29 @@ def run_ours(args, rank, world, local_rank):
     with ClockSampler(local_rank) as clk, torch.cuda.stream(stream):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        for k in range(args.steps):
+        for k, bi in enumerate(rank_batches(rank, world, args.warmup, args.steps, nb)):
             flush.fill_(float(k))
             ev[k][0].record(stream)
-            step(rank + (args.warmup + k) * world)
+            step(bi)
             ev[k][1].record(stream)
             path_ms.append(eng.kernel_ms())
         torch.cuda.synchronize(dev)
         wall = time.perf_counter() - t0
     step_ms = [a.elapsed_time(bq) for a, bq in ev]
-    t_ours = sum(step_ms) / 1e3
-    if world > 1:
-        tt = torch.tensor([t_ours], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ours = float(tt.item())
+    t_ours = max_over_ranks(sum(step_ms) / 1e3, dev)
     value = units * args.steps * world / t_ours
     ms_sorted = sorted(step_ms)
     p50 = ms_sorted[len(ms_sorted) // 2]
     p99 = ms_sorted[min(len(ms_sorted) - 1, int(math.ceil(0.99 * len(ms_sorted))) - 1)]
+
+    # ---- the plain unfused GPU path on the same minibatches (comparison arm of the metric)
+    plain = None
+    if not args.no_plain:
+        pt = time_plain(w, dev, pos_b, I_meas, steps=min(args.steps, 20), warmup=3)
+        ps = sorted(pt)
+        plain = {"value": units / (statistics.mean(pt) / 1e3), "unit": UNIT, "ms_per_step": statistics.mean(pt),
+                 "p50_ms": ps[len(ps) // 2], "p99_ms": ps[min(len(ps) - 1, int(math.ceil(0.99 * len(ps))) - 1)],
+                 "steps": len(pt), "impl": "torch.fft + elementwise + torch autograd, one request at a time"}
 
     # ---- end to end through the public C ABI with pinned host buffers
     n_e2e = max(3, min(args.steps, 50))
@@ -280,11 +387,7 @@ def run_ours(args, rank, world, local_rank):
         for k in range(n_e2e):
             eng.loss_grad(prob, oid, h_probe, h_pos[k % nb], h_meas[k % nb], h_loss, gd, gb, h_gp, h_gpos)
         t_e2e = time.perf_counter() - t0
-    e2e_val = units * n_e2e / t_e2e
-    if world > 1:
-        tt = torch.tensor([t_e2e / n_e2e], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_val = units * world / float(tt.item())
+    e2e_val = units * world * n_e2e / max_over_ranks(t_e2e, dev)
     h2d = h_meas[0].numel() * 4 + h_pos[0].numel() * 4 + h_probe.numel() * 8 + h_gp.numel() * 8
     d2h = 8 + h_gp.numel() * 8 + h_gpos.numel() * 4
 
@@ -315,6 +418,9 @@ def run_ours(args, rank, world, local_rank):
                                       f"x {sm_max:.0f} MHz",
                          "hbm_algorithmic_gbs": hbm_ach, "hbm_peak_gbs": peaks.get("hbm_gbs", 6795.5)},
             "clocks": clk.summary(), "wall_s_timed": wall}
+    if plain is not None:
+        plain["speedup_of_fused"] = value / plain["value"]
+        line["plain_gpu"] = plain
     if not args.no_cpu_baseline and world == 1:
         cores = os.cpu_count() or 1
         n_pos = min(8 * cores, len(all_pos))
@@ -346,6 +452,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the plain torch GPU path")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

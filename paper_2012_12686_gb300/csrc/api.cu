@@ -100,7 +100,7 @@ int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan
   {
     const size_t V = (size_t)p.Lz * p.Ly * p.Lx;
     q.off_T = take(V * f2);
-    if (q.tomo && q.want_obj) q.off_grot = take(2 * V * sizeof(float));
+    if (q.want_obj) q.off_grot = take(2 * V * sizeof(double));   // FP64 object-gradient accumulators
   }
   q.bytes_probe = M * NN * f2;
   q.bytes_pos = B * q.nd * 2 * sizeof(float);
@@ -187,7 +187,7 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
     *err = std::string(what) + ": " + cudaGetErrorString(e);
     return ADORYM_EDEVICE;
   };
-  float *gd = c.gd, *gb = c.gb;
+  double *gd = nullptr, *gb = nullptr;
   const size_t V = (size_t)p.Lz * p.Ly * p.Lx;
   const double cth = std::cos(p.theta), sth = std::sin(p.theta);
   int rc;
@@ -196,11 +196,12 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
                                     (float)sth, s),
                 "transmission")))
     return rc;
-  if (pl.tomo && pl.want_obj) {
-    float* grot = reinterpret_cast<float*>(W(pl.off_grot));
-    if ((rc = chk(cudaMemsetAsync(grot, 0, 2 * V * sizeof(float), s), "memset"))) return rc;
-    gd = grot;
-    gb = grot + V;
+  if (pl.want_obj) {
+    // the scatter-add over overlapping positions is a reduction: accumulate it in FP64
+    double* acc = reinterpret_cast<double*>(W(pl.off_grot));
+    if ((rc = chk(cudaMemsetAsync(acc, 0, 2 * V * sizeof(double), s), "memset"))) return rc;
+    gd = acc;
+    gb = acc + V;
   }
   float2* phat = reinterpret_cast<float2*>(W(pl.off_phat));
   if (two_pass(p.N)) {
@@ -302,9 +303,10 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
         return rc;
     }
   }
-  if (pl.tomo && pl.want_obj) {
-    if ((rc = chk(launch_rotate_adj(gd, gb, c.gd, c.gb, p.Lz, p.Ly, p.Lx, (float)cth, (float)sth, s), "rotate_adj")))
-      return rc;
+  if (pl.want_obj) {
+    if (pl.tomo) rc = chk(launch_rotate_adj(gd, gb, c.gd, c.gb, p.Lz, p.Ly, p.Lx, (float)cth, (float)sth, s), "rotate_adj");
+    else rc = chk(launch_grad_add(gd, gb, c.gd, c.gb, V, s), "grad_add");
+    if (rc) return rc;
   }
   return ADORYM_OK;
 }

@@ -429,8 +429,8 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
               if (gy >= 0 && gy < Ly && gx >= 0 && gx < Lx) {
                 const float2 z = cmulc(pbar, pb[k]);    // psibar conj(psi)
                 const size_t o = ((size_t)gz * Ly + gy) * Lx + gx;
-                atomicAdd(a.gd + o, kdz * z.y);
-                atomicAdd(a.gb + o, -kdz * z.x);
+                atomicAdd(a.gd + o, (double)(kdz * z.y));
+                atomicAdd(a.gb + o, (double)(-kdz * z.x));
               }
             }
             v[k] = pbar;

@@ -70,8 +70,8 @@ __global__ void k_transmission(const float* __restrict__ vd, const float* __rest
   }
 }
 
-__global__ void k_rotate_adj(const float* __restrict__ gdr, const float* __restrict__ gbr, float* __restrict__ gd,
-                           float* __restrict__ gb, int Lz, int Ly, int Lx, float c, float s) {
+__global__ void k_rotate_adj(const double* __restrict__ gdr, const double* __restrict__ gbr, float* __restrict__ gd,
+                             float* __restrict__ gb, int Lz, int Ly, int Lx, float c, float s) {
   const size_t n = (size_t)Lz * Ly * Lx;
   const float cx = 0.5f * (float)(Lx - 1), cz = 0.5f * (float)(Lz - 1);
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -83,7 +83,7 @@ __global__ void k_rotate_adj(const float* __restrict__ gdr, const float* __restr
     const float xs = c * u + s * w + cx, zs = -s * u + c * w + cz;
     const int xa = max(0, (int)floorf(xs - 1.5f)), xb = min(Lx - 1, (int)ceilf(xs + 1.5f));
     const int za = max(0, (int)floorf(zs - 1.5f)), zb = min(Lz - 1, (int)ceilf(zs + 1.5f));
-    float ad = 0.f, ab = 0.f;
+    double ad = 0.0, ab = 0.0;
     for (int zt = za; zt <= zb; ++zt) {
       for (int xt = xa; xt <= xb; ++xt) {
         const Tap t = tap(zt, xt, Lz, Lx, c, s);
@@ -94,14 +94,14 @@ __global__ void k_rotate_adj(const float* __restrict__ gdr, const float* __restr
         if (t.fz == z) wz = 1.f - t.az;
         else if (t.fz + 1 == z) wz = t.az;
         else continue;
-        const float wt = wx * wz;
+        const double wt = (double)(wx * wz);
         const size_t o = ((size_t)zt * Ly + y) * Lx + xt;
-        ad = fmaf(wt, __ldg(gdr + o), ad);
-        ab = fmaf(wt, __ldg(gbr + o), ab);
+        ad = fma(wt, __ldg(gdr + o), ad);
+        ab = fma(wt, __ldg(gbr + o), ab);
       }
     }
-    gd[i] += ad;
-    gb[i] += ab;
+    gd[i] = (float)((double)gd[i] + ad);
+    gb[i] = (float)((double)gb[i] + ab);
   }
 }
 
@@ -114,7 +114,7 @@ cudaError_t launch_transmission(const float* vd, const float* vb, float2* T, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_rotate_adj(const float* gdr, const float* gbr, float* gd, float* gb, int Lz, int Ly, int Lx,
+cudaError_t launch_rotate_adj(const double* gdr, const double* gbr, float* gd, float* gb, int Lz, int Ly, int Lx,
                               float c, float sn, cudaStream_t s) {
   const size_t n = (size_t)Lz * Ly * Lx;
   const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
@@ -123,5 +123,19 @@ cudaError_t launch_rotate_adj(const float* gdr, const float* gbr, float* gd, flo
 }
 
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s) { return cudaMemsetAsync(p, 0, bytes, s); }
+
+__global__ void k_grad_add(const double* __restrict__ ad, const double* __restrict__ ab, float* __restrict__ gd,
+                           float* __restrict__ gb, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    gd[i] = (float)((double)gd[i] + ad[i]);
+    gb[i] = (float)((double)gb[i] + ab[i]);
+  }
+}
+
+cudaError_t launch_grad_add(const double* ad, const double* ab, float* gd, float* gb, size_t n, cudaStream_t s) {
+  const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
+  k_grad_add<<<grid, 256, 0, s>>>(ad, ab, gd, gb, n);
+  return cudaGetLastError();
+}
 
 }  // namespace adorym

@@ -182,8 +182,8 @@ __global__ void __launch_bounds__(NT2) k_row(const TPArgs a) {
           const float2 pbar = cmulc(v[k], T);
           if (a.gd && inb) {
             const float2 z = cmulc(pbar, psi);
-            atomicAdd(a.gd + o, a.kdz * z.y);
-            atomicAdd(a.gb + o, -a.kdz * z.x);
+            atomicAdd(a.gd + o, (double)(a.kdz * z.y));
+            atomicAdd(a.gb + o, (double)(-a.kdz * z.x));
           }
           v[k] = pbar;
           if (!FAR && j == 0 && a.qacc) a.qacc[fo + px] = pbar;

@@ -33,8 +33,8 @@ struct PathArgs {
   float2* fbar;           // near field: [B][N*N] accumulated Fourier-space adjoint
   double* lossp;          // [B] per-problem loss sums
   float2* qacc;           // [B][M][N*N] per-position probe-gradient partials (Fourier space)
-  float* gd;              // object gradient [Lz][Ly][Lx] (+=), or null
-  float* gb;
+  double* gd;             // FP64 object-gradient accumulator [Lz][Ly][Lx] (+=), or null
+  double* gb;
   float* gpos;            // [B][2] or [B][n_dist][2] (overwritten), or null
 };
 
@@ -66,8 +66,8 @@ struct TPArgs {
   float2* qacc;            // [B][M][N*N]
   float2* qsum;            // [M][N*N]
   float2* tmp;             // [M][N*N]
-  float* gd;
-  float* gb;
+  double* gd;              // FP64 object-gradient accumulator
+  double* gb;
   float* gpos;
   float2* g_probe;
   double* loss_out;
@@ -84,9 +84,11 @@ cudaError_t launch_probe_grad(int N, int M, int B, int farfield, const float2* q
 // bilinear rotation of Eq. rotation_transform (rotate = 1)
 cudaError_t launch_transmission(const float* vd, const float* vb, float2* T, int Lz, int Ly, int Lx, float kdz,
                                 int rotate, float c, float sn, cudaStream_t s);
-// transpose of the rotation, added into gd/gb
-cudaError_t launch_rotate_adj(const float* gd_rot, const float* gb_rot, float* gd, float* gb, int Lz, int Ly, int Lx,
-                              float c, float sn, cudaStream_t s);
+// transpose of the rotation applied to the FP64 rotated-frame accumulators, added into gd/gb
+cudaError_t launch_rotate_adj(const double* gd_rot, const double* gb_rot, float* gd, float* gb, int Lz, int Ly,
+                              int Lx, float c, float sn, cudaStream_t s);
+// gd += (float) acc_d, gb += (float) acc_b over n voxels
+cudaError_t launch_grad_add(const double* acc_d, const double* acc_b, float* gd, float* gb, size_t n, cudaStream_t s);
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s);
 // qsum[i] = sum_b qacc[b][i] in FP64, fixed order
 cudaError_t launch_qsum(const float2* qacc, float2* qsum, int B, size_t MNN, cudaStream_t s);

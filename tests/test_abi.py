@@ -44,8 +44,9 @@ def test_workspace_planning_and_validation(lib):
     from paper_2012_12686_gb300.adorym import workspace_bytes, AdorymError
     ws = workspace_bytes(_problem())
     # checkpoints (6) + segment (6) + park + far field + probe partials: ~15 fields of 128 KB per
-    # position, plus the complex64 transmission volume (512 x 512 x 32)
-    T = 512 * 512 * 32 * 8
+    # position, plus the complex64 transmission volume (512 x 512 x 32) and the two FP64
+    # object-gradient accumulators
+    T = 512 * 512 * 32 * (8 + 16)
     assert T + 128 * 14 * 128 * 1024 < ws < T + 128 * 20 * 128 * 1024
     ws1 = workspace_bytes(_problem(checkpoint_every=1))
     assert ws1 > ws
