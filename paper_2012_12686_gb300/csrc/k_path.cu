@@ -619,12 +619,6 @@ int path_smem_bytes(int N) {
 template <int N, int FAR>
 static cudaError_t launch_path_t(const PathArgs& a, cudaStream_t s) {
   const int smem = path_smem_bytes(N);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_path<N, FAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
   k_path<N, FAR><<<a.B, Geo<N>::NT, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -648,12 +642,6 @@ cudaError_t launch_path(const PathArgs& a, int farfield, cudaStream_t s) {
 template <int N>
 static cudaError_t launch_probe_hat_t(int M, const float2* probe, float2* phat, const float2* tw, cudaStream_t s) {
   const int smem = (N * (N + 1) + N) * (int)sizeof(float2);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_probe_hat<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
   k_probe_hat<N><<<M, Geo<N>::NT, smem, s>>>(probe, phat, tw);
   return cudaGetLastError();
 }
@@ -677,12 +665,6 @@ static cudaError_t launch_probe_grad_t(int M, int B, const float2* qacc, float2*
     k_qsum<<<(unsigned)((MNN + 31) / 32), 256, 0, s>>>(qacc, qsum, B, MNN);
   }
   const int smem = (N * (N + 1) + N) * (int)sizeof(float2);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_probe_grad<N, FAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
   k_probe_grad<N, FAR><<<M, Geo<N>::NT, smem, s>>>(qsum, g, tw, lossp, B, inv_npix, loss_out);
   return cudaGetLastError();
 }
@@ -716,10 +698,17 @@ static cudaError_t prepare_t() {
 }
 
 cudaError_t prepare_path(int N, int farfield) {
+  // idempotent; called by every entry point before it enqueues (never inside a stream capture)
+  static bool done[11][2] = {};
+  int l = 0;
+  while ((1 << l) < N) ++l;
+  if (l < 11 && done[l][farfield ? 1 : 0]) return cudaSuccess;
+  cudaError_t e = cudaErrorInvalidValue;
   switch (N) {
 #define ADORYM_CASE(n) \
   case n:              \
-    return farfield ? prepare_t<n, 1>() : prepare_t<n, 0>();
+    e = farfield ? prepare_t<n, 1>() : prepare_t<n, 0>(); \
+    break;
     ADORYM_CASE(8)
     ADORYM_CASE(16)
     ADORYM_CASE(32)
@@ -729,6 +718,8 @@ cudaError_t prepare_path(int N, int farfield) {
     default:
       return cudaErrorInvalidValue;
   }
+  if (e == cudaSuccess && l < 11) done[l][farfield ? 1 : 0] = true;
+  return e;
 }
 
 }  // namespace adorym

@@ -591,23 +591,20 @@ static cudaError_t prepare_t2() {
   return e;
 }
 
+static bool g_prepared2[3] = {false, false, false};
+
 cudaError_t prepare_twopass(int N) {
-  switch (N) {
-    case 256: return prepare_t2<256>();
-    case 512: return prepare_t2<512>();
-    case 1024: return prepare_t2<1024>();
-    default: return cudaErrorInvalidValue;
-  }
+  // idempotent; called by every entry point before it enqueues (never inside a stream capture)
+  const int i = N == 256 ? 0 : N == 512 ? 1 : N == 1024 ? 2 : -1;
+  if (i < 0) return cudaErrorInvalidValue;
+  if (g_prepared2[i]) return cudaSuccess;
+  cudaError_t e = N == 256 ? prepare_t2<256>() : N == 512 ? prepare_t2<512>() : prepare_t2<1024>();
+  if (e == cudaSuccess) g_prepared2[i] = true;
+  return e;
 }
 
 template <int N>
 static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
-  static bool prepared = false;
-  if (!prepared) {
-    cudaError_t e = prepare_t2<N>();
-    if (e != cudaSuccess) return e;
-    prepared = true;
-  }
   const bool far = a.farfield != 0;
   const int B = a.B, M = a.M, L = a.L;
   const size_t NN = (size_t)N * N;
