@@ -433,6 +433,128 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Serving mix: Poisson arrivals of loss+gradient requests of uneven tile size, slice count
+    and batch over resident volumes, through adorym_submit / adorym_poll (slots, footprint
+    admission, captured graphs).  Latency = completion - arrival on the host clock.  The plain
+    torch path is timed once per request template and replayed one request at a time on the same
+    arrival schedule (a single server: start = max(arrival, previous finish))."""
+    import threading
+    import numpy as np
+    import torch
+    from paper_2012_12686_gb300 import synth
+    from paper_2012_12686_gb300.adorym import Engine, Problem, OK
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    g = np.random.default_rng(7)
+    Ls, Ns = (1, 8, 32, 64), (64, 128, 256)
+    side = args.serve_side
+    eng = Engine(0)
+    vols = {}
+    for L in Ls:   # resident volumes side x side x L (ellipsoids, beta = delta / 10)
+        d = synth.ellipsoid_volume((L, side, side), 96, (16, 96), (1, max(1, L // 2)), (1e-6, 3e-6), 5e-6, 50 + L)
+        td = torch.from_numpy(d).to(dev)
+        tb = (td / 10.0).contiguous()
+        vols[L] = (td, tb, eng.register_object(td, tb))
+    probes = {N: torch.from_numpy(synth.probe_phase_screen(N, N / 8.0, 4.0, 1.0, 1e6, 60 + N)).to(dev) for N in Ns}
+    # request templates with their own positions and measured data (forward of a perturbed object)
+    templates = []
+    for k in range(args.serve_templates):
+        N, L = int(g.choice(Ns)), int(g.choice(Ls))
+        B = int(g.integers(8, 257))
+        pos = torch.from_numpy(g.uniform(0, side - N, (B, 2)).astype(np.float32)).to(dev)
+        p = dict(N=N, L=L, M=1, B=B, Lz=L, Ly=side, Lx=side, kdz=synth.KDZ_10NM,
+                 lambda_dz_over_px2=synth.LAMBDA_DZ_OVER_PX2_10NM, farfield=1, nf=[], loss="poisson", eps=1e-3)
+        td, tb, oid = vols[L]
+        I = torch.empty((B, N, N), dtype=torch.float32, device=dev)
+        eng.forward(p, oid, probes[N], pos, I)
+        I = torch.poisson(I * 1.05)
+        templates.append(dict(p=p, prob=Problem.of(p), oid=oid, pos=pos, I=I, units=B * L))
+    torch.cuda.synchronize()
+    budget = args.serve_budget_gb << 30
+    eng.serve_config(args.serve_slots, budget)
+    n = args.serve_requests
+    arrivals = np.cumsum(g.exponential(1.0 / args.serve_rate, n))
+    which = g.integers(0, len(templates), n)
+    # output buffers rotate over 2 x slots sets (results are not inspected here; the serving test
+    # checks them)
+    per_slot = [{L: (torch.zeros_like(vols[L][0]), torch.zeros_like(vols[L][1])) for L in Ls}
+                for _ in range(2 * args.serve_slots)]
+    gpos_buf = [torch.zeros((256, 2), dtype=torch.float32, device=dev) for _ in range(2 * args.serve_slots)]
+    loss_buf = [torch.zeros((), dtype=torch.float64, device=dev) for _ in range(2 * args.serve_slots)]
+    # warm the graphs of every template once
+    for t in templates:
+        gd, gb = per_slot[0][t["p"]["L"]]
+        tk = eng.submit(t["prob"], t["oid"], probes[t["p"]["N"]], t["pos"], t["I"], loss_buf[0], gd, gb, None,
+                        gpos_buf[0][:t["p"]["B"]])
+        eng.poll(tk, -1)
+    done_t = [0.0] * n
+    tickets = [None] * n
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i in range(n):
+            now = time.perf_counter() - t0
+            if arrivals[i] > now:
+                time.sleep(arrivals[i] - now)
+            t = templates[which[i]]
+            slot = i % len(per_slot)
+            gd, gb = per_slot[slot][t["p"]["L"]]
+            tickets[i] = eng.submit(t["prob"], t["oid"], probes[t["p"]["N"]], t["pos"], t["I"], loss_buf[slot], gd,
+                                    gb, None, gpos_buf[slot][:t["p"]["B"]])
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    for i in range(n):
+        while tickets[i] is None:
+            time.sleep(0.0001)
+        assert eng.poll(tickets[i], -1) == OK
+        done_t[i] = time.perf_counter() - t0
+    th.join()
+    lat = np.array(done_t) - arrivals
+    units = np.array([templates[w]["units"] for w in which])
+    span = done_t[-1] - arrivals[0]
+    # plain path: per-template service time (sub-batches of <= 32 positions to bound autograd memory)
+    svc = []
+    for t in templates:
+        td, tb, _ = vols[t["p"]["L"]]
+        d = td.clone().requires_grad_()
+        b = tb.clone().requires_grad_()
+        pr = probes[t["p"]["N"]].clone().requires_grad_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for rep in range(2):
+            s.record()
+            B = t["p"]["B"]
+            for c0 in range(0, B, 32):
+                c1 = min(B, c0 + 32)
+                pos = t["pos"][c0:c1].clone().requires_grad_()
+                loss, _ = plain_loss(d, b, pr, pos, t["I"][c0:c1], dict(t["p"], B=c1 - c0))
+                (loss * ((c1 - c0) / B)).backward()
+            e.record()
+            torch.cuda.synchronize()
+        svc.append(s.elapsed_time(e) / 1e3)
+        del d, b, pr
+        torch.cuda.empty_cache()
+    svc = np.array(svc)
+    fin, plat = 0.0, []
+    for i in range(n):
+        fin = max(arrivals[i], fin) + svc[which[i]]
+        plat.append(fin - arrivals[i])
+    plat = np.array(plat)
+    line = {"metric": "serving mix: loss+gradient requests, Poisson arrivals", "requests": n,
+            "rate_per_s": args.serve_rate, "slots": args.serve_slots, "budget_gb": args.serve_budget_gb,
+            "mix": "N in {64,128,256}, L in {1,8,32,64}, B in U{8..256}, Poisson loss, grads delta/beta/positions",
+            "volumes": f"{side}x{side}x{{1,8,32,64}} resident", "templates": len(templates),
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "throughput": float(units.sum() / span), "unit": UNIT,
+            "admission_waits": eng.serve_stats()[1],
+            "plain_one_at_a_time": {"p50_ms": float(np.percentile(plat, 50) * 1e3),
+                                    "p99_ms": float(np.percentile(plat, 99) * 1e3),
+                                    "throughput": float(units.sum() / (fin - arrivals[0])),
+                                    "how": "measured service time per template, replayed on the same arrivals"}}
+    print(json.dumps(line), flush=True)
+
+
 def profiled_traffic(src_hash: str):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary, if it was taken
     on the current kernel source (else null)."""
@@ -453,6 +575,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain torch GPU path")
+    ap.add_argument("--serve", action="store_true", help="run the serving mix instead of the minibatch benchmark")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=int, default=24)
+    ap.add_argument("--serve-templates", type=int, default=48)
+    ap.add_argument("--serve-side", type=int, default=1024)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -460,6 +589,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.serve:
+        if rank == 0:
+            run_serve(args)
         return
     if world > 1:
         import torch

@@ -97,6 +97,7 @@ int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan
     q.off_lossp = take(B * sizeof(double));
   }
   q.off_loss = take(sizeof(double));
+  q.off_box = take(4 * sizeof(int));
   {
     const size_t V = (size_t)p.Lz * p.Ly * p.Lx;
     q.off_T = take(V * f2);
@@ -192,14 +193,17 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
   const double cth = std::cos(p.theta), sth = std::sin(p.theta);
   int rc;
   float2* T = reinterpret_cast<float2*>(W(pl.off_T));
+  int* box = reinterpret_cast<int*>(W(pl.off_box));
+  if ((rc = chk(launch_bbox(c.pos, p.B, p.N, p.Ly, p.Lx, pl.far ? 1 : 0, pl.tomo ? 1 : 0, box, s), "bbox")))
+    return rc;
   if ((rc = chk(launch_transmission(obj.d, obj.b, T, p.Lz, p.Ly, p.Lx, (float)p.kdz, pl.tomo ? 1 : 0, (float)cth,
-                                    (float)sth, s),
+                                    (float)sth, box, s),
                 "transmission")))
     return rc;
   if (pl.want_obj) {
     // the scatter-add over overlapping positions is a reduction: accumulate it in FP64
     double* acc = reinterpret_cast<double*>(W(pl.off_grot));
-    if ((rc = chk(cudaMemsetAsync(acc, 0, 2 * V * sizeof(double), s), "memset"))) return rc;
+    if ((rc = chk(launch_zero_box(acc, acc + V, p.Lz, p.Ly, p.Lx, box, s), "zero"))) return rc;
     gd = acc;
     gb = acc + V;
   }
@@ -304,8 +308,10 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
     }
   }
   if (pl.want_obj) {
-    if (pl.tomo) rc = chk(launch_rotate_adj(gd, gb, c.gd, c.gb, p.Lz, p.Ly, p.Lx, (float)cth, (float)sth, s), "rotate_adj");
-    else rc = chk(launch_grad_add(gd, gb, c.gd, c.gb, V, s), "grad_add");
+    if (pl.tomo)
+      rc = chk(launch_rotate_adj(gd, gb, c.gd, c.gb, p.Lz, p.Ly, p.Lx, (float)cth, (float)sth, box, s), "rotate_adj");
+    else
+      rc = chk(launch_grad_add(gd, gb, c.gd, c.gb, p.Lz, p.Ly, p.Lx, box, s), "grad_add");
     if (rc) return rc;
   }
   return ADORYM_OK;

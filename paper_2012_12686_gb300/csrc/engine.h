@@ -34,6 +34,7 @@ struct Plan {
          off_lossp = 0, off_qacc = 0, off_qsum = 0, off_T = 0, off_grot = 0, off_loss = 0;
   // two-pass path (N >= 256)
   size_t off_FA = 0, off_FR = 0, off_tmp = 0, off_posp = 0;
+  size_t off_box = 0;   // int4 bounding box of the batch's patches
   // staging for host-memory arguments
   size_t off_s_probe = 0, off_s_pos = 0, off_s_meas = 0, off_s_gprobe = 0, off_s_gpos = 0, off_s_iout = 0;
   size_t bytes_probe = 0, bytes_pos = 0, bytes_meas = 0, bytes_iout = 0;

@@ -31,19 +31,86 @@ __device__ __forceinline__ Tap tap(int zt, int xt, int Lz, int Lx, float c, floa
   return t;
 }
 
-// T = exp(-kdz beta) exp(i kdz delta) of the (optionally rotated) volume, Eq. ri_modulation.
-// Computed once per call so the fused kernel gathers a complex64 per voxel instead of
-// evaluating sincos/exp for every (position, slice, pixel) it touches.
+// Region of the volume a call touches: rows / columns covered by the batch's patches (far field)
+// or the whole slab (near field), clamped to the volume, as box = {y0, y1, x0, x1}.  With
+// full_x the column range is the whole width (tomography: the rotation transpose mixes x and z).
+__global__ void __launch_bounds__(256) k_bbox(const float* __restrict__ pos, int B, int N, int Ly, int Lx, int far,
+                                              int full_x, int* __restrict__ box) {
+  __shared__ int red[4][8];
+  int y0 = 1 << 30, y1 = -(1 << 30), x0 = 1 << 30, x1 = -(1 << 30);
+  if (far) {
+    for (int b = threadIdx.x; b < B; b += 256) {
+      const int py = (int)floor((double)pos[2 * b] + 0.5), px = (int)floor((double)pos[2 * b + 1] + 0.5);
+      y0 = min(y0, py);
+      y1 = max(y1, py + N);
+      x0 = min(x0, px);
+      x1 = max(x1, px + N);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    y0 = min(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+    y1 = max(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+    x0 = min(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+    x1 = max(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][w] = y0;
+    red[1][w] = y1;
+    red[2][w] = x0;
+    red[3][w] = x1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < 8; ++i) {
+      y0 = min(y0, red[0][i]);
+      y1 = max(y1, red[1][i]);
+      x0 = min(x0, red[2][i]);
+      x1 = max(x1, red[3][i]);
+    }
+    if (!far) {
+      y0 = 0;
+      y1 = Ly;
+      x0 = 0;
+      x1 = Lx;
+    }
+    box[0] = max(0, y0);
+    box[1] = min(Ly, y1);
+    box[2] = full_x ? 0 : max(0, x0);
+    box[3] = full_x ? Lx : min(Lx, x1);
+  }
+}
+
+struct Region {
+  int y0, h, x0, w;
+  size_t n;   // Lz * h * w
+};
+
+__device__ __forceinline__ Region region(const int* __restrict__ box, int Lz) {
+  Region r;
+  r.y0 = box[0];
+  r.h = max(0, box[1] - box[0]);
+  r.x0 = box[2];
+  r.w = max(0, box[3] - box[2]);
+  r.n = (size_t)Lz * r.h * r.w;
+  return r;
+}
+
+// T = exp(-kdz beta) exp(i kdz delta) of the (optionally rotated) volume over the box, Eq.
+// ri_modulation.  Computed once per call so the fused kernels gather a complex64 per voxel
+// instead of evaluating sincos/exp for every (position, slice, pixel) they touch.
 template <bool ROT>
 __global__ void k_transmission(const float* __restrict__ vd, const float* __restrict__ vb, float2* __restrict__ T,
-                               int Lz, int Ly, int Lx, float kdz, float c, float s) {
-  const size_t n = (size_t)Lz * Ly * Lx;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+                               int Lz, int Ly, int Lx, float kdz, float c, float s, const int* __restrict__ box) {
+  const Region R = region(box, Lz);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n; i += (size_t)gridDim.x * blockDim.x) {
+    const int xt = R.x0 + (int)(i % R.w);
+    const int y = R.y0 + (int)((i / R.w) % R.h);
+    const int zt = (int)(i / ((size_t)R.w * R.h));
+    const size_t io = ((size_t)zt * Ly + y) * Lx + xt;
     float sd, sb;
     if (ROT) {
-      const int xt = (int)(i % Lx);
-      const int y = (int)((i / Lx) % Ly);
-      const int zt = (int)(i / ((size_t)Lx * Ly));
       const Tap t = tap(zt, xt, Lz, Lx, c, s);
       sd = 0.f;
       sb = 0.f;
@@ -60,24 +127,27 @@ __global__ void k_transmission(const float* __restrict__ vd, const float* __rest
         }
       }
     } else {
-      sd = __ldg(vd + i);
-      sb = __ldg(vb + i);
+      sd = __ldg(vd + io);
+      sb = __ldg(vb + io);
     }
     float sn, cs;
     sincosf(kdz * sd, &sn, &cs);
     const float e = expf(-kdz * sb);
-    T[i] = make_float2(e * cs, e * sn);
+    T[io] = make_float2(e * cs, e * sn);
   }
 }
 
+// transpose of the rotation: each unrotated node (z, y, x) with y in the box collects the
+// rotated-frame accumulators whose sample point lies within one pixel of it
 __global__ void k_rotate_adj(const double* __restrict__ gdr, const double* __restrict__ gbr, float* __restrict__ gd,
-                             float* __restrict__ gb, int Lz, int Ly, int Lx, float c, float s) {
-  const size_t n = (size_t)Lz * Ly * Lx;
+                             float* __restrict__ gb, int Lz, int Ly, int Lx, float c, float s,
+                             const int* __restrict__ box) {
+  const Region R = region(box, Lz);
   const float cx = 0.5f * (float)(Lx - 1), cz = 0.5f * (float)(Lz - 1);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % Lx);
-    const int y = (int)((i / Lx) % Ly);
-    const int z = (int)(i / ((size_t)Lx * Ly));
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n; i += (size_t)gridDim.x * blockDim.x) {
+    const int x = R.x0 + (int)(i % R.w);
+    const int y = R.y0 + (int)((i / R.w) % R.h);
+    const int z = (int)(i / ((size_t)R.w * R.h));
     // rotated-frame point that maps exactly onto this node (inverse rotation)
     const float u = (float)x - cx, w = (float)z - cz;
     const float xs = c * u + s * w + cx, zs = -s * u + c * w + cz;
@@ -100,42 +170,65 @@ __global__ void k_rotate_adj(const double* __restrict__ gdr, const double* __res
         ab = fma(wt, __ldg(gbr + o), ab);
       }
     }
-    gd[i] = (float)((double)gd[i] + ad);
-    gb[i] = (float)((double)gb[i] + ab);
+    const size_t io = ((size_t)z * Ly + y) * Lx + x;
+    gd[io] = (float)((double)gd[io] + ad);
+    gb[io] = (float)((double)gb[io] + ab);
   }
 }
 
+// FP64 object-gradient accumulators: zero the box, then add the box into the caller's gradient
+__global__ void k_zero_box(double* __restrict__ a, double* __restrict__ b, int Lz, int Ly, int Lx,
+                           const int* __restrict__ box) {
+  const Region R = region(box, Lz);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t io = ((size_t)(i / ((size_t)R.w * R.h)) * Ly + R.y0 + (i / R.w) % R.h) * Lx + R.x0 + i % R.w;
+    a[io] = 0.0;
+    b[io] = 0.0;
+  }
+}
+
+__global__ void k_grad_add(const double* __restrict__ ad, const double* __restrict__ ab, float* __restrict__ gd,
+                           float* __restrict__ gb, int Lz, int Ly, int Lx, const int* __restrict__ box) {
+  const Region R = region(box, Lz);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t io = ((size_t)(i / ((size_t)R.w * R.h)) * Ly + R.y0 + (i / R.w) % R.h) * Lx + R.x0 + i % R.w;
+    gd[io] = (float)((double)gd[io] + ad[io]);
+    gb[io] = (float)((double)gb[io] + ab[io]);
+  }
+}
+
+static unsigned vol_grid(size_t n) { return (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16); }
+
+cudaError_t launch_bbox(const float* pos, int B, int N, int Ly, int Lx, int far, int full_x, int* box, cudaStream_t s) {
+  k_bbox<<<1, 256, 0, s>>>(pos, B, N, Ly, Lx, far, full_x, box);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_transmission(const float* vd, const float* vb, float2* T, int Lz, int Ly, int Lx, float kdz,
-                                int rotate, float c, float sn, cudaStream_t s) {
-  const size_t n = (size_t)Lz * Ly * Lx;
-  const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
-  if (rotate) k_transmission<true><<<grid, 256, 0, s>>>(vd, vb, T, Lz, Ly, Lx, kdz, c, sn);
-  else k_transmission<false><<<grid, 256, 0, s>>>(vd, vb, T, Lz, Ly, Lx, kdz, c, sn);
+                                int rotate, float c, float sn, const int* box, cudaStream_t s) {
+  const unsigned grid = vol_grid((size_t)Lz * Ly * Lx);
+  if (rotate) k_transmission<true><<<grid, 256, 0, s>>>(vd, vb, T, Lz, Ly, Lx, kdz, c, sn, box);
+  else k_transmission<false><<<grid, 256, 0, s>>>(vd, vb, T, Lz, Ly, Lx, kdz, c, sn, box);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rotate_adj(const double* gdr, const double* gbr, float* gd, float* gb, int Lz, int Ly, int Lx,
-                              float c, float sn, cudaStream_t s) {
-  const size_t n = (size_t)Lz * Ly * Lx;
-  const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
-  k_rotate_adj<<<grid, 256, 0, s>>>(gdr, gbr, gd, gb, Lz, Ly, Lx, c, sn);
+                              float c, float sn, const int* box, cudaStream_t s) {
+  k_rotate_adj<<<vol_grid((size_t)Lz * Ly * Lx), 256, 0, s>>>(gdr, gbr, gd, gb, Lz, Ly, Lx, c, sn, box);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_box(double* a, double* b, int Lz, int Ly, int Lx, const int* box, cudaStream_t s) {
+  k_zero_box<<<vol_grid((size_t)Lz * Ly * Lx), 256, 0, s>>>(a, b, Lz, Ly, Lx, box);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_add(const double* ad, const double* ab, float* gd, float* gb, int Lz, int Ly, int Lx,
+                            const int* box, cudaStream_t s) {
+  k_grad_add<<<vol_grid((size_t)Lz * Ly * Lx), 256, 0, s>>>(ad, ab, gd, gb, Lz, Ly, Lx, box);
   return cudaGetLastError();
 }
 
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s) { return cudaMemsetAsync(p, 0, bytes, s); }
-
-__global__ void k_grad_add(const double* __restrict__ ad, const double* __restrict__ ab, float* __restrict__ gd,
-                           float* __restrict__ gb, size_t n) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    gd[i] = (float)((double)gd[i] + ad[i]);
-    gb[i] = (float)((double)gb[i] + ab[i]);
-  }
-}
-
-cudaError_t launch_grad_add(const double* ad, const double* ab, float* gd, float* gb, size_t n, cudaStream_t s) {
-  const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
-  k_grad_add<<<grid, 256, 0, s>>>(ad, ab, gd, gb, n);
-  return cudaGetLastError();
-}
 
 }  // namespace adorym

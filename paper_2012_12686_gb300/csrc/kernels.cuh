@@ -80,15 +80,20 @@ cudaError_t launch_path(const PathArgs& a, int farfield, cudaStream_t s);
 cudaError_t launch_probe_grad(int N, int M, int B, int farfield, const float2* qacc, float2* qsum, float2* g_probe,
                               const float2* tw, const double* lossp, double inv_npix, double* loss_out,
                               cudaStream_t s);
-// T = exp(-kdz beta) exp(i kdz delta) over a volume (Eq. ri_modulation), optionally after the
+// box = {y0, y1, x0, x1}: rows / columns of the volume the batch's patches touch (whole width if
+// full_x), computed on the device from the positions
+cudaError_t launch_bbox(const float* pos, int B, int N, int Ly, int Lx, int far, int full_x, int* box, cudaStream_t s);
+// T = exp(-kdz beta) exp(i kdz delta) over the box (Eq. ri_modulation), optionally after the
 // bilinear rotation of Eq. rotation_transform (rotate = 1)
 cudaError_t launch_transmission(const float* vd, const float* vb, float2* T, int Lz, int Ly, int Lx, float kdz,
-                                int rotate, float c, float sn, cudaStream_t s);
-// transpose of the rotation applied to the FP64 rotated-frame accumulators, added into gd/gb
+                                int rotate, float c, float sn, const int* box, cudaStream_t s);
+// transpose of the rotation applied to the FP64 rotated-frame accumulators, added into gd/gb (rows of the box)
 cudaError_t launch_rotate_adj(const double* gd_rot, const double* gb_rot, float* gd, float* gb, int Lz, int Ly,
-                              int Lx, float c, float sn, cudaStream_t s);
-// gd += (float) acc_d, gb += (float) acc_b over n voxels
-cudaError_t launch_grad_add(const double* acc_d, const double* acc_b, float* gd, float* gb, size_t n, cudaStream_t s);
+                              int Lx, float c, float sn, const int* box, cudaStream_t s);
+// FP64 accumulators: zero the box; add the box into the caller's FP32 gradient
+cudaError_t launch_zero_box(double* a, double* b, int Lz, int Ly, int Lx, const int* box, cudaStream_t s);
+cudaError_t launch_grad_add(const double* acc_d, const double* acc_b, float* gd, float* gb, int Lz, int Ly, int Lx,
+                            const int* box, cudaStream_t s);
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s);
 // qsum[i] = sum_b qacc[b][i] in FP64, fixed order
 cudaError_t launch_qsum(const float2* qacc, float2* qsum, int B, size_t MNN, cudaStream_t s);
