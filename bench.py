@@ -50,6 +50,18 @@ def bytes_per_unit(N: int, L: int, cp: int) -> float:
     return 8 * N * N + 16 * N * N + 16 * N * N / cp
 
 
+def twopass_bytes_per_unit(N: int, L: int, cp: int, nd: int, far: bool) -> float:
+    """Algorithmic HBM bytes per unit of the two-pass structure: every 2-D transform of an N x N
+    complex64 field in HBM needs two read+write passes (32 N^2 bytes).  Far field per (position,
+    slice): forward + adjoint propagation (4 transforms) + T gather (8 N^2) + checkpoint (16 N^2 /
+    cp).  Near field per hologram: the exit-wave transform and the final inverse shared by nd
+    holograms, one inverse and one forward transform per hologram, I_meas read (4 N^2), T and the
+    object-gradient update per slice shared by nd."""
+    if far:
+        return 4 * 32 * N * N + 8 * N * N + 16 * N * N / cp
+    return (2 * 32 * N * N) / nd + 2 * 32 * N * N + 4 * N * N + L * (8 + 16) * N * N / nd
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -300,13 +312,15 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(dev)
-    w = synth.workload(WORKLOAD, seed=0)
+    w = synth.workload(args.workload, seed=0)
     p = w["problem"]
     N, L, B, M = p["N"], p["L"], p["B"], p["M"]
+    far = bool(p["farfield"])
+    nd = 1 if far else len(p["nf"])
     cp = p["checkpoint_every"] or int(math.ceil(math.sqrt(L)))
-    all_pos = w["all_pos"]
-    nb = len(all_pos) // B
-    units = B * L * M
+    all_pos = w.get("all_pos", w["pos"])
+    nb = max(1, len(all_pos) // B)
+    units = B * L * M if far else B * nd          # near field: one hologram distance is one unit
     with torch.cuda.stream(stream):
         d = torch.from_numpy(w["delta"]).to(dev)
         b = torch.from_numpy(w["beta"]).to(dev)
@@ -319,17 +333,19 @@ def run_ours(args, rank, world, local_rank):
         oid_m = eng.register_object(dm, bm)
         prob = Problem.of(p)
         # measured data of the epoch: forward model of the second object + Poisson noise
-        I_meas = torch.empty((nb, B, N, N), dtype=torch.float32, device=dev)
+        shape = (nb, B, N, N) if far else (nb, B, nd, N, N)
+        I_meas = torch.empty(shape, dtype=torch.float32, device=dev)
         for k in range(nb):
             eng.forward(prob, oid_m, probe, pos_all[k * B:(k + 1) * B].contiguous(), I_meas[k])
         gen = torch.Generator(device=dev)
         gen.manual_seed(1234)
-        I_meas = torch.poisson(I_meas, generator=gen)
+        ph = float(w.get("photons", 1.0))
+        I_meas = torch.poisson(I_meas * ph, generator=gen) / ph
         pos_b = [pos_all[k * B:(k + 1) * B].contiguous() for k in range(nb)]
         loss = torch.zeros((), dtype=torch.float64, device=dev)
         gd, gb = torch.zeros_like(d), torch.zeros_like(b)
         gp = torch.zeros_like(probe)
-        gpos = torch.zeros((B, 2), dtype=torch.float32, device=dev)
+        gpos = torch.zeros(tuple(pos_all[:B].shape), dtype=torch.float32, device=dev)
         flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
         eng.enable_kernel_timing(True)
 
@@ -363,7 +379,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- the plain unfused GPU path on the same minibatches (comparison arm of the metric)
     plain = None
-    if not args.no_plain:
+    if not args.no_plain and far:
         pt = time_plain(w, dev, pos_b, I_meas, steps=min(args.steps, 20), warmup=3)
         ps = sorted(pt)
         plain = {"value": units / (statistics.mean(pt) / 1e3), "unit": UNIT, "ms_per_step": statistics.mean(pt),
@@ -377,7 +393,7 @@ def run_ours(args, rank, world, local_rank):
     h_probe = probe.cpu().pin_memory()
     h_loss = np.zeros(1, np.float64)
     h_gp = torch.zeros(probe.shape, dtype=torch.complex64).pin_memory()
-    h_gpos = torch.zeros((B, 2), dtype=torch.float32).pin_memory()
+    h_gpos = torch.zeros(tuple(pos_all[:B].shape), dtype=torch.float32).pin_memory()
     eng.enable_kernel_timing(False)
     with torch.cuda.stream(stream):
         for k in range(2):
@@ -398,7 +414,18 @@ def run_ours(args, rank, world, local_rank):
     sm_max = (peaks.get("sm_max_mhz") or 2070.0)
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     k_ms = statistics.mean(path_ms)
-    achieved = units * flops_per_unit(N) / (k_ms * 1e-3) / 1e12
+    if far and N <= 128:
+        achieved = units * flops_per_unit(N) / (k_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "kernel": f"k_path<{N},far>"}
+    else:
+        # two-pass / near field: HBM-bound; algorithmic bytes of the minimal pass structure
+        bpu = twopass_bytes_per_unit(N, L, cp, nd, far)
+        achieved = units * bpu / (k_ms * 1e-3) / 1e9
+        hpk = peaks.get("hbm_gbs", 6795.5)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hpk, "unit": "GB/s", "frac": achieved / hpk,
+                "kernel": "k_row/k_col two-pass sequence" if N >= 256 else f"k_path<{N},near>",
+                "bytes_per_unit": bpu}
     hbm_ach = units * bytes_per_unit(N, L, cp) / (k_ms * 1e-3) / 1e9
     src = open(os.path.join(ROOT, "paper_2012_12686_gb300", "csrc", "k_path.cu"), "rb").read() + \
         open(os.path.join(ROOT, "paper_2012_12686_gb300", "csrc", "fft_block.cuh"), "rb").read()
@@ -411,17 +438,18 @@ def run_ours(args, rank, world, local_rank):
             "latency_ms": {"p50": p50, "p99": p99},
             "gpu_launches": 4 * args.steps,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp32_peak, "traffic": traffic,
-                         "kernel": "k_path<128,far>", "kernel_ms": k_ms,
-                         "peak_note": f"FP32 FMA peak derived: {props.multi_processor_count} SMs x 128 lanes x 2 "
-                                      f"x {sm_max:.0f} MHz",
-                         "hbm_algorithmic_gbs": hbm_ach, "hbm_peak_gbs": peaks.get("hbm_gbs", 6795.5)},
+            "roofline": dict(roof, traffic=traffic if args.workload == WORKLOAD else None, kernel_ms=k_ms,
+                             peak_note=(f"FP32 FMA peak derived: {props.multi_processor_count} SMs x 128 lanes x 2 "
+                                        f"x {sm_max:.0f} MHz" if roof["bound"] == "alu" else
+                                        "measured copy bandwidth (MEASURED_PEAKS.json)"),
+                             hbm_algorithmic_gbs=hbm_ach, hbm_peak_gbs=peaks.get("hbm_gbs", 6795.5)),
             "clocks": clk.summary(), "wall_s_timed": wall}
     if plain is not None:
         plain["speedup_of_fused"] = value / plain["value"]
         line["plain_gpu"] = plain
-    if not args.no_cpu_baseline and world == 1:
+    if args.workload != WORKLOAD:
+        line["config"]["workload"] = args.workload
+    if not args.no_cpu_baseline and world == 1 and args.workload == WORKLOAD:
         cores = os.cpu_count() or 1
         n_pos = min(8 * cores, len(all_pos))
         Im_np = I_meas.reshape(-1, N, N)[:n_pos].cpu().numpy()
@@ -575,6 +603,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain torch GPU path")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["multislice", "ptycho2d", "tomo", "holo"],
+                    help="workload of the timed steps (default: the metric's multislice configuration)")
     ap.add_argument("--serve", action="store_true", help="run the serving mix instead of the minibatch benchmark")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
