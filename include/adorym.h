@@ -124,6 +124,23 @@ int adorym_loss_grad(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const
                      const float* I_meas, double* loss_out, float* g_delta, float* g_beta, float* g_probe,
                      float* g_pos, float* I_out);
 
+/* Outputs of adorym_loss_grad_ext (NULL members are skipped). */
+typedef struct adorym_grads {
+  double* loss;     /* one double (host or device), overwritten                                  */
+  float* g_delta;   /* device FP32 [Lz][Ly][Lx], added (+=)                                      */
+  float* g_beta;
+  float* g_probe;   /* complex [M][N][N], added                                                  */
+  float* g_pos;     /* far [B][2] / near [B][n_dist][2], overwritten                              */
+  float* g_nf;      /* near field only: [B][n_dist] dL/dN_F, the gradient w.r.t. each problem's
+                       Fresnel numbers (free-propagation distance refinement, Sec. 2.3.2;
+                       N_F = dx^2 / (lambda z), so dL/dz = -dL/dN_F * N_F / z), overwritten   */
+  float* I_out;     /* predicted intensities, overwritten                                        */
+} adorym_grads;
+
+/* adorym_loss_grad with its outputs in a struct, including the near-field distance gradient. */
+int adorym_loss_grad_ext(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const float* probe, const float* pos,
+                         const float* I_meas, const adorym_grads* out);
+
 /* A loss/gradient request for the serving loop: the arguments of adorym_loss_grad. */
 typedef struct adorym_request {
   adorym_problem problem;

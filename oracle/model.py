@@ -299,10 +299,12 @@ def loss(problem, delta, beta, probe, pos, I_meas):
     return float(np.mean(loss_terms(I, I_meas, pb.loss, pb.eps)))
 
 
-def loss_grad(problem, delta, beta, probe, pos, I_meas):
+def loss_grad(problem, delta, beta, probe, pos, I_meas, want_nf=False):
     """Loss and its gradients w.r.t. delta, beta (volume frame), probe and positions/shifts.
 
-    Returns (loss, g_delta, g_beta, g_probe, g_pos) in FP64 / complex128.
+    Returns (loss, g_delta, g_beta, g_probe, g_pos) in FP64 / complex128; with want_nf (near
+    field) also g_nf [B, n_dist], the gradient w.r.t. each problem's Fresnel numbers (the
+    free-propagation distance refinement of Sec. 2.3.2: N_F = dx^2 / (lambda z)).
     """
     pb = problem if isinstance(problem, Problem) else Problem.of(problem)
     d, b = _object_frames(pb, delta, beta)
@@ -339,6 +341,8 @@ def loss_grad(problem, delta, beta, probe, pos, I_meas):
         shifts = np.asarray(pos, np.float64)
         f = freq(N)
         g_pos = np.zeros((pb.B, nd, 2))
+        g_nf = np.zeros((pb.B, nd))
+        f2 = f[:, None] ** 2 + f[None, :] ** 2
         for i in range(pb.B):
             Psi, Phi, G, T, psis = _nearfield_problem(pb, d, b, probe, i, shifts[i])
             I = np.sum(np.abs(Psi) ** 2, axis=1)                 # [n_dist, N, N]
@@ -351,6 +355,8 @@ def loss_grad(problem, delta, beta, probe, pos, I_meas):
                 base = np.conj(Q) * Phi * G[di]
                 g_pos[i, di, 0] = np.real(np.sum(base * (-2j * np.pi * f[:, None]))) / (N * N)
                 g_pos[i, di, 1] = np.real(np.sum(base * (-2j * np.pi * f[None, :]))) / (N * N)
+                # dH_d/dN_F = -i pi |f|^2 / N_F^2 H_d (Eq. paraxial_kernel with lambda z / dx^2 = 1 / N_F)
+                g_nf[i, di] = np.real(np.sum(base * (-1j * np.pi * f2 / pb.nf[di] ** 2))) / (N * N)
             phibar = idft_minus(Phibar_sum)
             psibar0, gd, gb = _multislice_T(pb, T, psis, phibar, pb.kdz)
             gvd[i * pb.L:(i + 1) * pb.L] += gd
@@ -358,4 +364,8 @@ def loss_grad(problem, delta, beta, probe, pos, I_meas):
             g_probe += psibar0
     if pb.tomo:
         gvd, gvb = rotate_T(gvd, pb.theta), rotate_T(gvb, pb.theta)
+    if want_nf:
+        if pb.farfield:
+            raise ValueError("Fresnel-number gradients are defined for the near-field geometry")
+        return total / npix, gvd, gvb, g_probe, g_pos, g_nf
     return total / npix, gvd, gvb, g_probe, g_pos

@@ -21,7 +21,7 @@ LOSS = {"lsq": 0, "poisson": 1}
 EXPORTS = ["adorym_create", "adorym_destroy", "adorym_last_error", "adorym_register_object",
            "adorym_unregister_object", "adorym_forward", "adorym_loss_grad", "adorym_submit", "adorym_poll",
            "adorym_serve_config", "adorym_serve_stats", "adorym_workspace_bytes", "adorym_enable_kernel_timing",
-           "adorym_kernel_ms", "adorym_loss_grad_noalloc"]
+           "adorym_kernel_ms", "adorym_loss_grad_noalloc", "adorym_loss_grad_ext"]
 
 
 class Problem(ctypes.Structure):
@@ -51,6 +51,12 @@ class Problem(ctypes.Structure):
         p.theta = float(d.get("theta", 0.0))
         p.checkpoint_every = int(d.get("checkpoint_every", 0))
         return p
+
+
+class Grads(ctypes.Structure):
+    _fields_ = [("loss", ctypes.c_void_p), ("g_delta", ctypes.c_void_p), ("g_beta", ctypes.c_void_p),
+                ("g_probe", ctypes.c_void_p), ("g_pos", ctypes.c_void_p), ("g_nf", ctypes.c_void_p),
+                ("I_out", ctypes.c_void_p)]
 
 
 class Request(ctypes.Structure):
@@ -87,6 +93,7 @@ def lib() -> ctypes.CDLL:
         L.adorym_workspace_bytes.argtypes = [ctypes.POINTER(Problem), i32, ctypes.POINTER(u64)]
         L.adorym_enable_kernel_timing.argtypes = [vp, i32]
         L.adorym_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+        L.adorym_loss_grad_ext.argtypes = [vp, ctypes.POINTER(Problem), i32, vp, vp, vp, ctypes.POINTER(Grads)]
         L.adorym_loss_grad_noalloc.argtypes = [vp, ctypes.POINTER(Problem), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("adorym_destroy", "adorym_last_error"):
@@ -169,6 +176,17 @@ class Engine:
         return self._check(lib().adorym_loss_grad(self._ctx, ctypes.byref(p), obj_id, _ptr(probe), _ptr(pos),
                                                   _ptr(I_meas), _ptr(loss_out), _ptr(g_delta), _ptr(g_beta),
                                                   _ptr(g_probe), _ptr(g_pos), _ptr(I_out)))
+
+    def loss_grad_ext(self, problem, obj_id, probe, pos, I_meas, loss_out=None, g_delta=None, g_beta=None,
+                      g_probe=None, g_pos=None, g_nf=None, I_out=None):
+        """adorym_loss_grad_ext: as loss_grad, plus g_nf (near field: dL/dN_F per problem and distance)."""
+        p = problem if isinstance(problem, Problem) else Problem.of(problem)
+        g = Grads()
+        for k, v in (("loss", loss_out), ("g_delta", g_delta), ("g_beta", g_beta), ("g_probe", g_probe),
+                     ("g_pos", g_pos), ("g_nf", g_nf), ("I_out", I_out)):
+            setattr(g, k, _ptr(v))
+        return self._check(lib().adorym_loss_grad_ext(self._ctx, ctypes.byref(p), obj_id, _ptr(probe), _ptr(pos),
+                                                      _ptr(I_meas), ctypes.byref(g)))
 
     def enable_kernel_timing(self, on: bool = True):
         self._check(lib().adorym_enable_kernel_timing(self._ctx, 1 if on else 0))

@@ -55,6 +55,7 @@ int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan
   q.want_obj = adj && (grads & 1);
   q.want_probe = adj && (grads & 2);
   q.want_pos = adj && (grads & 4);
+  q.want_nf = adj && (grads & 8) && !p.farfield;
   q.want_loss = want_loss;
   q.nd = q.far ? 1 : p.n_dist;
   q.cp = p.checkpoint_every > 0 ? p.checkpoint_every : (int)std::ceil(std::sqrt((double)p.L));
@@ -77,7 +78,7 @@ int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan
       q.off_seg = take(B * M * q.cp * NN * f2);
       q.off_qacc = take(B * M * NN * f2);
       q.off_qsum = take(M * NN * f2);
-      q.off_posp = take(B * q.nd * (N / (N == 256 ? 64 : N == 512 ? 32 : 16)) * 2 * sizeof(double));
+      q.off_posp = take(B * q.nd * (N / (N == 256 ? 64 : N == 512 ? 32 : 16)) * 3 * sizeof(double));
     }
     q.off_tmp = take(M * NN * f2);
     q.off_far = take(B * (q.far ? 1 : q.nd + 1) * M * NN * f2);
@@ -113,6 +114,7 @@ int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan
   q.off_s_gprobe = take(q.bytes_probe);
   q.off_s_gpos = take(q.bytes_pos);
   q.off_s_iout = take(q.bytes_iout);
+  q.off_s_gnf = take(B * q.nd * sizeof(float));
   q.total = o;
   *pl = q;
   return ADORYM_OK;
@@ -247,7 +249,9 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
       t.seg = reinterpret_cast<float2*>(W(pl.off_seg));
       t.qacc = pl.want_probe ? reinterpret_cast<float2*>(W(pl.off_qacc)) : nullptr;
       t.qsum = reinterpret_cast<float2*>(W(pl.off_qsum));
-      t.posp = pl.want_pos ? reinterpret_cast<double*>(W(pl.off_posp)) : nullptr;
+      t.posp = (pl.want_pos || pl.want_nf) ? reinterpret_cast<double*>(W(pl.off_posp)) : nullptr;
+      t.gnf = pl.want_nf ? c.g_nf : nullptr;
+      for (int d = 0; d < 4; ++d) t.nf[d] = p.nf[d];
       t.gd = pl.want_obj ? gd : nullptr;
       t.gb = pl.want_obj ? gb : nullptr;
       t.gpos = pl.want_pos ? c.g_pos : nullptr;
@@ -293,6 +297,8 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
       a.gd = pl.want_obj ? gd : nullptr;
       a.gb = pl.want_obj ? gb : nullptr;
       a.gpos = pl.want_pos ? c.g_pos : nullptr;
+      a.gnf = pl.want_nf ? c.g_nf : nullptr;
+      for (int d = 0; d < 4; ++d) a.nf[d] = p.nf[d];
     }
     a.far = reinterpret_cast<float2*>(W(pl.off_far));
     a.gI = reinterpret_cast<float*>(W(pl.off_gI));
@@ -439,7 +445,7 @@ int adorym_workspace_bytes(const adorym_problem* p, int grads, uint64_t* bytes) 
 
 static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const float* probe, const float* pos,
                     const float* I_meas, double* loss_out, float* g_delta, float* g_beta, float* g_probe,
-                    float* g_pos, float* I_out, bool adj) {
+                    float* g_pos, float* I_out, bool adj, float* g_nf = nullptr) {
   if (!ctx) return ADORYM_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (!p) return fail(ctx, ADORYM_EINVAL, "null problem");
@@ -455,7 +461,8 @@ static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const 
     return fail(ctx, ADORYM_EINVAL, "problem Lz/Ly/Lx differ from the registered object");
   if (g_delta && (ptr_kind(g_delta) != 1 || ptr_kind(g_beta) != 1))
     return fail(ctx, ADORYM_EINVAL, "g_delta / g_beta must be device memory");
-  const int grads = (g_delta ? 1 : 0) | (g_probe ? 2 : 0) | (g_pos ? 4 : 0);
+  const int grads = (g_delta ? 1 : 0) | (g_probe ? 2 : 0) | (g_pos ? 4 : 0) | (g_nf ? 8 : 0);
+  if (g_nf && p->farfield) return fail(ctx, ADORYM_EINVAL, "g_nf is defined for the near-field geometry only");
   Plan pl;
   const char* msg = "";
   int rc = make_plan(*p, adj, grads, loss_out != nullptr, &pl, &msg);
@@ -484,6 +491,8 @@ static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const 
   const bool host_gprobe = g_probe && ptr_kind(g_probe) == 0;
   const bool host_gpos = g_pos && ptr_kind(g_pos) == 0;
   const bool host_iout = I_out && ptr_kind(I_out) == 0;
+  const bool host_gnf = g_nf && ptr_kind(g_nf) == 0;
+  if (g_nf) c.g_nf = host_gnf ? reinterpret_cast<float*>(ws + pl.off_s_gnf) : g_nf;
   c.loss = loss_out ? (host_loss ? reinterpret_cast<double*>(ws + pl.off_loss) : loss_out) : nullptr;
   if (g_probe) {
     if (host_gprobe) {
@@ -516,6 +525,10 @@ static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const 
   }
   if (host_iout) {
     cudaMemcpyAsync(I_out, c.I_out, pl.bytes_iout, cudaMemcpyDeviceToHost, s);
+    sync_after = true;
+  }
+  if (host_gnf) {
+    cudaMemcpyAsync(g_nf, c.g_nf, (size_t)p->B * pl.nd * sizeof(float), cudaMemcpyDeviceToHost, s);
     sync_after = true;
   }
   cudaError_t e = cudaGetLastError();
@@ -553,6 +566,14 @@ int adorym_loss_grad(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const
                      const float* I_meas, double* loss_out, float* g_delta, float* g_beta, float* g_probe,
                      float* g_pos, float* I_out) {
   return run_call(ctx, p, obj_id, probe, pos, I_meas, loss_out, g_delta, g_beta, g_probe, g_pos, I_out, true);
+}
+
+int adorym_loss_grad_ext(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const float* probe, const float* pos,
+                         const float* I_meas, const adorym_grads* out) {
+  if (!out) return run_call(ctx, p, obj_id, probe, pos, I_meas, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                            true);
+  return run_call(ctx, p, obj_id, probe, pos, I_meas, out->loss, out->g_delta, out->g_beta, out->g_probe, out->g_pos,
+                  out->I_out, true, out->g_nf);
 }
 
 }  // extern "C"

@@ -28,7 +28,7 @@ struct Plan {
   adorym_problem p{};
   int cp = 1, ncp = 1, nd = 1;
   bool far = true, tomo = false, adj = false;
-  bool want_obj = false, want_probe = false, want_pos = false, want_loss = false;
+  bool want_obj = false, want_probe = false, want_pos = false, want_loss = false, want_nf = false;
   size_t NN = 0;
   size_t off_phat = 0, off_ckpt = 0, off_seg = 0, off_park = 0, off_far = 0, off_gI = 0, off_fbar = 0,
          off_lossp = 0, off_qacc = 0, off_qsum = 0, off_T = 0, off_grot = 0, off_loss = 0;
@@ -36,7 +36,8 @@ struct Plan {
   size_t off_FA = 0, off_FR = 0, off_tmp = 0, off_posp = 0;
   size_t off_box = 0;   // int4 bounding box of the batch's patches
   // staging for host-memory arguments
-  size_t off_s_probe = 0, off_s_pos = 0, off_s_meas = 0, off_s_gprobe = 0, off_s_gpos = 0, off_s_iout = 0;
+  size_t off_s_probe = 0, off_s_pos = 0, off_s_meas = 0, off_s_gprobe = 0, off_s_gpos = 0, off_s_iout = 0,
+         off_s_gnf = 0;
   size_t bytes_probe = 0, bytes_pos = 0, bytes_meas = 0, bytes_iout = 0;
   size_t total = 0;
 };
@@ -51,6 +52,7 @@ struct CallPtrs {
   float* gb = nullptr;
   float2* g_probe = nullptr;
   float* g_pos = nullptr;
+  float* g_nf = nullptr;
   float* I_out = nullptr;
 };
 

@@ -151,27 +151,57 @@ struct NoPre {
   __device__ __forceinline__ void operator()(float2 (&)[R], float2 (&)[R], int, int) const {}
 };
 
+// Every pass below gives each thread TPT = ceil(tasks / NT) tasks and processes them in three
+// phases -- issue all loads, compute, issue all stores -- so a warp keeps several shared/global
+// loads in flight instead of waiting on each task in turn (the tasks of a pass touch disjoint
+// slots, so reordering them within a thread is safe).
+template <int TASKS, int NT>
+struct Tpt {
+  static constexpr int n = (TASKS + NT - 1) / NT;
+  __device__ static __forceinline__ bool ok(int tau) { return TASKS % NT == 0 || tau < TASKS; }
+};
+
 template <int N, int S4, int S1, bool LOAD, bool STORE, class Pre, class Op>
 __device__ __forceinline__ void pass_c14(float2* __restrict__ A, const float2* __restrict__ tw, Pre pre, Op op) {
   using F = Field<N>;
   constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD;
-  for (int tau = threadIdx.x; tau < N * N2; tau += F::NT) {
-    const int x = tau % N, t = tau / N;
-    float2 pa[N1], pb[N1], v[N1];
-    pre(pa, pb, x, t);
-    if (LOAD) {
+  using P = Tpt<N * N2, F::NT>;
+  // the spatial pass keeps three register arrays per task; phase its tasks only when they fit
+  constexpr int Q = (F::NT <= 512) ? P::n : 1;
+  for (int q0 = 0; q0 < P::n; q0 += Q) {
+    float2 pa[Q][N1], pb[Q][N1], v[Q][N1];
 #pragma unroll
-      for (int i = 0; i < N1; ++i) v[i] = A[(N2 * i + t) * LD + x];
-      if (S4) dft<N1, S4>(v);
-    }
-    op(v, pa, pb, x, t);
-    if (STORE) {
-      if (S1) {
-        dft<N1, S1>(v);
-        twiddle<S1>(v, tw, t);
+    for (int q = 0; q < Q; ++q) {
+      const int tau = threadIdx.x + (q0 + q) * F::NT;
+      if (!P::ok(tau)) continue;
+      const int x = tau % N, t = tau / N;
+      pre(pa[q], pb[q], x, t);
+      if (LOAD) {
+#pragma unroll
+        for (int i = 0; i < N1; ++i) v[q][i] = A[(N2 * i + t) * LD + x];
       }
+    }
 #pragma unroll
-      for (int i = 0; i < N1; ++i) A[(N2 * i + t) * LD + x] = v[i];
+    for (int q = 0; q < Q; ++q) {
+      const int tau = threadIdx.x + (q0 + q) * F::NT;
+      if (!P::ok(tau)) continue;
+      const int x = tau % N, t = tau / N;
+      if (LOAD && S4) dft<N1, S4>(v[q]);
+      op(v[q], pa[q], pb[q], x, t);
+      if (STORE && S1) {
+        dft<N1, S1>(v[q]);
+        twiddle<S1>(v[q], tw, t);
+      }
+    }
+    if (STORE) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int tau = threadIdx.x + (q0 + q) * F::NT;
+        if (!P::ok(tau)) continue;
+        const int x = tau % N, t = tau / N;
+#pragma unroll
+        for (int i = 0; i < N1; ++i) A[(N2 * i + t) * LD + x] = v[q][i];
+      }
     }
   }
 }
@@ -181,15 +211,31 @@ template <int N, bool IS_S3, int S>
 __device__ __noinline__ void pass_c23(float2* __restrict__ A, const float2* __restrict__ tw) {
   using F = Field<N>;
   constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD;
-  for (int tau = threadIdx.x; tau < N * N1; tau += F::NT) {
+  using P = Tpt<N * N1, F::NT>;
+  float2 v[P::n][N2];
+#pragma unroll
+  for (int q = 0; q < P::n; ++q) {
+    const int tau = threadIdx.x + q * F::NT;
+    if (!P::ok(tau)) continue;
     const int x = tau % N, t = tau / N;
-    float2 v[N2];
 #pragma unroll
-    for (int i = 0; i < N2; ++i) v[i] = A[(N2 * t + i) * LD + x];
-    dft<N2, S>(v);
-    if (IS_S3) twiddle<S>(v, tw, t);
+    for (int i = 0; i < N2; ++i) v[q][i] = A[(N2 * t + i) * LD + x];
+  }
 #pragma unroll
-    for (int i = 0; i < N2; ++i) A[(N2 * t + i) * LD + x] = v[i];
+  for (int q = 0; q < P::n; ++q) {
+    const int tau = threadIdx.x + q * F::NT;
+    if (!P::ok(tau)) continue;
+    const int t = tau / N;
+    dft<N2, S>(v[q]);
+    if (IS_S3) twiddle<S>(v[q], tw, t);
+  }
+#pragma unroll
+  for (int q = 0; q < P::n; ++q) {
+    const int tau = threadIdx.x + q * F::NT;
+    if (!P::ok(tau)) continue;
+    const int x = tau % N, t = tau / N;
+#pragma unroll
+    for (int i = 0; i < N2; ++i) A[(N2 * t + i) * LD + x] = v[q][i];
   }
 }
 
@@ -198,15 +244,31 @@ template <int N, bool IS_S1, int S>
 __device__ __noinline__ void pass_r14(float2* __restrict__ A, const float2* __restrict__ tw) {
   using F = Field<N>;
   constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD;
-  for (int tau = threadIdx.x; tau < N * N2; tau += F::NT) {
+  using P = Tpt<N * N2, F::NT>;
+  float2 v[P::n][N1];
+#pragma unroll
+  for (int q = 0; q < P::n; ++q) {
+    const int tau = threadIdx.x + q * F::NT;
+    if (!P::ok(tau)) continue;
     const int r = tau % N, t = tau / N;
-    float2 v[N1];
 #pragma unroll
-    for (int i = 0; i < N1; ++i) v[i] = A[r * LD + N2 * i + t];
-    dft<N1, S>(v);
-    if (IS_S1) twiddle<S>(v, tw, t);
+    for (int i = 0; i < N1; ++i) v[q][i] = A[r * LD + N2 * i + t];
+  }
 #pragma unroll
-    for (int i = 0; i < N1; ++i) A[r * LD + N2 * i + t] = v[i];
+  for (int q = 0; q < P::n; ++q) {
+    const int tau = threadIdx.x + q * F::NT;
+    if (!P::ok(tau)) continue;
+    const int t = tau / N;
+    dft<N1, S>(v[q]);
+    if (IS_S1) twiddle<S>(v[q], tw, t);
+  }
+#pragma unroll
+  for (int q = 0; q < P::n; ++q) {
+    const int tau = threadIdx.x + q * F::NT;
+    if (!P::ok(tau)) continue;
+    const int r = tau % N, t = tau / N;
+#pragma unroll
+    for (int i = 0; i < N1; ++i) A[r * LD + N2 * i + t] = v[q][i];
   }
 }
 
@@ -218,21 +280,38 @@ template <int N, int S2, int S3, class Op>
 __device__ __forceinline__ void pass_r23(float2* __restrict__ A, const float2* __restrict__ tw, Op op) {
   using F = Field<N>;
   constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD;
-  for (int tau = threadIdx.x; tau < N * N1; tau += F::NT) {
-    const int r = tau % N, t = tau / N;
-    const int ky = F::row_freq(r);
-    float2 v[N2];
-    if (S2) {
+  using P = Tpt<N * N1, F::NT>;
+  float2 v[P::n][N2];
+  if (S2) {
 #pragma unroll
-      for (int i = 0; i < N2; ++i) v[i] = A[r * LD + N2 * t + i];
-      dft<N2, S2>(v);
+    for (int q = 0; q < P::n; ++q) {
+      const int tau = threadIdx.x + q * F::NT;
+      if (!P::ok(tau)) continue;
+      const int r = tau % N, t = tau / N;
+#pragma unroll
+      for (int i = 0; i < N2; ++i) v[q][i] = A[r * LD + N2 * t + i];
     }
-    op(v, ky, t);
-    if (S3) {
-      dft<N2, S3>(v);
-      twiddle<S3>(v, tw, t);
+  }
 #pragma unroll
-      for (int i = 0; i < N2; ++i) A[r * LD + N2 * t + i] = v[i];
+  for (int q = 0; q < P::n; ++q) {
+    const int tau = threadIdx.x + q * F::NT;
+    if (!P::ok(tau)) continue;
+    const int r = tau % N, t = tau / N;
+    if (S2) dft<N2, S2>(v[q]);
+    op(v[q], F::row_freq(r), t);
+    if (S3) {
+      dft<N2, S3>(v[q]);
+      twiddle<S3>(v[q], tw, t);
+    }
+  }
+  if (S3) {
+#pragma unroll
+    for (int q = 0; q < P::n; ++q) {
+      const int tau = threadIdx.x + q * F::NT;
+      if (!P::ok(tau)) continue;
+      const int r = tau % N, t = tau / N;
+#pragma unroll
+      for (int i = 0; i < N2; ++i) A[r * LD + N2 * t + i] = v[q][i];
     }
   }
 }

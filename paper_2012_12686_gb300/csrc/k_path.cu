@@ -41,14 +41,17 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;   // valid on thread 0
 }
 
-__device__ __forceinline__ double freqd(int k, int N) { return (double)(k <= (N - 1) / 2 ? k : k - N) / (double)N; }
+__device__ __forceinline__ double freqd(int k, int N) { return (double)(k <= (N - 1) / 2 ? k : k - N) * (1.0 / (double)N); }
 
-// exp(-2 pi i d f_k) for k < N into out (FP64 argument, rounded once)
+// exp(-2 pi i d f_k) for k < N into out: argument formed and reduced to [-1, 1] (units of pi) in
+// FP64, evaluated in FP32
 __device__ __forceinline__ void ramp_table(float2* out, double d, int N, int NT) {
   for (int k = threadIdx.x; k < N; k += NT) {
-    double s, c;
-    sincospi(-2.0 * d * freqd(k, N), &s, &c);
-    out[k] = make_float2((float)c, (float)s);
+    double ph = -2.0 * d * freqd(k, N);
+    ph -= 2.0 * rint(0.5 * ph);
+    float s, c;
+    sincospif((float)ph, &s, &c);
+    out[k] = make_float2(c, s);
   }
 }
 
@@ -289,7 +292,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
   __syncthreads();
 
   // ------------------------------------------------------------------ adjoint
-  double gacc[2 * 4] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double gacc[3 * 4] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};   // per distance: shift y, x; N_F
   const bool want_obj = a.gd != nullptr;
   for (int m = 0; m < M; ++m) {
     float2* ck = ck_b + (size_t)m * ncp * NN;
@@ -341,19 +344,22 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
         pass_r23<N, -1, 0>(A, tw, [&](V2& v, int ky, int t) {
           const float2 gy = cmul(__ldg(&hd[ky]), ry[ky]);
           const float fyk = (float)freqd(ky, N);
-          float ay = 0.f, ax = 0.f;
+          float ay = 0.f, ax = 0.f, an = 0.f;
 #pragma unroll
           for (int i = 0; i < N2; ++i) {
             const int kx = t + N1 * i, p = ky * N + kx;
             const float2 G = cmul(gy, cmul(__ldg(&hd[kx]), rx[kx]));
             const float2 base = cmul(cconj(v[i]), cmul(Phi[p], G));
+            const float fxk = (float)freqd(kx, N);
             ay += fyk * base.y;
-            ax += (float)freqd(kx, N) * base.y;
+            ax += fxk * base.y;
+            an += (fyk * fyk + fxk * fxk) * base.y;
             const float2 c = cmulc(v[i], G);   // conj(G) Q
             fb[p] = (d == 0) ? c : cadd(fb[p], c);
           }
-          gacc[2 * d] += ay;
-          gacc[2 * d + 1] += ax;
+          gacc[3 * d] += ay;
+          gacc[3 * d + 1] += ax;
+          gacc[3 * d + 2] += an;
         });
         __syncthreads();
       }
@@ -473,14 +479,19 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
       }
     }
   }
-  if (a.gpos) {
-    const double sc = 2.0 * 3.14159265358979323846 / (double)NN;
+  if (a.gpos || a.gnf) {
+    // dL/ds_a = (2 pi / N^2) sum f_a Im(base);  dL/dN_F = (pi / (N_F^2 N^2)) sum |f|^2 Im(base)
+    const double pi = 3.14159265358979323846, sc = 2.0 * pi / (double)NN;
     for (int d = 0; d < nd; ++d) {
-      const double gy = block_sum<NT>(gacc[2 * d], red);
-      const double gx = block_sum<NT>(gacc[2 * d + 1], red);
+      const double gy = block_sum<NT>(gacc[3 * d], red);
+      const double gx = block_sum<NT>(gacc[3 * d + 1], red);
+      const double gn = FAR ? 0.0 : block_sum<NT>(gacc[3 * d + 2], red);
       if (threadIdx.x == 0) {
-        a.gpos[((size_t)b * nd + d) * 2] = (float)(sc * gy);
-        a.gpos[((size_t)b * nd + d) * 2 + 1] = (float)(sc * gx);
+        if (a.gpos) {
+          a.gpos[((size_t)b * nd + d) * 2] = (float)(sc * gy);
+          a.gpos[((size_t)b * nd + d) * 2 + 1] = (float)(sc * gx);
+        }
+        if (!FAR && a.gnf) a.gnf[(size_t)b * nd + d] = (float)(pi * gn / (a.nf[d] * a.nf[d] * (double)NN));
       }
     }
   }

@@ -23,10 +23,12 @@ namespace adorym {
 
 template <int N>
 struct Geo2;
-template <> struct Geo2<256>  { static constexpr int N1 = 16, N2 = 16, RB = 32, CW = 64; };
-template <> struct Geo2<512>  { static constexpr int N1 = 16, N2 = 32, RB = 32, CW = 32; };
-template <> struct Geo2<1024> { static constexpr int N1 = 32, N2 = 32, RB = 16, CW = 16; };
-constexpr int NT2 = 512;
+// RB rows per row-kernel CTA, CW columns per column-kernel CTA; 256 threads, tiles of ~64 KB so
+// two CTAs share an SM and one CTA's loads overlap the other's transforms
+template <> struct Geo2<256>  { static constexpr int N1 = 16, N2 = 16, RB = 16, CW = 32; };
+template <> struct Geo2<512>  { static constexpr int N1 = 16, N2 = 32, RB = 16, CW = 16; };
+template <> struct Geo2<1024> { static constexpr int N1 = 32, N2 = 32, RB = 8, CW = 8; };
+constexpr int NT2 = 256;
 
 template <int N>
 constexpr int row_smem_bytes() {
@@ -43,10 +45,16 @@ enum ColMode { C_PROP, C_PROP_ADJ, C_PSI0, C_FAR, C_SEED, C_Q, C_PHAT, C_PG, C_N
 __device__ __forceinline__ float freqf(int k, int N) { return (float)(k <= (N - 1) / 2 ? k : k - N) / (float)N; }
 __device__ __forceinline__ double freq2(int k, int N) { return (double)(k <= (N - 1) / 2 ? k : k - N) / (double)N; }
 
+// exp(-2 pi i d f_k): the argument is formed and reduced to [-1, 1] (units of pi) in FP64, then
+// evaluated in FP32 (FP64 transcendentals are slow on this part; the reduced argument is exact
+// to FP32 rounding)
 __device__ __forceinline__ float2 ramp1(double d, int k, int N) {
-  double s, c;
-  sincospi(-2.0 * d * freq2(k, N), &s, &c);
-  return make_float2((float)c, (float)s);
+  const double fk = (double)(k <= (N - 1) / 2 ? k : k - N) * (1.0 / (double)N);
+  double ph = -2.0 * d * fk;
+  ph -= 2.0 * rint(0.5 * ph);
+  float s, c;
+  sincospif((float)ph, &s, &c);
+  return make_float2(c, s);
 }
 
 __device__ __forceinline__ double block_sum2(double v, double* red) {
@@ -65,7 +73,7 @@ __device__ __forceinline__ double block_sum2(double v, double* red) {
 
 // ============================================================================ row kernel
 template <int N, int MODE>
-__global__ void __launch_bounds__(NT2) k_row(const TPArgs a) {
+__global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
   constexpr int N1 = Geo2<N>::N1, N2 = Geo2<N>::N2, RB = Geo2<N>::RB, LDR = N + N1;
   constexpr size_t NN = (size_t)N * N;
   extern __shared__ float2 sm[];
@@ -237,7 +245,7 @@ __global__ void __launch_bounds__(NT2) k_row(const TPArgs a) {
 
 // ============================================================================ column kernel
 template <int N, int MODE>
-__global__ void __launch_bounds__(NT2) k_col(const TPArgs a) {
+__global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
   constexpr int N1 = Geo2<N>::N1, N2 = Geo2<N>::N2, CW = Geo2<N>::CW;
   constexpr size_t NN = (size_t)N * N;
   extern __shared__ float2 sm[];
@@ -402,9 +410,10 @@ __global__ void __launch_bounds__(NT2) k_col(const TPArgs a) {
     if (MODE == C_Q && a.posp) {
       const double sy = block_sum2(ay, red), sx = block_sum2(ax, red);
       if (threadIdx.x == 0) {
-        double* pp = a.posp + ((size_t)b * gridDim.x + blockIdx.x) * 2;
+        double* pp = a.posp + ((size_t)b * gridDim.x + blockIdx.x) * 3;
         pp[0] = (m == 0) ? sy : pp[0] + sy;
         pp[1] = (m == 0) ? sx : pp[1] + sx;
+        pp[2] = 0.0;
       }
     }
   } else if (MODE == C_NEAR_PHI) {
@@ -458,7 +467,7 @@ __global__ void __launch_bounds__(NT2) k_col(const TPArgs a) {
       stage_in(a.far + (((size_t)b * (a.nd + 1) + d) * a.M + m) * NN, -1);
       for (int i = threadIdx.x; i < N; i += NT2) ry[i] = cmul(ramp1(sy, i, N), a.hd[(size_t)d * N + i]);
       __syncthreads();
-      float ay = 0.f, ax = 0.f;
+      float ay = 0.f, ax = 0.f, an = 0.f;
 #pragma unroll
       for (int it = 0; it < NTASK; ++it) {
         const int tau = threadIdx.x + it * NT2;
@@ -471,19 +480,22 @@ __global__ void __launch_bounds__(NT2) k_col(const TPArgs a) {
 #pragma unroll
         for (int i = 0; i < N2; ++i) {
           const int ky = t + N1 * i;
+          const float fy = freqf(ky, N);
           const float2 G = cmul(ry[ky], gx);
           const float2 base = cmul(cconj(v[i]), cmul(Phi[(size_t)ky * N + kx], G));
-          ay += freqf(ky, N) * base.y;
+          ay += fy * base.y;
           ax += fx * base.y;
+          an += (fy * fy + fx * fx) * base.y;
           acc[it][i] = cadd(acc[it][i], cmulc(v[i], G));
         }
       }
       if (a.posp) {
-        const double s_y = block_sum2(ay, red), s_x = block_sum2(ax, red);
+        const double s_y = block_sum2(ay, red), s_x = block_sum2(ax, red), s_n = block_sum2(an, red);
         if (threadIdx.x == 0) {
-          double* pp = a.posp + (((size_t)b * a.nd + d) * gridDim.x + blockIdx.x) * 2;
+          double* pp = a.posp + (((size_t)b * a.nd + d) * gridDim.x + blockIdx.x) * 3;
           pp[0] = (m == 0) ? s_y : pp[0] + s_y;
           pp[1] = (m == 0) ? s_x : pp[1] + s_x;
+          pp[2] = (m == 0) ? s_n : pp[2] + s_n;
         }
       }
     }
@@ -543,16 +555,23 @@ __global__ void __launch_bounds__(256) k_final2(const TPArgs a, int nloss, int n
     const double s = block_sum2(acc, red);
     if (threadIdx.x == 0) *a.loss_out = s * a.inv_npix;
   }
-  if (a.gpos) {
-    const double sc = 2.0 * 3.14159265358979323846 / ((double)a.N * a.N);
+  if (a.posp && (a.gpos || a.gnf)) {
+    const double pi = 3.14159265358979323846, NN = (double)a.N * a.N, sc = 2.0 * pi / NN;
     for (int q = threadIdx.x; q < a.B * a.nd; q += 256) {
-      double sy = 0.0, sx = 0.0;
+      double sy = 0.0, sx = 0.0, sn = 0.0;
       for (int k = 0; k < ncolblk; ++k) {
-        sy += a.posp[((size_t)q * ncolblk + k) * 2];
-        sx += a.posp[((size_t)q * ncolblk + k) * 2 + 1];
+        sy += a.posp[((size_t)q * ncolblk + k) * 3];
+        sx += a.posp[((size_t)q * ncolblk + k) * 3 + 1];
+        sn += a.posp[((size_t)q * ncolblk + k) * 3 + 2];
       }
-      a.gpos[2 * q] = (float)(sc * sy);
-      a.gpos[2 * q + 1] = (float)(sc * sx);
+      if (a.gpos) {
+        a.gpos[2 * q] = (float)(sc * sy);
+        a.gpos[2 * q + 1] = (float)(sc * sx);
+      }
+      if (a.gnf) {
+        const double nf = a.nf[q % a.nd];
+        a.gnf[q] = (float)(pi * sn / (nf * nf * NN));
+      }
     }
   }
 }

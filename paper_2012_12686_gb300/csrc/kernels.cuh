@@ -36,6 +36,8 @@ struct PathArgs {
   double* gd;             // FP64 object-gradient accumulator [Lz][Ly][Lx] (+=), or null
   double* gb;
   float* gpos;            // [B][2] or [B][n_dist][2] (overwritten), or null
+  float* gnf;             // near field: [B][n_dist] dL/dN_F (overwritten), or null
+  double nf[4];           // near field: Fresnel numbers
 };
 
 // Arguments of the two-pass path (N >= 256): fields in HBM, one row and one column kernel per
@@ -62,13 +64,15 @@ struct TPArgs {
   float2* far;             // far [B][M][N*N]; near [B][n_dist + 1][M][N*N] (Psi_d, then Phi)
   float* gI;               // [B][n_dist][N*N]
   double* lossp;           // [B * n_dist][N*N / 1024] loss partials
-  double* posp;            // [B][n_dist][N / CW][2] position / shift gradient partials
+  double* posp;            // [B][n_dist][N / CW][3] shift (y, x) and Fresnel-number gradient partials
   float2* qacc;            // [B][M][N*N]
   float2* qsum;            // [M][N*N]
   float2* tmp;             // [M][N*N]
   double* gd;              // FP64 object-gradient accumulator
   double* gb;
   float* gpos;
+  float* gnf;
+  double nf[4];
   float2* g_probe;
   double* loss_out;
   int m, j, s, j0, j1, d, buf;

@@ -127,3 +127,23 @@ def test_zero_residual_has_zero_loss_and_gradient():
     assert L < 1e-25
     for a in (gd, gb, gp, gpos):
         assert np.max(np.abs(a)) < 1e-9
+
+
+def test_nearfield_fresnel_number_gradient_brute_force():
+    """dL/dN_F (free-propagation distance refinement) against central differences in N_F."""
+    base = dict(N=8, L=1, M=1, B=2, Lz=2, Ly=8, Lx=8, kdz=20.0, lambda_dz_over_px2=0.0,
+                farfield=0, nf=[0.05, 0.11, 0.3], loss="poisson", eps=1e-3)
+    g = np.random.default_rng(17)
+    delta = g.uniform(0, 0.05, (2, 8, 8)); beta = g.uniform(0, 0.002, delta.shape)
+    probe = np.ones((1, 8, 8), complex)
+    shifts = g.uniform(-2, 2, (2, 3, 2))
+    Im = model.forward(model.Problem.of(base), delta * 1.2, beta, probe, shifts + 0.1)
+    out = model.loss_grad(model.Problem.of(base), delta, beta, probe, shifts, Im, want_nf=True)
+    for di in range(3):
+        h = 1e-7
+        pp = dict(base, nf=[v + (h if k == di else 0.0) for k, v in enumerate(base["nf"])])
+        pm = dict(base, nf=[v - (h if k == di else 0.0) for k, v in enumerate(base["nf"])])
+        # the loss is a mean over both problems; N_F is per problem in the gradient, shared here
+        fd = (model.loss(model.Problem.of(pp), delta, beta, probe, shifts, Im)
+              - model.loss(model.Problem.of(pm), delta, beta, probe, shifts, Im)) / (2 * h)
+        assert abs(out[5][:, di].sum() - fd) <= 1e-6 * abs(fd) + 1e-12, (di, out[5][:, di].sum(), fd)
