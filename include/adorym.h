@@ -141,6 +141,28 @@ typedef struct adorym_grads {
 int adorym_loss_grad_ext(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const float* probe, const float* pos,
                          const float* I_meas, const adorym_grads* out);
 
+/* Regularizers of Table regularizers (refractive-index form), added to the data term as in
+ * Eq. tikhonov:  R = (1/N_o) [ sum a_d W_d|delta| + a_b W_b|beta|
+ *                              + gamma sum over x, y, z of (|grad delta| + |grad beta|) ],
+ * N_o = Lz Ly Lx, forward differences with no term past the last index, subgradient 0 at 0. */
+typedef struct adorym_reg {
+  double alpha_delta;     /* l1 weight on delta (alpha_1)                                         */
+  double alpha_beta;      /* l1 weight on beta (alpha_2)                                          */
+  const float* w_delta;   /* reweighted l1: device [Lz][Ly][Lx] weights W_1, or NULL (plain l1)   */
+  const float* w_beta;    /* W_2, or NULL                                                         */
+  double gamma_tv;        /* total-variation weight gamma (0: no TV term)                         */
+} adorym_reg;
+
+/* R and its gradient for a registered object: *loss_out = R (host or device double, may be NULL);
+ * g_delta, g_beta (device [Lz][Ly][Lx], may be NULL together) receive dR/ddelta, dR/dbeta added
+ * (+=). */
+int adorym_regularize(adorym_ctx* ctx, int obj_id, const adorym_reg* r, double* loss_out, float* g_delta,
+                      float* g_beta);
+
+/* Reweighted-l1 weights from a snapshot object: W = max|C| / (|C| + eps) for C = delta and beta,
+ * written to device arrays w_delta, w_beta [Lz][Ly][Lx] (treated as constants by adorym_regularize). */
+int adorym_l1_weights(adorym_ctx* ctx, int obj_id, double eps, float* w_delta, float* w_beta);
+
 /* A loss/gradient request for the serving loop: the arguments of adorym_loss_grad. */
 typedef struct adorym_request {
   adorym_problem problem;

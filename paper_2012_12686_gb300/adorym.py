@@ -21,7 +21,8 @@ LOSS = {"lsq": 0, "poisson": 1}
 EXPORTS = ["adorym_create", "adorym_destroy", "adorym_last_error", "adorym_register_object",
            "adorym_unregister_object", "adorym_forward", "adorym_loss_grad", "adorym_submit", "adorym_poll",
            "adorym_serve_config", "adorym_serve_stats", "adorym_workspace_bytes", "adorym_enable_kernel_timing",
-           "adorym_kernel_ms", "adorym_loss_grad_noalloc", "adorym_loss_grad_ext"]
+           "adorym_kernel_ms", "adorym_loss_grad_noalloc", "adorym_loss_grad_ext", "adorym_regularize",
+           "adorym_l1_weights"]
 
 
 class Problem(ctypes.Structure):
@@ -59,6 +60,11 @@ class Grads(ctypes.Structure):
                 ("I_out", ctypes.c_void_p)]
 
 
+class Reg(ctypes.Structure):
+    _fields_ = [("alpha_delta", ctypes.c_double), ("alpha_beta", ctypes.c_double), ("w_delta", ctypes.c_void_p),
+                ("w_beta", ctypes.c_void_p), ("gamma_tv", ctypes.c_double)]
+
+
 class Request(ctypes.Structure):
     _fields_ = [("problem", Problem), ("obj_id", ctypes.c_int),
                 ("probe", ctypes.c_void_p), ("pos", ctypes.c_void_p), ("I_meas", ctypes.c_void_p),
@@ -93,6 +99,8 @@ def lib() -> ctypes.CDLL:
         L.adorym_workspace_bytes.argtypes = [ctypes.POINTER(Problem), i32, ctypes.POINTER(u64)]
         L.adorym_enable_kernel_timing.argtypes = [vp, i32]
         L.adorym_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+        L.adorym_regularize.argtypes = [vp, i32, ctypes.POINTER(Reg), vp, vp, vp]
+        L.adorym_l1_weights.argtypes = [vp, i32, ctypes.c_double, vp, vp]
         L.adorym_loss_grad_ext.argtypes = [vp, ctypes.POINTER(Problem), i32, vp, vp, vp, ctypes.POINTER(Grads)]
         L.adorym_loss_grad_noalloc.argtypes = [vp, ctypes.POINTER(Problem), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         for name in EXPORTS:
@@ -187,6 +195,16 @@ class Engine:
             setattr(g, k, _ptr(v))
         return self._check(lib().adorym_loss_grad_ext(self._ctx, ctypes.byref(p), obj_id, _ptr(probe), _ptr(pos),
                                                       _ptr(I_meas), ctypes.byref(g)))
+
+    def regularize(self, obj_id, alpha_delta=0.0, alpha_beta=0.0, gamma_tv=0.0, w_delta=None, w_beta=None,
+                   loss_out=None, g_delta=None, g_beta=None):
+        """adorym_regularize: l1 / reweighted l1 / TV regularizer value and gradient (Eq. tikhonov)."""
+        r = Reg(float(alpha_delta), float(alpha_beta), _ptr(w_delta), _ptr(w_beta), float(gamma_tv))
+        return self._check(lib().adorym_regularize(self._ctx, obj_id, ctypes.byref(r), _ptr(loss_out), _ptr(g_delta),
+                                                   _ptr(g_beta)))
+
+    def l1_weights(self, obj_id, eps, w_delta, w_beta):
+        return self._check(lib().adorym_l1_weights(self._ctx, obj_id, float(eps), _ptr(w_delta), _ptr(w_beta)))
 
     def enable_kernel_timing(self, on: bool = True):
         self._check(lib().adorym_enable_kernel_timing(self._ctx, 1 if on else 0))

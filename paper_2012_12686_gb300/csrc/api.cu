@@ -568,6 +568,57 @@ int adorym_loss_grad(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const
   return run_call(ctx, p, obj_id, probe, pos, I_meas, loss_out, g_delta, g_beta, g_probe, g_pos, I_out, true);
 }
 
+int adorym_regularize(adorym_ctx* ctx, int obj_id, const adorym_reg* r, double* loss_out, float* g_delta,
+                      float* g_beta) {
+  if (!ctx) return ADORYM_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!r) return fail(ctx, ADORYM_EINVAL, "null regularizer description");
+  if ((g_delta == nullptr) != (g_beta == nullptr))
+    return fail(ctx, ADORYM_EINVAL, "g_delta and g_beta must both be given or both be NULL");
+  auto it = ctx->objects.find(obj_id);
+  if (it == ctx->objects.end()) return fail(ctx, ADORYM_ENOENT, "unknown object id");
+  const Object& o = it->second;
+  const void* dev_ptrs[] = {g_delta, g_beta, r->w_delta, r->w_beta};
+  for (const void* q : dev_ptrs)
+    if (q && ptr_kind(q) != 1) return fail(ctx, ADORYM_EINVAL, "gradient and weight arrays must be device memory");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "set device");
+  const size_t n = (size_t)o.Lz * o.Ly * o.Lx;
+  const size_t need = al(reg_parts(n) * sizeof(double)) + al(sizeof(double));
+  int rc = ensure_ws(ctx, need);
+  if (rc) return rc;
+  double* part = reinterpret_cast<double*>(ctx->ws);
+  double* dloss = reinterpret_cast<double*>(ctx->ws + al(reg_parts(n) * sizeof(double)));
+  const bool host_loss = loss_out && ptr_kind(loss_out) == 0;
+  double* lp = loss_out ? (host_loss ? dloss : loss_out) : nullptr;
+  cudaError_t e = launch_regularize(o.d, o.b, r->w_delta, r->w_beta, o.Lz, o.Ly, o.Lx, r->alpha_delta, r->alpha_beta,
+                                    r->gamma_tv, g_delta, g_beta, part, lp, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "regularize");
+  if (host_loss) {
+    cudaMemcpyAsync(loss_out, dloss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+  }
+  return ADORYM_OK;
+}
+
+int adorym_l1_weights(adorym_ctx* ctx, int obj_id, double eps, float* w_delta, float* w_beta) {
+  if (!ctx) return ADORYM_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->objects.find(obj_id);
+  if (it == ctx->objects.end()) return fail(ctx, ADORYM_ENOENT, "unknown object id");
+  if (!(eps > 0.0)) return fail(ctx, ADORYM_EINVAL, "eps must be > 0");
+  if (ptr_kind(w_delta) != 1 || ptr_kind(w_beta) != 1) return fail(ctx, ADORYM_EINVAL, "weights must be device memory");
+  const Object& o = it->second;
+  const size_t n = (size_t)o.Lz * o.Ly * o.Lx;
+  int rc = ensure_ws(ctx, al(reg_parts(n) * sizeof(float)));
+  if (rc) return rc;
+  float* part = reinterpret_cast<float*>(ctx->ws);
+  cudaError_t e = launch_l1_weights(o.d, n, (float)eps, part, w_delta, ctx->stream);
+  if (e == cudaSuccess) e = launch_l1_weights(o.b, n, (float)eps, part, w_beta, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "l1 weights");
+  return ADORYM_OK;
+}
+
 int adorym_loss_grad_ext(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const float* probe, const float* pos,
                          const float* I_meas, const adorym_grads* out) {
   if (!out) return run_call(ctx, p, obj_id, probe, pos, I_meas, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,

@@ -167,7 +167,7 @@ __device__ __forceinline__ void pass_c14(float2* __restrict__ A, const float2* _
   constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD;
   using P = Tpt<N * N2, F::NT>;
   // the spatial pass keeps three register arrays per task; phase its tasks only when they fit
-  constexpr int Q = (F::NT <= 512) ? P::n : 1;
+  constexpr int Q = (F::NT <= 512) ? (P::n < 2 ? P::n : 2) : 1;
   for (int q0 = 0; q0 < P::n; q0 += Q) {
     float2 pa[Q][N1], pb[Q][N1], v[Q][N1];
 #pragma unroll

@@ -99,6 +99,13 @@ cudaError_t launch_zero_box(double* a, double* b, int Lz, int Ly, int Lx, const 
 cudaError_t launch_grad_add(const double* acc_d, const double* acc_b, float* gd, float* gb, int Lz, int Ly, int Lx,
                             const int* box, cudaStream_t s);
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s);
+// regularizers (l1 / reweighted l1 / TV): part needs reg_parts(n) doubles
+int reg_parts(size_t n);
+cudaError_t launch_regularize(const float* d, const float* b, const float* wd, const float* wb, int Lz, int Ly, int Lx,
+                              double ad, double ab, double gam, float* gd, float* gb, double* part, double* loss,
+                              cudaStream_t s);
+// W = max|C| / (|C| + eps); part needs reg_parts(n) floats
+cudaError_t launch_l1_weights(const float* c, size_t n, float eps, float* part, float* w, cudaStream_t s);
 // qsum[i] = sum_b qacc[b][i] in FP64, fixed order
 cudaError_t launch_qsum(const float2* qacc, float2* qsum, int B, size_t MNN, cudaStream_t s);
 int path_smem_bytes(int N);
