@@ -129,13 +129,18 @@ def _oracle_one(args):
     return time.perf_counter() - t
 
 
-def oracle_sample(w, I_meas_np, n_pos: int, workers: int):
-    """Time the FP64 oracle (as it stands) on n_pos positions of the minibatch, one position per
-    task, over a spawn pool of `workers` single-threaded processes.  Returns (wall s, positions)."""
+def oracle_pool(workers: int):
+    """Spawn pool of single-threaded oracle workers (one BLAS thread each)."""
     import multiprocessing as mp
-    import numpy as np
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[k] = "1"
+    return mp.get_context("spawn").Pool(workers)
+
+
+def oracle_sample(w, I_meas_np, n_pos: int, workers: int, pool=None):
+    """Time the FP64 oracle (as it stands) on n_pos positions of the minibatch, one position per
+    task, over a spawn pool of `workers` single-threaded processes.  Returns (wall s, positions)."""
+    import numpy as np
     N = w["problem"]["N"]
     p = dict(w["problem"], B=1, Ly=N, Lx=N)
     jobs = []
@@ -151,12 +156,18 @@ def oracle_sample(w, I_meas_np, n_pos: int, workers: int):
             out[:, ya - c[0]:yb - c[0], xa - c[1]:xb - c[1]] = vol[:, ya:yb, xa:xb]
             crop.append(out)
         jobs.append((p, crop[0], crop[1], w["probe"], pos - c, I_meas_np[i:i + 1]))
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(workers) as pool:
+    own = pool is None
+    if own:
+        pool = oracle_pool(workers)
+    try:
         pool.map(_oracle_one, jobs[:workers])          # warm: imports, DFT matrices
         t = time.perf_counter()
         pool.map(_oracle_one, jobs)
         wall = time.perf_counter() - t
+    finally:
+        if own:
+            pool.close()
+            pool.join()
     return wall, n_pos
 
 
@@ -282,13 +293,18 @@ def run_reference(args, rank):
     times = []
     t_all = time.perf_counter()
     steps_run = 0
-    for k in range(args.warmup + args.steps):
-        wall, npos = oracle_sample(ws, Im, n_pos, cores)
-        if k >= args.warmup:
-            times.append(wall)
-            steps_run += 1
-        if time.perf_counter() - t_all > budget_s and steps_run >= 1:
-            break
+    pool = oracle_pool(cores)
+    try:
+        for k in range(args.warmup + args.steps):
+            wall, npos = oracle_sample(ws, Im, n_pos, cores, pool=pool)
+            if k >= args.warmup:
+                times.append(wall)
+                steps_run += 1
+            if time.perf_counter() - t_all > budget_s and steps_run >= 1:
+                break
+    finally:
+        pool.close()
+        pool.join()
     mean_s = statistics.mean(times)
     value = n_pos * L / mean_s
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": steps_run,
