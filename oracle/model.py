@@ -41,6 +41,11 @@ class Problem:
     tomo: int = 0
     theta: float = 0.0
     checkpoint_every: int = 0
+    gaps: list = None               # sparse / variable multislice: L-1 values lambda dz_j / dx^2 (None: uniform)
+
+    def gap(self, j):
+        """lambda dz_j / dx^2 of the Fresnel step from slice j to slice j + 1."""
+        return self.lambda_dz_over_px2 if self.gaps is None else float(self.gaps[j])
 
     @staticmethod
     def of(d: dict) -> "Problem":
@@ -222,13 +227,12 @@ def _multislice(pb, T, psi0):
 
     Returns the exit wave phi_{L-1} and the list of pre-modulation fields psi_j.
     """
-    H = fresnel_kernel(pb.N, pb.lambda_dz_over_px2)
     psis, psi = [], psi0
     for j in range(pb.L):
         psis.append(psi)
         phi = T[j] * psi
         if j < pb.L - 1:
-            psi = propagate(phi, H)
+            psi = propagate(phi, fresnel_kernel(pb.N, pb.gap(j)))   # variable spacing: Sec. 2.2
     return phi, psis
 
 
@@ -238,18 +242,25 @@ def _multislice_T(pb, T, psis, phibar, kdz):
     phi_j = T_j psi_j gives psibar_j = conj(T_j) phibar_j and, with
     dphi/ddelta = i kdz phi, dphi/dbeta = -kdz phi (Eq. ri_modulation):
       dL/ddelta_j = kdz Im(psibar_j conj(psi_j)),  dL/dbeta_j = -kdz Re(psibar_j conj(psi_j))
-    summed over probe modes; phibar_{j-1} = P^H psibar_j.
+    summed over probe modes; phibar_{j-1} = P^H psibar_j.  Also returns dL/dc_j for the slice
+    gaps c_j = lambda dz_j / dx^2 (slice-position refinement, Sec. 2.3.2): with
+    psi_{j+1} = F^-1{F[phi_j] H_j}, dH_j/dc = i pi |f|^2 H_j and Parseval,
+      dL/dc_j = Re[(1/N^2) sum_nu conj(F[psibar_{j+1}]) i pi |f|^2 F[psi_{j+1}]].
     """
-    H = fresnel_kernel(pb.N, pb.lambda_dz_over_px2)
-    gd = np.zeros((pb.L, pb.N, pb.N)); gb = np.zeros((pb.L, pb.N, pb.N))
+    N = pb.N
+    f = freq(N)
+    f2 = f[:, None] ** 2 + f[None, :] ** 2
+    gd = np.zeros((pb.L, N, N)); gb = np.zeros((pb.L, N, N))
+    g_gap = np.zeros(max(pb.L - 1, 0))
     for j in range(pb.L - 1, -1, -1):
         if j < pb.L - 1:
-            phibar = propagate_T(psibar, H)
+            g_gap[j] = np.real(np.sum(np.conj(dft_minus(psibar)) * 1j * np.pi * f2 * dft_minus(psis[j + 1]))) / (N * N)
+            phibar = propagate_T(psibar, fresnel_kernel(N, pb.gap(j)))
         psibar = np.conj(T[j]) * phibar
         z = psibar * np.conj(psis[j])
         gd[j] = kdz * np.sum(z.imag, axis=0)
         gb[j] = -kdz * np.sum(z.real, axis=0)
-    return psibar, gd, gb
+    return psibar, gd, gb, g_gap
 
 
 def _farfield_position(pb, d, b, probe_hat, p0, dr):
@@ -299,12 +310,13 @@ def loss(problem, delta, beta, probe, pos, I_meas):
     return float(np.mean(loss_terms(I, I_meas, pb.loss, pb.eps)))
 
 
-def loss_grad(problem, delta, beta, probe, pos, I_meas, want_nf=False):
+def loss_grad(problem, delta, beta, probe, pos, I_meas, want_nf=False, want_gaps=False):
     """Loss and its gradients w.r.t. delta, beta (volume frame), probe and positions/shifts.
 
     Returns (loss, g_delta, g_beta, g_probe, g_pos) in FP64 / complex128; with want_nf (near
     field) also g_nf [B, n_dist], the gradient w.r.t. each problem's Fresnel numbers (the
-    free-propagation distance refinement of Sec. 2.3.2: N_F = dx^2 / (lambda z)).
+    free-propagation distance refinement of Sec. 2.3.2: N_F = dx^2 / (lambda z)); with want_gaps
+    also g_gaps [L-1], the gradient w.r.t. the slice gaps lambda dz_j / dx^2 (slice positions).
     """
     pb = problem if isinstance(problem, Problem) else Problem.of(problem)
     d, b = _object_frames(pb, delta, beta)
@@ -313,6 +325,7 @@ def loss_grad(problem, delta, beta, probe, pos, I_meas, want_nf=False):
     N = pb.N
     gvd = np.zeros(d.shape); gvb = np.zeros(b.shape)
     g_probe = np.zeros(probe.shape, np.complex128)
+    g_gaps = np.zeros(max(pb.L - 1, 0))
     total = 0.0
     if pb.farfield:
         npix = pb.B * N * N
@@ -327,7 +340,8 @@ def loss_grad(problem, delta, beta, probe, pos, I_meas, want_nf=False):
             gI = loss_dI(I, I_meas[i], pb.loss, pb.eps) / npix
             Psibar = 2.0 * gI * Psi                              # dI = 2 Re(conj(Psi) dPsi)
             phibar = farfield_T(Psibar)
-            psibar0, gd, gb = _multislice_T(pb, T[:, :, :, :], psis, phibar, pb.kdz)
+            psibar0, gd, gb, gg = _multislice_T(pb, T[:, :, :, :], psis, phibar, pb.kdz)
+            g_gaps += gg
             put_chunk_T(gvd, p0[i], gd); put_chunk_T(gvb, p0[i], gb)
             Q = dft_minus(psibar0)                               # [M, N, N]
             g_probe += idft_minus(Q * np.conj(rp))
@@ -358,14 +372,18 @@ def loss_grad(problem, delta, beta, probe, pos, I_meas, want_nf=False):
                 # dH_d/dN_F = -i pi |f|^2 / N_F^2 H_d (Eq. paraxial_kernel with lambda z / dx^2 = 1 / N_F)
                 g_nf[i, di] = np.real(np.sum(base * (-1j * np.pi * f2 / pb.nf[di] ** 2))) / (N * N)
             phibar = idft_minus(Phibar_sum)
-            psibar0, gd, gb = _multislice_T(pb, T, psis, phibar, pb.kdz)
+            psibar0, gd, gb, gg = _multislice_T(pb, T, psis, phibar, pb.kdz)
+            g_gaps += gg
             gvd[i * pb.L:(i + 1) * pb.L] += gd
             gvb[i * pb.L:(i + 1) * pb.L] += gb
             g_probe += psibar0
     if pb.tomo:
         gvd, gvb = rotate_T(gvd, pb.theta), rotate_T(gvb, pb.theta)
+    out = (total / npix, gvd, gvb, g_probe, g_pos)
     if want_nf:
         if pb.farfield:
             raise ValueError("Fresnel-number gradients are defined for the near-field geometry")
-        return total / npix, gvd, gvb, g_probe, g_pos, g_nf
-    return total / npix, gvd, gvb, g_probe, g_pos
+        out = out + (g_nf,)
+    if want_gaps:
+        out = out + (g_gaps,)
+    return out

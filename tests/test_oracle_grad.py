@@ -147,3 +147,36 @@ def test_nearfield_fresnel_number_gradient_brute_force():
         fd = (model.loss(model.Problem.of(pp), delta, beta, probe, shifts, Im)
               - model.loss(model.Problem.of(pm), delta, beta, probe, shifts, Im)) / (2 * h)
         assert abs(out[5][:, di].sum() - fd) <= 1e-6 * abs(fd) + 1e-12, (di, out[5][:, di].sum(), fd)
+
+
+@pytest.mark.parametrize("far", [True, False])
+def test_slice_gap_gradient_brute_force(far):
+    """Sparse / variable multislice: dL/d(lambda dz_j / dx^2) against central differences."""
+    if far:
+        base = dict(N=8, L=4, M=2, B=2, Lz=4, Ly=12, Lx=12, kdz=253.354, lambda_dz_over_px2=0.0,
+                    farfield=1, nf=[], loss="lsq", eps=1e-6, gaps=[0.4, 1.7, 0.9])
+        pos = np.array([[1.2, 2.7], [3.3, 0.8]])
+    else:
+        base = dict(N=8, L=3, M=1, B=2, Lz=6, Ly=8, Lx=8, kdz=20.0, lambda_dz_over_px2=0.0,
+                    farfield=0, nf=[0.05, 0.11], loss="poisson", eps=1e-3, gaps=[0.6, 2.2])
+        pos = np.array([[[1.3, -2.2], [0.4, 0.1]], [[-0.3, 3.35], [2.2, -1.4]]])
+    g = np.random.default_rng(19)
+    shape = (base["Lz"], base["Ly"], base["Lx"])
+    delta = g.uniform(0, 2e-3 if far else 0.05, shape); beta = g.uniform(0, 2e-4 if far else 0.002, shape)
+    probe = _cplx(g, (base["M"], 8, 8)) * (3.0 if far else 0.1) + (0 if far else 1.0)
+    pb = model.Problem.of(base)
+    Im = model.forward(pb, delta * 1.2, beta, probe, pos + 0.1)
+    out = model.loss_grad(pb, delta, beta, probe, pos, Im, want_gaps=True)
+    gg = out[-1]
+    for j in range(len(base["gaps"])):
+        h = 1e-6
+        gp = list(base["gaps"]); gp[j] += h
+        gm = list(base["gaps"]); gm[j] -= h
+        fd = (model.loss(model.Problem.of(dict(base, gaps=gp)), delta, beta, probe, pos, Im)
+              - model.loss(model.Problem.of(dict(base, gaps=gm)), delta, beta, probe, pos, Im)) / (2 * h)
+        assert abs(gg[j] - fd) <= 1e-6 * max(abs(fd), 1e-12) + 1e-13, (j, gg[j], fd)
+    # uniform gaps reproduce the equal-spacing model
+    pu = model.Problem.of(dict(base, gaps=[0.5] * len(base["gaps"])))
+    pe = model.Problem.of(dict(base, gaps=None, lambda_dz_over_px2=0.5))
+    np.testing.assert_allclose(model.forward(pu, delta, beta, probe, pos), model.forward(pe, delta, beta, probe, pos),
+                               rtol=1e-13)
