@@ -81,6 +81,9 @@ typedef struct adorym_problem {
   int tomo;           /* 1: sample the object rotated by theta about y (Eq. rotation_transform) */
   double theta;       /* tilt angle in radians                                              */
   int checkpoint_every; /* adjoint checkpoint spacing in slices; 0 = ceil(sqrt(L))          */
+  const double* gaps; /* sparse / variable multislice (Sec. 2.2): NULL for equal spacing, else a
+                         host array of L-1 values lambda dz_j / dx^2 for the Fresnel step from
+                         slice j to j+1 (read during the call; replaces lambda_dz_over_px2)     */
 } adorym_problem;
 
 /* Create a context on CUDA device `device`, enqueueing on `cuda_stream` (a cudaStream_t; NULL =
@@ -135,6 +138,8 @@ typedef struct adorym_grads {
                        Fresnel numbers (free-propagation distance refinement, Sec. 2.3.2;
                        N_F = dx^2 / (lambda z), so dL/dz = -dL/dN_F * N_F / z), overwritten   */
   float* I_out;     /* predicted intensities, overwritten                                        */
+  float* g_gaps;    /* with variable spacing: [L-1] dL/d(lambda dz_j / dx^2), the slice-position
+                       gradient (Sec. 2.3.2), summed over the batch, overwritten                  */
 } adorym_grads;
 
 /* adorym_loss_grad with its outputs in a struct, including the near-field distance gradient. */

@@ -31,11 +31,15 @@ class Problem(ctypes.Structure):
                 ("kdz", ctypes.c_double), ("lambda_dz_over_px2", ctypes.c_double),
                 ("farfield", ctypes.c_int), ("n_dist", ctypes.c_int), ("nf", ctypes.c_double * 4),
                 ("loss", ctypes.c_int), ("eps", ctypes.c_double), ("tomo", ctypes.c_int),
-                ("theta", ctypes.c_double), ("checkpoint_every", ctypes.c_int)]
+                ("theta", ctypes.c_double), ("checkpoint_every", ctypes.c_int), ("gaps", ctypes.c_void_p)]
 
     @staticmethod
     def of(d: dict) -> "Problem":
         p = Problem()
+        gaps = d.get("gaps")
+        if gaps is not None:
+            p._gaps = (ctypes.c_double * len(gaps))(*[float(v) for v in gaps])   # kept alive with p
+            p.gaps = ctypes.cast(p._gaps, ctypes.c_void_p)
         for k in ("N", "L", "M", "B", "Ly", "Lx", "Lz"):
             setattr(p, k, int(d[k]))
         p.kdz = float(d["kdz"])
@@ -57,7 +61,7 @@ class Problem(ctypes.Structure):
 class Grads(ctypes.Structure):
     _fields_ = [("loss", ctypes.c_void_p), ("g_delta", ctypes.c_void_p), ("g_beta", ctypes.c_void_p),
                 ("g_probe", ctypes.c_void_p), ("g_pos", ctypes.c_void_p), ("g_nf", ctypes.c_void_p),
-                ("I_out", ctypes.c_void_p)]
+                ("I_out", ctypes.c_void_p), ("g_gaps", ctypes.c_void_p)]
 
 
 class Reg(ctypes.Structure):
@@ -186,12 +190,13 @@ class Engine:
                                                   _ptr(g_probe), _ptr(g_pos), _ptr(I_out)))
 
     def loss_grad_ext(self, problem, obj_id, probe, pos, I_meas, loss_out=None, g_delta=None, g_beta=None,
-                      g_probe=None, g_pos=None, g_nf=None, I_out=None):
-        """adorym_loss_grad_ext: as loss_grad, plus g_nf (near field: dL/dN_F per problem and distance)."""
+                      g_probe=None, g_pos=None, g_nf=None, I_out=None, g_gaps=None):
+        """adorym_loss_grad_ext: as loss_grad, plus g_nf (near field: dL/dN_F per problem and distance)
+        and g_gaps (variable slice spacing: dL/d(lambda dz_j / dx^2))."""
         p = problem if isinstance(problem, Problem) else Problem.of(problem)
         g = Grads()
         for k, v in (("loss", loss_out), ("g_delta", g_delta), ("g_beta", g_beta), ("g_probe", g_probe),
-                     ("g_pos", g_pos), ("g_nf", g_nf), ("I_out", I_out)):
+                     ("g_pos", g_pos), ("g_nf", g_nf), ("I_out", I_out), ("g_gaps", g_gaps)):
             setattr(g, k, _ptr(v))
         return self._check(lib().adorym_loss_grad_ext(self._ctx, ctypes.byref(p), obj_id, _ptr(probe), _ptr(pos),
                                                       _ptr(I_meas), ctypes.byref(g)))

@@ -25,6 +25,9 @@ int validate(const adorym_problem& p, const char** err) {
   if (!(p.eps >= 0.0)) return bad("eps must be >= 0");
   if (!std::isfinite(p.kdz) || !std::isfinite(p.lambda_dz_over_px2)) return bad("kdz / lambda_dz_over_px2 not finite");
   if (p.checkpoint_every < 0 || p.checkpoint_every > p.L) return bad("checkpoint_every must be in 0..L");
+  if (p.gaps)
+    for (int j = 0; j + 1 < p.L; ++j)
+      if (!std::isfinite(p.gaps[j])) return bad("slice gaps must be finite");
   if (p.farfield) {
     if (!pow2_in(p.N, 8, 1024)) return bad("far field: N must be a power of two in 8..1024");
     if (p.Lz != p.L) return bad("far field: Lz must equal L (the wave crosses every slice)");
@@ -56,6 +59,8 @@ int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan
   q.want_probe = adj && (grads & 2);
   q.want_pos = adj && (grads & 4);
   q.want_nf = adj && (grads & 8) && !p.farfield;
+  q.gaps = p.gaps != nullptr && p.L > 1;
+  q.want_gaps = adj && (grads & 16) && q.gaps;
   q.want_loss = want_loss;
   q.nd = q.far ? 1 : p.n_dist;
   q.cp = p.checkpoint_every > 0 ? p.checkpoint_every : (int)std::ceil(std::sqrt((double)p.L));
@@ -99,6 +104,13 @@ int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan
   }
   q.off_loss = take(sizeof(double));
   q.off_box = take(4 * sizeof(int));
+  if (q.want_gaps) {
+    const int parts = two_pass(p.N) ? (int)(N / (N == 256 ? 32 : N == 512 ? 16 : 8)) : 1;
+    q.off_spck = take(B * M * q.ncp * NN * f2);
+    q.off_spseg = take(B * M * q.cp * NN * f2);
+    q.off_gapp = take(B * (size_t)(p.L - 1) * parts * sizeof(double));
+    q.off_s_ggap = take((size_t)(p.L - 1) * sizeof(float));
+  }
   {
     const size_t V = (size_t)p.Lz * p.Ly * p.Lx;
     q.off_T = take(V * f2);
@@ -125,12 +137,24 @@ static std::string table_key(const adorym_problem& p) {
   int n = snprintf(buf, sizeof buf, "%d|%.17g|%d", p.N, p.lambda_dz_over_px2, p.farfield ? 0 : p.n_dist);
   if (!p.farfield)
     for (int d = 0; d < p.n_dist; ++d) n += snprintf(buf + n, sizeof buf - n, "|%.17g", p.nf[d]);
-  return std::string(buf);
+  std::string key(buf);
+  if (p.gaps && p.L > 1) {
+    key += "|gaps";
+    for (int j = 0; j + 1 < p.L; ++j) {
+      snprintf(buf, sizeof buf, "|%.17g", p.gaps[j]);
+      key += buf;
+    }
+  }
+  return key;
 }
 
 static double freq(int k, int N) { return (double)(k <= (N - 1) / 2 ? k : k - N) / (double)N; }
 
-size_t table_count(const adorym_problem& p) { return (size_t)(3 + (p.farfield ? 0 : p.n_dist)) * p.N; }
+static int ngaps(const adorym_problem& p) { return (p.gaps && p.L > 1) ? p.L - 1 : 0; }
+
+size_t table_count(const adorym_problem& p) {
+  return (size_t)(3 + (p.farfield ? 0 : p.n_dist)) * p.N + 2 * (size_t)ngaps(p) * p.N;
+}
 
 void fill_tables(const adorym_problem& p, float2* h) {
   const int N = p.N, nd = p.farfield ? 0 : p.n_dist;
@@ -150,6 +174,16 @@ void fill_tables(const adorym_problem& p, float2* h) {
       h[(size_t)(3 + d) * N + k] = make_float2((float)std::cos(ph), (float)std::sin(ph));
     }
   }
+  const int ng = ngaps(p);
+  float2* hyj = h + (size_t)(3 + nd) * N;
+  for (int j = 0; j < ng; ++j) {   // per-gap factors exp(i pi c_j f^2) / N (variable spacing)
+    for (int k = 0; k < N; ++k) {
+      const double f = freq(k, N), ph = kPi * p.gaps[j] * f * f;
+      const float2 v = make_float2((float)(std::cos(ph) / N), (float)(std::sin(ph) / N));
+      hyj[(size_t)j * N + k] = v;
+      hyj[(size_t)(ng + j) * N + k] = v;
+    }
+  }
 }
 
 int get_tables(adorym_ctx* ctx, const adorym_problem& p, Tables* out) {
@@ -165,6 +199,7 @@ int get_tables(adorym_ctx* ctx, const adorym_problem& p, Tables* out) {
   Tables t;
   t.N = N;
   t.nd = nd;
+  t.ngap = ngaps(p);
   cudaError_t e = cudaMalloc(&t.dev, h.size() * sizeof(float2));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -238,6 +273,8 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
     t.hy = tab.hy();
     t.hx = tab.hx();
     t.hd = pl.far ? nullptr : tab.hd();
+    t.hyj = tab.hyj();
+    t.hxj = tab.hxj();
     t.FA = reinterpret_cast<float2*>(W(pl.off_FA));
     t.far = reinterpret_cast<float2*>(W(pl.off_far));
     t.gI = reinterpret_cast<float*>(W(pl.off_gI));
@@ -252,6 +289,12 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
       t.posp = (pl.want_pos || pl.want_nf) ? reinterpret_cast<double*>(W(pl.off_posp)) : nullptr;
       t.gnf = pl.want_nf ? c.g_nf : nullptr;
       for (int d = 0; d < 4; ++d) t.nf[d] = p.nf[d];
+      if (pl.want_gaps) {
+        t.spec_out = reinterpret_cast<float2*>(W(pl.off_spck));    // spectra: [B][M][ncp] then [B][M][cp]
+        t.spec_in = reinterpret_cast<float2*>(W(pl.off_spseg));
+        t.gapp = reinterpret_cast<double*>(W(pl.off_gapp));
+        t.ggap = c.g_gaps;
+      }
       t.gd = pl.want_obj ? gd : nullptr;
       t.gb = pl.want_obj ? gb : nullptr;
       t.gpos = pl.want_pos ? c.g_pos : nullptr;
@@ -288,6 +331,8 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
     a.hy = tab.hy();
     a.hx = tab.hx();
     a.hd = pl.far ? nullptr : tab.hd();
+    a.hyj = tab.hyj();
+    a.hxj = tab.hxj();
     if (pl.adj) {
       a.ckpt = reinterpret_cast<float2*>(W(pl.off_ckpt));
       a.seg = reinterpret_cast<float2*>(W(pl.off_seg));
@@ -299,6 +344,11 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
       a.gpos = pl.want_pos ? c.g_pos : nullptr;
       a.gnf = pl.want_nf ? c.g_nf : nullptr;
       for (int d = 0; d < 4; ++d) a.nf[d] = p.nf[d];
+      if (pl.want_gaps) {
+        a.spck = reinterpret_cast<float2*>(W(pl.off_spck));
+        a.spseg = reinterpret_cast<float2*>(W(pl.off_spseg));
+        a.gapp = reinterpret_cast<double*>(W(pl.off_gapp));
+      }
     }
     a.far = reinterpret_cast<float2*>(W(pl.off_far));
     a.gI = reinterpret_cast<float*>(W(pl.off_gI));
@@ -306,6 +356,9 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
     if (ev_start) cudaEventRecord(ev_start, s);
     if ((rc = chk(launch_path(a, pl.far ? 1 : 0, s), "path"))) return rc;
     if (ev_stop) cudaEventRecord(ev_stop, s);
+    if (pl.want_gaps && c.g_gaps) {
+      if ((rc = chk(launch_gap_final(a.gapp, p.B, p.L - 1, 1, c.g_gaps, s), "gap_final"))) return rc;
+    }
     if (pl.adj && (pl.want_probe || c.loss)) {
       if ((rc = chk(launch_probe_grad(p.N, p.M, p.B, pl.far ? 1 : 0, a.qacc, reinterpret_cast<float2*>(W(pl.off_qsum)),
                                       pl.want_probe ? c.g_probe : nullptr, tab.tw(), a.lossp, a.inv_npix, c.loss, s),
@@ -445,7 +498,7 @@ int adorym_workspace_bytes(const adorym_problem* p, int grads, uint64_t* bytes) 
 
 static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const float* probe, const float* pos,
                     const float* I_meas, double* loss_out, float* g_delta, float* g_beta, float* g_probe,
-                    float* g_pos, float* I_out, bool adj, float* g_nf = nullptr) {
+                    float* g_pos, float* I_out, bool adj, float* g_nf = nullptr, float* g_gaps = nullptr) {
   if (!ctx) return ADORYM_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (!p) return fail(ctx, ADORYM_EINVAL, "null problem");
@@ -461,7 +514,9 @@ static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const 
     return fail(ctx, ADORYM_EINVAL, "problem Lz/Ly/Lx differ from the registered object");
   if (g_delta && (ptr_kind(g_delta) != 1 || ptr_kind(g_beta) != 1))
     return fail(ctx, ADORYM_EINVAL, "g_delta / g_beta must be device memory");
-  const int grads = (g_delta ? 1 : 0) | (g_probe ? 2 : 0) | (g_pos ? 4 : 0) | (g_nf ? 8 : 0);
+  const int grads = (g_delta ? 1 : 0) | (g_probe ? 2 : 0) | (g_pos ? 4 : 0) | (g_nf ? 8 : 0) | (g_gaps ? 16 : 0);
+  if (g_gaps && !(p->gaps && p->L > 1))
+    return fail(ctx, ADORYM_EINVAL, "g_gaps needs variable slice spacing (gaps) and L > 1");
   if (g_nf && p->farfield) return fail(ctx, ADORYM_EINVAL, "g_nf is defined for the near-field geometry only");
   Plan pl;
   const char* msg = "";
@@ -492,6 +547,8 @@ static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const 
   const bool host_gpos = g_pos && ptr_kind(g_pos) == 0;
   const bool host_iout = I_out && ptr_kind(I_out) == 0;
   const bool host_gnf = g_nf && ptr_kind(g_nf) == 0;
+  const bool host_ggap = g_gaps && ptr_kind(g_gaps) == 0;
+  if (g_gaps) c.g_gaps = host_ggap ? reinterpret_cast<float*>(ws + pl.off_s_ggap) : g_gaps;
   if (g_nf) c.g_nf = host_gnf ? reinterpret_cast<float*>(ws + pl.off_s_gnf) : g_nf;
   c.loss = loss_out ? (host_loss ? reinterpret_cast<double*>(ws + pl.off_loss) : loss_out) : nullptr;
   if (g_probe) {
@@ -529,6 +586,10 @@ static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const 
   }
   if (host_gnf) {
     cudaMemcpyAsync(g_nf, c.g_nf, (size_t)p->B * pl.nd * sizeof(float), cudaMemcpyDeviceToHost, s);
+    sync_after = true;
+  }
+  if (host_ggap) {
+    cudaMemcpyAsync(g_gaps, c.g_gaps, (size_t)(p->L - 1) * sizeof(float), cudaMemcpyDeviceToHost, s);
     sync_after = true;
   }
   cudaError_t e = cudaGetLastError();
@@ -624,7 +685,7 @@ int adorym_loss_grad_ext(adorym_ctx* ctx, const adorym_problem* p, int obj_id, c
   if (!out) return run_call(ctx, p, obj_id, probe, pos, I_meas, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                             true);
   return run_call(ctx, p, obj_id, probe, pos, I_meas, out->loss, out->g_delta, out->g_beta, out->g_probe, out->g_pos,
-                  out->I_out, true, out->g_nf);
+                  out->I_out, true, out->g_nf, out->g_gaps);
 }
 
 }  // extern "C"

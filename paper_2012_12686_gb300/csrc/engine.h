@@ -29,12 +29,14 @@ struct Plan {
   int cp = 1, ncp = 1, nd = 1;
   bool far = true, tomo = false, adj = false;
   bool want_obj = false, want_probe = false, want_pos = false, want_loss = false, want_nf = false;
+  bool gaps = false, want_gaps = false;   // variable slice spacing / its gradient
   size_t NN = 0;
   size_t off_phat = 0, off_ckpt = 0, off_seg = 0, off_park = 0, off_far = 0, off_gI = 0, off_fbar = 0,
          off_lossp = 0, off_qacc = 0, off_qsum = 0, off_T = 0, off_grot = 0, off_loss = 0;
   // two-pass path (N >= 256)
   size_t off_FA = 0, off_FR = 0, off_tmp = 0, off_posp = 0;
   size_t off_box = 0;   // int4 bounding box of the batch's patches
+  size_t off_spck = 0, off_spseg = 0, off_gapp = 0, off_s_ggap = 0;   // slice-gap gradient
   // staging for host-memory arguments
   size_t off_s_probe = 0, off_s_pos = 0, off_s_meas = 0, off_s_gprobe = 0, off_s_gpos = 0, off_s_iout = 0,
          off_s_gnf = 0;
@@ -54,6 +56,7 @@ struct CallPtrs {
   float* g_pos = nullptr;
   float* g_nf = nullptr;
   float* I_out = nullptr;
+  float* g_gaps = nullptr;
 };
 
 int validate(const adorym_problem& p, const char** err);
@@ -64,12 +67,14 @@ size_t table_count(const adorym_problem& p);
 void fill_tables(const adorym_problem& p, float2* out);
 
 struct Tables {
-  float2* dev = nullptr;   // [tw N][hy N][hx N][hd n_dist*N]
-  int N = 0, nd = 0;
+  float2* dev = nullptr;   // [tw N][hy N][hx N][hd n_dist*N][hyj (L-1)*N][hxj (L-1)*N]
+  int N = 0, nd = 0, ngap = 0;
   const float2* tw() const { return dev; }
   const float2* hy() const { return dev + N; }
   const float2* hx() const { return dev + 2 * N; }
   const float2* hd() const { return dev + 3 * N; }
+  const float2* hyj() const { return ngap ? dev + (size_t)(3 + nd) * N : nullptr; }
+  const float2* hxj() const { return ngap ? dev + (size_t)(3 + nd) * N + (size_t)ngap * N : nullptr; }
 };
 
 // Enqueue every kernel of one call on `s` with workspace `ws` (no allocation, no host sync):

@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
 
   const int Ly = a.Ly, Lx = a.Lx;
   const float kdz = a.kdz;
+  int cur_mode = 0;   // probe mode being processed (partials of mode 0 overwrite, later modes add)
   // transmission T_j at patch pixel (y, x); voxels outside the volume are vacuum (T = 1)
   auto tload = [&](int j, int y, int x) -> float2 {
     const int gy = p0y + y, gx = p0x + x, gz = FAR ? j : b * L + j;
@@ -104,29 +105,50 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
       for (int k = 0; k < N1; ++k) pa[k] = tload(j, N2 * k + t, x);
     };
   };
-  auto hop = [&](V2& v, int ky, int t) {
-    const float2 h = hy[ky];
-#pragma unroll
-    for (int i = 0; i < N2; ++i) v[i] = cmul(cmul(v[i], h), hx[t + N1 * i]);
-  };
-  auto hop_conj = [&](V2& v, int ky, int t) {
-    const float2 h = hy[ky];
-#pragma unroll
-    for (int i = 0; i < N2; ++i) v[i] = cmulc(cmulc(v[i], h), hx[t + N1 * i]);
-  };
-  // the rest of a propagation step after C14: C2, R1, R23(H or conj H), R4, C3
-  auto propagate_tail = [&](bool adjoint) {
+  // the rest of a propagation step after C14: C2, R1, R23(H_gap or conj H_gap), R4, C3.  With
+  // variable spacing the propagator factors of gap `gapj` come from the per-gap tables; spec_out
+  // keeps F[psi_{gapj+1}] / N^2 for the slice-gap gradient, spec_in (adjoint) accumulates
+  // dL/dc_gap = -pi sum |f|^2 Im(conj(F[psibar]) F[psi]) into gapp
+  auto propagate_tail = [&](bool adjoint, int gapj, float2* spec_out, const float2* spec_in) {
+    const float2* hyp = a.hyj ? a.hyj + (size_t)gapj * N : hy;
+    const float2* hxp = a.hxj ? a.hxj + (size_t)gapj * N : hx;
     pass_c23<N, false, -1>(A, tw);
     __syncthreads();
     pass_r14<N, true, -1>(A, tw);
     __syncthreads();
-    if (adjoint) pass_r23<N, -1, +1>(A, tw, hop_conj);
-    else pass_r23<N, -1, +1>(A, tw, hop);
+    float gs = 0.f;
+    pass_r23<N, -1, +1>(A, tw, [&](V2& v, int ky, int t) {
+      const float2 h = hyp[ky];
+      const float fy = (float)freqd(ky, N);
+#pragma unroll
+      for (int i = 0; i < N2; ++i) {
+        const int kx = t + N1 * i;
+        const float2 H = cmul(h, hxp[kx]);
+        if (!adjoint) {
+          v[i] = cmul(v[i], H);
+          if (spec_out) spec_out[ky * N + kx] = v[i];
+        } else {
+          if (spec_in) {
+            const float fx = (float)freqd(kx, N);
+            gs += (fy * fy + fx * fx) * cmulc(spec_in[ky * N + kx], v[i]).y;
+          }
+          v[i] = cmulc(v[i], H);
+        }
+      }
+    });
     __syncthreads();
     pass_r14<N, false, +1>(A, tw);
     __syncthreads();
     pass_c23<N, true, +1>(A, tw);
     __syncthreads();
+    if (adjoint && spec_in) {
+      const double g = block_sum<NT>((double)gs, red);
+      if (threadIdx.x == 0) {
+        double* gp = a.gapp + (size_t)blockIdx.x * (a.L - 1) + gapj;
+        const double val = -3.14159265358979323846 * g;
+        *gp = (cur_mode == 0) ? val : *gp + val;
+      }
+    }
   };
 
   const bool adj = a.adj != 0;
@@ -138,9 +160,22 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
   float* gI_b = a.gI + (size_t)b * nd * NN;
 
   // ------------------------------------------------------------------ forward
+  const bool want_gap = adj && a.gapp != nullptr;
+  float2* spck_b = want_gap ? a.spck + (size_t)b * M * ncp * NN : nullptr;
+  float2* spsg_b = want_gap ? a.spseg + (size_t)b * M * cp * NN : nullptr;
   for (int m = 0; m < M; ++m) {
+    cur_mode = m;
     float2* ck = ck_b + (size_t)m * ncp * NN;
     float2* sg = seg_b + (size_t)m * cp * NN;
+    float2* spck = want_gap ? spck_b + (size_t)m * ncp * NN : nullptr;
+    float2* spsg = want_gap ? spsg_b + (size_t)m * cp * NN : nullptr;
+    // spectrum slot of slice jn (propagated into by gap jn - 1): checkpoint or last segment
+    auto spec_slot_fwd = [&](int jn) -> float2* {
+      if (!want_gap) return nullptr;
+      if (jn % cp == 0) return spck + (size_t)(jn / cp) * NN;
+      if (jn > j0_last) return spsg + (size_t)(jn - j0_last) * NN;
+      return nullptr;
+    };
     // spatial op of slice j: store psi_j where the adjoint needs it, then modulate
     auto fwd_op = [&](int j, bool from_pb) {
       return [&, j, from_pb](V1& v, V1& pa, V1& pb, int x, int t) {
@@ -191,7 +226,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
       }
       __syncthreads();
       if (!last) {
-        propagate_tail(false);
+        propagate_tail(false, j, spec_slot_fwd(j + 1), nullptr);
         continue;
       }
       if (FAR) {
@@ -295,8 +330,11 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
   double gacc[3 * 4] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};   // per distance: shift y, x; N_F
   const bool want_obj = a.gd != nullptr;
   for (int m = 0; m < M; ++m) {
+    cur_mode = m;
     float2* ck = ck_b + (size_t)m * ncp * NN;
     float2* sg = seg_b + (size_t)m * cp * NN;
+    float2* spck = want_gap ? spck_b + (size_t)m * ncp * NN : nullptr;
+    float2* spsg = want_gap ? spsg_b + (size_t)m * cp * NN : nullptr;
     if (FAR) {
       // phibar_{L-1} = (1/N) DFT_-[2 gI Psi]
       const float2* fm = a.far + ((size_t)b * M + m) * NN;
@@ -403,7 +441,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
             });
           }
           __syncthreads();
-          propagate_tail(false);
+          propagate_tail(false, j, want_gap ? spsg + (size_t)(j + 1 - j0) * NN : nullptr, nullptr);
         }
         pass_c14<N, +1, 0, true, false>(A, tw, NoPre(), [&](V1& v, V1&, V1&, int x, int t) {
 #pragma unroll
@@ -448,7 +486,8 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
         else pass_c14<N, +1, -1, true, true>(A, tw, pre, op);
         __syncthreads();
         if (!first) {
-          propagate_tail(true);
+          const float2* sp_in = !want_gap ? nullptr : (j == j0) ? spck + (size_t)s * NN : spsg + (size_t)(j - j0) * NN;
+          propagate_tail(true, j - 1, nullptr, sp_in);
           continue;
         }
         if (!FAR) continue;
@@ -556,6 +595,20 @@ __global__ void __launch_bounds__(256) k_qsum(const float2* __restrict__ qacc, f
     }
     qsum[i] = make_float2((float)r, (float)im);
   }
+}
+
+__global__ void k_gap_final(const double* __restrict__ gapp, int B, int ngap, int parts, float* __restrict__ g) {
+  for (int j = threadIdx.x; j < ngap; j += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < B; ++b)
+      for (int k = 0; k < parts; ++k) s += gapp[((size_t)b * ngap + j) * parts + k];
+    g[j] = (float)s;
+  }
+}
+
+cudaError_t launch_gap_final(const double* gapp, int B, int ngap, int parts, float* g_gap, cudaStream_t s) {
+  k_gap_final<<<1, 256, 0, s>>>(gapp, B, ngap, parts, g_gap);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_qsum(const float2* qacc, float2* qsum, int B, size_t MNN, cudaStream_t s) {

@@ -259,9 +259,13 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
   const bool FAR = a.farfield != 0;
   const int b = f, m = a.m;
   const size_t fo = ((size_t)b * a.M + m) * NN;
+  // propagator factors of this launch's gap (variable spacing) or the uniform ones
+  const int gap = (MODE == C_PROP_ADJ) ? a.j - 1 : a.j;
+  const float2* hysrc = (a.hyj && (MODE == C_PROP || MODE == C_PROP_ADJ)) ? a.hyj + (size_t)gap * N : a.hy;
+  const float2* hxsrc = (a.hxj && (MODE == C_PROP || MODE == C_PROP_ADJ)) ? a.hxj + (size_t)gap * N : a.hx;
   for (int i = threadIdx.x; i < N; i += NT2) {
     tw[i] = a.tw[i];
-    hy[i] = a.hy[i];
+    hy[i] = hysrc[i];
   }
   double dry = 0.0, drx = 0.0;
   if (FAR && (MODE == C_PSI0 || MODE == C_Q)) {
@@ -314,22 +318,48 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
 
   if (MODE == C_PROP || MODE == C_PROP_ADJ) {
     float2* F = (a.buf == 1 ? a.FR : a.FA) + fo;
+    // slice-gap gradient: keep F[psi_{gap+1}] / N^2 (forward / recompute), or accumulate
+    // -pi sum |f|^2 Im(conj(F[psibar]) F[psi]) against the kept spectrum (adjoint)
+    float2* so = (MODE == C_PROP && a.spec_out)
+                     ? a.spec_out + (((size_t)b * a.M + m) * a.spo_n + a.spo_slot) * NN : nullptr;
+    const float2* si = (MODE == C_PROP_ADJ && a.spec_in)
+                           ? a.spec_in + (((size_t)b * a.M + m) * a.spi_n + a.spi_slot) * NN : nullptr;
     stage_in(F, -1);
     __syncthreads();
+    float gs = 0.f;
     for (int tau = threadIdx.x; tau < CW * N1; tau += NT2) {
-      const int c = tau % CW, t = tau / CW;
+      const int c = tau % CW, t = tau / CW, kx = p0 + c;
       float2 v[N2];
       s2_load(v, c, t, -1);
-      const float2 hx = a.hx[p0 + c];
+      const float2 hx = hxsrc[kx];
+      const float fx = freqf(kx, N);
 #pragma unroll
       for (int i = 0; i < N2; ++i) {
-        const float2 h = cmul(hy[t + N1 * i], hx);
-        v[i] = (MODE == C_PROP) ? cmul(v[i], h) : cmulc(v[i], h);
+        const int ky = t + N1 * i;
+        const float2 h = cmul(hy[ky], hx);
+        if (MODE == C_PROP) {
+          v[i] = cmul(v[i], h);
+          if (so) so[(size_t)ky * N + kx] = v[i];
+        } else {
+          if (si) {
+            const float fy = freqf(ky, N);
+            gs += (fy * fy + fx * fx) * cmulc(si[(size_t)ky * N + kx], v[i]).y;
+          }
+          v[i] = cmulc(v[i], h);
+        }
       }
       s3_store(v, c, t, +1);
     }
     __syncthreads();
     stage_out(F, +1);
+    if (si && a.gapp) {
+      const double g = block_sum2((double)gs, red);
+      if (threadIdx.x == 0) {
+        double* gp = a.gapp + (((size_t)b * (a.L - 1) + gap) * gridDim.x + blockIdx.x);
+        const double val = -3.14159265358979323846 * g;
+        *gp = (m == 0) ? val : *gp + val;
+      }
+    }
   } else if (MODE == C_PSI0 || MODE == C_SEED || MODE == C_PG) {
     // Fourier-space input from op, inverse y-transform to global
     for (int tau = threadIdx.x; tau < CW * N1; tau += NT2) {
@@ -627,6 +657,18 @@ static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEven
   const bool far = a.farfield != 0;
   const int B = a.B, M = a.M, L = a.L;
   const size_t NN = (size_t)N * N;
+  // slice-gap gradient: spectra of checkpoint slices [B][M][ncp] and of segment slices [B][M][cp]
+  float2* spck = a.spec_out;
+  float2* spsg = const_cast<float2*>(a.spec_in);
+  const bool want_gap = a.adj && a.gapp && spck && spsg;
+  const int j0_last = (a.ncp - 1) * a.cp;
+  a.spec_out = nullptr;
+  a.spec_in = nullptr;
+  auto out_slot = [&](float2* base, int n, int slot) {
+    a.spec_out = want_gap ? base : nullptr;
+    a.spo_n = n;
+    a.spo_slot = slot;
+  };
   const int nloss = (int)(B * a.nd * (NN / LOSS_PX));
   const int ncol = N / Geo2<N>::CW;
   if (ev0) cudaEventRecord(ev0, s);
@@ -643,7 +685,12 @@ static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEven
       row<N, R_FWD>(a, B, s);
       if (j < L - 1) {
         a.buf = 0;
+        const int jn = j + 1;
+        if (jn % a.cp == 0) out_slot(spck, a.ncp, jn / a.cp);
+        else if (jn > j0_last) out_slot(spsg, a.cp, jn - j0_last);
+        else out_slot(nullptr, 1, 0);
         col<N, C_PROP>(a, B, s);
+        a.spec_out = nullptr;
       } else if (far) {
         col<N, C_FAR>(a, B, s);
       } else {
@@ -679,7 +726,10 @@ static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEven
           row<N, R_RC_FIRST>(a, B, s);
           for (int j = j0 + 1; j <= j1; ++j) {
             a.buf = 1;
+            a.j = j - 1;                                  // gap j-1 -> j
+            out_slot(spsg, a.cp, j - j0);
             col<N, C_PROP>(a, B, s);
+            a.spec_out = nullptr;
             a.j = j;
             row<N, R_RC>(a, B, s);
           }
@@ -689,7 +739,13 @@ static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEven
           row<N, R_ADJ>(a, B, s);
           if (j > 0) {
             a.buf = 0;
+            if (want_gap) {
+              a.spec_in = (j == j0) ? spck : spsg;
+              a.spi_n = (j == j0) ? a.ncp : a.cp;
+              a.spi_slot = (j == j0) ? sg : j - j0;
+            }
             col<N, C_PROP_ADJ>(a, B, s);
+            a.spec_in = nullptr;
           } else if (far) {
             col<N, C_Q>(a, B, s);
           }
@@ -700,6 +756,7 @@ static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEven
   if (ev1) cudaEventRecord(ev1, s);
   if (a.adj) {
     k_final2<<<1, 256, 0, s>>>(a, nloss, ncol);
+    if (want_gap && a.ggap) launch_gap_final(a.gapp, B, L - 1, ncol, a.ggap, s);
     if (a.g_probe) {
       const size_t MNN = (size_t)M * NN;
       // per-element FP64 sum over the batch (deterministic), then back to real space

@@ -38,6 +38,12 @@ struct PathArgs {
   float* gpos;            // [B][2] or [B][n_dist][2] (overwritten), or null
   float* gnf;             // near field: [B][n_dist] dL/dN_F (overwritten), or null
   double nf[4];           // near field: Fresnel numbers
+  // sparse / variable multislice: per-gap propagator factors [L-1][N] (null: uniform hy, hx)
+  const float2* hyj;
+  const float2* hxj;
+  float2* spck;           // gap gradient: spectra F[psi_j] / N^2 of checkpoint slices [B][M][ncp][N*N]
+  float2* spseg;          //               and of segment slices [B][M][cp][N*N]
+  double* gapp;           // [B][L-1] per-position slice-gap gradient partials, or null
 };
 
 // Arguments of the two-pass path (N >= 256): fields in HBM, one row and one column kernel per
@@ -73,6 +79,13 @@ struct TPArgs {
   float* gpos;
   float* gnf;
   double nf[4];
+  const float2* hyj;       // variable slice spacing: per-gap propagator factors [L-1][N], or null
+  const float2* hxj;
+  float2* spec_out;        // per launch: base of the spectra array to write [B][M][spo_n][N*N] (or null)
+  const float2* spec_in;   // per launch: base of the spectra array to read  [B][M][spi_n][N*N] (or null)
+  int spo_slot, spo_n, spi_slot, spi_n;
+  double* gapp;            // [B][L-1][N / CW] slice-gap gradient partials, or null
+  float* ggap;             // [L-1] output
   float2* g_probe;
   double* loss_out;
   int m, j, s, j0, j1, d, buf;
@@ -81,6 +94,8 @@ struct TPArgs {
 // launchers (return cudaGetLastError())
 cudaError_t launch_probe_hat(int N, int M, const float2* probe, float2* phat, const float2* tw, cudaStream_t s);
 cudaError_t launch_path(const PathArgs& a, int farfield, cudaStream_t s);
+// g_gap[j] = sum_b gapp[b][j][k] over b and k < parts (fixed order)
+cudaError_t launch_gap_final(const double* gapp, int B, int ngap, int parts, float* g_gap, cudaStream_t s);
 cudaError_t launch_probe_grad(int N, int M, int B, int farfield, const float2* qacc, float2* qsum, float2* g_probe,
                               const float2* tw, const double* lossp, double inv_npix, double* loss_out,
                               cudaStream_t s);

@@ -66,6 +66,7 @@ extern "C" int adorym_loss_grad_noalloc(void* cuda_stream, const adorym_problem*
                                         const float* I_meas, double* loss_out, float* g_delta, float* g_beta,
                                         float* g_probe, float* g_pos, float* I_out) {
   if (!p || !delta || !beta || !probe || !pos || !I_meas) return ADORYM_EINVAL;
+  if (p->gaps && p->L > 1) return ADORYM_EINVAL;   // per-gap tables would not fit the fixed host buffer
   if ((g_delta == nullptr) != (g_beta == nullptr)) return ADORYM_EINVAL;
   const void* ptrs[] = {delta, beta, probe, pos, I_meas, loss_out, g_delta, g_beta, g_probe, g_pos, I_out};
   for (const void* q : ptrs)
@@ -88,8 +89,11 @@ extern "C" int adorym_loss_grad_noalloc(void* cuda_stream, const adorym_problem*
   if ((rc = scratch_address(dev, &ws))) return rc;
   if ((rc = prepare_kernels(*p, &msg))) return rc;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
-  // tables are built on the host stack (at most 7 * 128 values) and copied into the scratch
-  float2 tab[7 * 128];
+  // tables are built on the host stack and copied into the scratch: twiddles, two propagator
+  // factors and up to four detector factors of N <= 1024 values each
+  constexpr size_t kTab = 7 * 1024;
+  if (ntab > kTab) return ADORYM_EINVAL;
+  float2 tab[kTab];
   fill_tables(*p, tab);
   if (cudaMemcpyAsync(ws + tab_off, tab, ntab * sizeof(float2), cudaMemcpyHostToDevice, s) != cudaSuccess) {
     cudaGetLastError();
