@@ -123,10 +123,13 @@ struct Geo;
 #ifndef ADORYM_NT128
 #define ADORYM_NT128 1024
 #endif
+#ifndef ADORYM_NT64
+#define ADORYM_NT64 512
+#endif
 template <> struct Geo<8>   { static constexpr int N1 = 4, N2 = 2,  NT = 64,  MINB = 8; };
 template <> struct Geo<16>  { static constexpr int N1 = 4, N2 = 4,  NT = 64,  MINB = 8; };
 template <> struct Geo<32>  { static constexpr int N1 = 4, N2 = 8,  NT = 128, MINB = 4; };
-template <> struct Geo<64>  { static constexpr int N1 = 8, N2 = 8,  NT = 256, MINB = 2; };
+template <> struct Geo<64>  { static constexpr int N1 = 8, N2 = 8,  NT = ADORYM_NT64, MINB = 512 / ADORYM_NT64; };
 template <> struct Geo<128> { static constexpr int N1 = 8, N2 = 16, NT = ADORYM_NT128, MINB = 1; };
 
 template <int N>
