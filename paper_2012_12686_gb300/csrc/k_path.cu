@@ -1,540 +1,8 @@
-// Fused multislice forward + loss + adjoint, one CTA per position (far field) or per problem
-// (near field), wavefield resident in shared memory (N <= 128).
-//
-// Forward (Algorithm 1, per probe mode):
-//   psi_0   = IDFT_-{ DFT_-[P] exp(-2 pi i dr.nu) }                 Eq. fourier_shift
-//   phi_j   = psi_j exp(-k dz beta_j) exp(i k dz delta_j)           Eq. ri_modulation
-//   psi_j+1 = IDFT_-{ DFT_-[phi_j] H },  H = exp(i pi lambda dz |nu|^2)   Eqs. fresnel_prop, paraxial_kernel
-//   far:  Psi = (1/N) DFT_+[phi_L-1]                                 Eq. fraunhofer (negative phase convention)
-//   near: Psi_d = IDFT_-{ DFT_-[phi_L-1] H_d exp(-2 pi i s_d.nu) }   Eq. fresnel_prop to the detector
-//   I = sum_modes |Psi|^2                                            Eq. multimode
-// Loss: mean over the batch's detector pixels of Eq. lsq_loss (amplitudes, I + eps) or
-// Eq. poisson_loss (log(I + eps)), summed in FP64.
-// Adjoint (chain rule; the paper obtains it by reverse-mode AD, Sec. 2.3.1):
-//   Psibar = 2 dL/dI Psi;  phibar_L-1 = (1/N) DFT_-[Psibar] (far) or IDFT_-{sum_d conj(G_d) DFT_-[Psibar_d]} (near)
-//   psibar_j = conj(T_j) phibar_j;  dL/ddelta_j += k dz Im(psibar_j conj psi_j);
-//   dL/dbeta_j += -k dz Re(psibar_j conj psi_j);  phibar_j-1 = IDFT_-{ DFT_-[psibar_j] conj H }
-//   far: Q = DFT_-[psibar_0];  dL/dP = IDFT_-{ sum_b Q conj(ramp) } (reduced later);
-//        dL/ddr_a = Re[(1/N^2) sum_nu conj(Q) (-2 pi i nu_a) P^ ramp]
-//   near: dL/dP = sum_b psibar_0;  dL/ds_d,a = Re[(1/N^2) sum_nu conj(Q_d) (-2 pi i nu_a) Phi G_d]
-// The psi_j needed by the adjoint are not kept: psi is checkpointed every cp slices
-// (cp = ceil(sqrt(L)) by default) and each segment is recomputed from its checkpoint
-// before it is reversed (the recompute-vs-store trade-off discussed in Sec. 4).
-#include "fft_block.cuh"
-#include "kernels.cuh"
+// Launchers of the fused kernel without per-gap propagators, and the per-call probe kernels
+// around it (probe DFT, probe-gradient reduction, slice-gap gradient reduction).
+#include "k_path.cuh"
 
 namespace adorym {
-
-template <int NT>
-__device__ __forceinline__ double block_sum(double v, double* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < NT / 32; ++i) s += red[i];   // fixed order: deterministic
-  }
-  __syncthreads();
-  return s;   // valid on thread 0
-}
-
-__device__ __forceinline__ double freqd(int k, int N) { return (double)(k <= (N - 1) / 2 ? k : k - N) * (1.0 / (double)N); }
-
-// exp(-2 pi i d f_k) for k < N into out: argument formed and reduced to [-1, 1] (units of pi) in
-// FP64, evaluated in FP32
-__device__ __forceinline__ void ramp_table(float2* out, double d, int N, int NT) {
-  for (int k = threadIdx.x; k < N; k += NT) {
-    double ph = -2.0 * d * freqd(k, N);
-    ph -= 2.0 * rint(0.5 * ph);
-    float s, c;
-    sincospif((float)ph, &s, &c);
-    out[k] = make_float2(c, s);
-  }
-}
-
-template <int N, int FAR>
-__global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArgs a) {
-  using F = Field<N>;
-  constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD, NT = F::NT;
-  constexpr size_t NN = (size_t)N * N;
-  using V1 = float2[N1];
-  using V2 = float2[N2];
-  extern __shared__ float2 sm[];
-  float2* A = sm;
-  float2* tw = A + N * LD;
-  float2* hy = tw + N;
-  float2* hx = hy + N;
-  float2* ry = hx + N;
-  float2* rx = ry + N;
-  double* red = reinterpret_cast<double*>(rx + N);
-
-  const int b = blockIdx.x;
-  const int M = a.M, L = a.L, cp = a.cp, ncp = a.ncp;
-  for (int i = threadIdx.x; i < N; i += NT) {
-    tw[i] = a.tw[i];
-    hy[i] = a.hy[i];
-    hx[i] = a.hx[i];
-  }
-  int p0y = 0, p0x = 0;
-  if (FAR) {
-    // S1: integer corner p0 = floor(pos + 1/2), residual dr = pos - p0 (FP64, exact for float input)
-    const double py = a.pos[2 * b], px = a.pos[2 * b + 1];
-    const double fy = floor(py + 0.5), fx = floor(px + 0.5);
-    p0y = (int)fy;
-    p0x = (int)fx;
-    ramp_table(ry, py - fy, N, NT);
-    ramp_table(rx, px - fx, N, NT);
-  }
-  __syncthreads();
-
-  const int Ly = a.Ly, Lx = a.Lx;
-  const float kdz = a.kdz;
-  int cur_mode = 0;   // probe mode being processed (partials of mode 0 overwrite, later modes add)
-  // transmission T_j at patch pixel (y, x); voxels outside the volume are vacuum (T = 1)
-  auto tload = [&](int j, int y, int x) -> float2 {
-    const int gy = p0y + y, gx = p0x + x, gz = FAR ? j : b * L + j;
-    if (gy >= 0 && gy < Ly && gx >= 0 && gx < Lx) return __ldg(a.T + ((size_t)gz * Ly + gy) * Lx + gx);
-    return make_float2(1.f, 0.f);
-  };
-  auto pre_T = [&](int j) {
-    return [&, j](V1& pa, V1&, int x, int t) {
-#pragma unroll
-      for (int k = 0; k < N1; ++k) pa[k] = tload(j, N2 * k + t, x);
-    };
-  };
-  // the rest of a propagation step after C14: C2, R1, R23(H_gap or conj H_gap), R4, C3.  With
-  // variable spacing the propagator factors of gap `gapj` come from the per-gap tables; spec_out
-  // keeps F[psi_{gapj+1}] / N^2 for the slice-gap gradient, spec_in (adjoint) accumulates
-  // dL/dc_gap = -pi sum |f|^2 Im(conj(F[psibar]) F[psi]) into gapp
-  auto propagate_tail = [&](bool adjoint, int gapj, float2* spec_out, const float2* spec_in) {
-    const float2* hyp = a.hyj ? a.hyj + (size_t)gapj * N : hy;
-    const float2* hxp = a.hxj ? a.hxj + (size_t)gapj * N : hx;
-    pass_c23<N, false, -1>(A, tw);
-    __syncthreads();
-    pass_r14<N, true, -1>(A, tw);
-    __syncthreads();
-    float gs = 0.f;
-    pass_r23<N, -1, +1>(A, tw, [&](V2& v, int ky, int t) {
-      const float2 h = hyp[ky];
-      const float fy = (float)freqd(ky, N);
-#pragma unroll
-      for (int i = 0; i < N2; ++i) {
-        const int kx = t + N1 * i;
-        const float2 H = cmul(h, hxp[kx]);
-        if (!adjoint) {
-          v[i] = cmul(v[i], H);
-          if (spec_out) spec_out[ky * N + kx] = v[i];
-        } else {
-          if (spec_in) {
-            const float fx = (float)freqd(kx, N);
-            gs += (fy * fy + fx * fx) * cmulc(spec_in[ky * N + kx], v[i]).y;
-          }
-          v[i] = cmulc(v[i], H);
-        }
-      }
-    });
-    __syncthreads();
-    pass_r14<N, false, +1>(A, tw);
-    __syncthreads();
-    pass_c23<N, true, +1>(A, tw);
-    __syncthreads();
-    if (adjoint && spec_in) {
-      const double g = block_sum<NT>((double)gs, red);
-      if (threadIdx.x == 0) {
-        double* gp = a.gapp + (size_t)blockIdx.x * (a.L - 1) + gapj;
-        const double val = -3.14159265358979323846 * g;
-        *gp = (cur_mode == 0) ? val : *gp + val;
-      }
-    }
-  };
-
-  const bool adj = a.adj != 0;
-  const int nd = FAR ? 1 : a.n_dist;
-  const int j0_last = (ncp - 1) * cp;
-  const float invN = 1.0f / (float)N, invNN = 1.0f / (float)NN;
-  float2* ck_b = a.ckpt + (size_t)b * M * ncp * NN;
-  float2* seg_b = a.seg + (size_t)b * M * cp * NN;
-  float* gI_b = a.gI + (size_t)b * nd * NN;
-
-  // ------------------------------------------------------------------ forward
-  const bool want_gap = adj && a.gapp != nullptr;
-  float2* spck_b = want_gap ? a.spck + (size_t)b * M * ncp * NN : nullptr;
-  float2* spsg_b = want_gap ? a.spseg + (size_t)b * M * cp * NN : nullptr;
-  for (int m = 0; m < M; ++m) {
-    cur_mode = m;
-    float2* ck = ck_b + (size_t)m * ncp * NN;
-    float2* sg = seg_b + (size_t)m * cp * NN;
-    float2* spck = want_gap ? spck_b + (size_t)m * ncp * NN : nullptr;
-    float2* spsg = want_gap ? spsg_b + (size_t)m * cp * NN : nullptr;
-    // spectrum slot of slice jn (propagated into by gap jn - 1): checkpoint or last segment
-    auto spec_slot_fwd = [&](int jn) -> float2* {
-      if (!want_gap) return nullptr;
-      if (jn % cp == 0) return spck + (size_t)(jn / cp) * NN;
-      if (jn > j0_last) return spsg + (size_t)(jn - j0_last) * NN;
-      return nullptr;
-    };
-    // spatial op of slice j: store psi_j where the adjoint needs it, then modulate
-    auto fwd_op = [&](int j, bool from_pb) {
-      return [&, j, from_pb](V1& v, V1& pa, V1& pb, int x, int t) {
-#pragma unroll
-        for (int k = 0; k < N1; ++k) {
-          const int y = N2 * k + t;
-          if (from_pb) v[k] = pb[k];
-          if (adj) {
-            if (j % cp == 0) ck[(size_t)(j / cp) * NN + y * N + x] = v[k];
-            else if (j > j0_last) sg[(size_t)(j - j0_last) * NN + y * N + x] = v[k];
-          }
-          v[k] = cmul(v[k], pa[k]);
-        }
-      };
-    };
-    if (FAR) {
-      // psi_0 = IDFT_-(P^ ramp), built in Fourier space at the R23 layout
-      const float2* ph = a.phat + (size_t)m * NN;
-      pass_r23<N, 0, +1>(A, tw, [&](V2& v, int ky, int t) {
-        const float2 r = cscale(ry[ky], invNN);
-#pragma unroll
-        for (int i = 0; i < N2; ++i) {
-          const int kx = t + N1 * i;
-          v[i] = cmul(cmul(__ldg(&ph[ky * N + kx]), r), rx[kx]);
-        }
-      });
-      __syncthreads();
-      pass_r14<N, false, +1>(A, tw);
-      __syncthreads();
-      pass_c23<N, true, +1>(A, tw);
-      __syncthreads();
-    }
-    for (int j = 0; j < L; ++j) {
-      const bool last = (j == L - 1);
-      if (!FAR && j == 0) {
-        // the illumination enters through pb; near field always starts its last transform with DFT_-
-        const float2* pr = a.probe + (size_t)m * NN;
-        auto T0 = pre_T(0);
-        pass_c14<N, 0, -1, false, true>(A, tw, [&](V1& pa, V1& pb, int x, int t) {
-          T0(pa, pb, x, t);
-#pragma unroll
-          for (int k = 0; k < N1; ++k) pb[k] = __ldg(&pr[(N2 * k + t) * N + x]);
-        }, fwd_op(0, true));
-      } else if (FAR && last) {
-        pass_c14<N, +1, +1, true, true>(A, tw, pre_T(j), fwd_op(j, false));
-      } else {
-        pass_c14<N, +1, -1, true, true>(A, tw, pre_T(j), fwd_op(j, false));
-      }
-      __syncthreads();
-      if (!last) {
-        propagate_tail(false, j, spec_slot_fwd(j + 1), nullptr);
-        continue;
-      }
-      if (FAR) {
-        // Psi = (1/N) DFT_+[phi]; keep Psi, accumulate I over modes
-        pass_c23<N, false, +1>(A, tw);
-        __syncthreads();
-        pass_r14<N, true, +1>(A, tw);
-        __syncthreads();
-        float2* fm = a.far + ((size_t)b * M + m) * NN;
-        pass_r23<N, +1, 0>(A, tw, [&](V2& v, int ky, int t) {
-#pragma unroll
-          for (int i = 0; i < N2; ++i) {
-            const int p = ky * N + t + N1 * i;
-            const float2 P = cscale(v[i], invN);
-            fm[p] = P;
-            const float I = fmaf(P.x, P.x, P.y * P.y);
-            gI_b[p] = (m == 0) ? I : gI_b[p] + I;
-          }
-        });
-        __syncthreads();
-      } else {
-        // Phi = DFT_-[phi] kept at slot n_dist; then Psi_d = IDFT_-{Phi G_d} per distance
-        pass_c23<N, false, -1>(A, tw);
-        __syncthreads();
-        pass_r14<N, true, -1>(A, tw);
-        __syncthreads();
-        float2* Phi = a.far + (((size_t)b * (nd + 1) + nd) * M + m) * NN;
-        pass_r23<N, -1, 0>(A, tw, [&](V2& v, int ky, int t) {
-#pragma unroll
-          for (int i = 0; i < N2; ++i) Phi[ky * N + t + N1 * i] = v[i];
-        });
-        __syncthreads();
-        for (int d = 0; d < nd; ++d) {
-          const float* sd = a.pos + ((size_t)b * nd + d) * 2;
-          ramp_table(ry, (double)sd[0], N, NT);
-          ramp_table(rx, (double)sd[1], N, NT);
-          __syncthreads();
-          const float2* hd = a.hd + (size_t)d * N;
-          pass_r23<N, 0, +1>(A, tw, [&](V2& v, int ky, int t) {
-            const float2 gy = cscale(cmul(__ldg(&hd[ky]), ry[ky]), invNN);
-#pragma unroll
-            for (int i = 0; i < N2; ++i) {
-              const int kx = t + N1 * i;
-              v[i] = cmul(cmul(Phi[ky * N + kx], gy), cmul(__ldg(&hd[kx]), rx[kx]));
-            }
-          });
-          __syncthreads();
-          pass_r14<N, false, +1>(A, tw);
-          __syncthreads();
-          pass_c23<N, true, +1>(A, tw);
-          __syncthreads();
-          float2* fd = a.far + (((size_t)b * (nd + 1) + d) * M + m) * NN;
-          float* gId = gI_b + (size_t)d * NN;
-          pass_c14<N, +1, 0, true, false>(A, tw, NoPre(), [&](V1& v, V1&, V1&, int x, int t) {
-#pragma unroll
-            for (int k = 0; k < N1; ++k) {
-              const int p = (N2 * k + t) * N + x;
-              fd[p] = v[k];
-              const float I = fmaf(v[k].x, v[k].x, v[k].y * v[k].y);
-              gId[p] = (m == 0) ? I : gId[p] + I;
-            }
-          });
-          __syncthreads();
-        }
-      }
-    }
-  }
-
-  // ------------------------------------------------------------------ loss, dL/dI
-  {
-    const size_t npx = (size_t)nd * NN;
-    const float* Im = a.I_meas ? a.I_meas + (size_t)b * npx : nullptr;
-    float* Io = a.I_out ? a.I_out + (size_t)b * npx : nullptr;
-    const float eps = a.eps, sc = (float)a.inv_npix;
-    double acc = 0.0;
-    for (size_t p = threadIdx.x; p < npx; p += NT) {
-      const float I = gI_b[p];
-      if (Io) Io[p] = I;
-      if (!Im) continue;
-      const float im = Im[p];
-      float term, dI;
-      if (a.loss == 0) {
-        const float sI = sqrtf(I + eps), sM = sqrtf(im + eps);
-        const float df = sI - sM;
-        term = df * df;
-        dI = df / sI;
-      } else {
-        term = I - im * logf(I + eps);
-        dI = 1.0f - im / (I + eps);
-      }
-      acc += (double)term;
-      gI_b[p] = dI * sc;
-    }
-    const double s = block_sum<NT>(acc, red);
-    if (threadIdx.x == 0 && a.lossp) a.lossp[b] = s;
-  }
-  if (!adj) return;
-  __syncthreads();
-
-  // ------------------------------------------------------------------ adjoint
-  double gacc[3 * 4] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};   // per distance: shift y, x; N_F
-  const bool want_obj = a.gd != nullptr;
-  for (int m = 0; m < M; ++m) {
-    cur_mode = m;
-    float2* ck = ck_b + (size_t)m * ncp * NN;
-    float2* sg = seg_b + (size_t)m * cp * NN;
-    float2* spck = want_gap ? spck_b + (size_t)m * ncp * NN : nullptr;
-    float2* spsg = want_gap ? spsg_b + (size_t)m * cp * NN : nullptr;
-    if (FAR) {
-      // phibar_{L-1} = (1/N) DFT_-[2 gI Psi]
-      const float2* fm = a.far + ((size_t)b * M + m) * NN;
-      const float sc = 2.0f * invN;
-      pass_r23<N, 0, -1>(A, tw, [&](V2& v, int ky, int t) {
-#pragma unroll
-        for (int i = 0; i < N2; ++i) {
-          const int p = ky * N + t + N1 * i;
-          v[i] = cscale(fm[p], sc * gI_b[p]);
-        }
-      });
-      __syncthreads();
-      pass_r14<N, false, -1>(A, tw);
-      __syncthreads();
-      pass_c23<N, true, -1>(A, tw);
-      __syncthreads();
-    } else {
-      const float2* Phi = a.far + (((size_t)b * (nd + 1) + nd) * M + m) * NN;
-      float2* fb = a.fbar + (size_t)b * NN;
-      for (int d = 0; d < nd; ++d) {
-        const float* sd = a.pos + ((size_t)b * nd + d) * 2;
-        ramp_table(ry, (double)sd[0], N, NT);
-        ramp_table(rx, (double)sd[1], N, NT);
-        const float2* fd = a.far + (((size_t)b * (nd + 1) + d) * M + m) * NN;
-        const float* gId = gI_b + (size_t)d * NN;
-        __syncthreads();
-        // Q_d = DFT_-[2 gI_d Psi_d]
-        pass_c14<N, 0, -1, false, true>(A, tw, [&](V1& pa, V1& pb, int x, int t) {
-#pragma unroll
-          for (int k = 0; k < N1; ++k) {
-            const int p = (N2 * k + t) * N + x;
-            pa[k] = fd[p];
-            pb[k].x = gId[p];
-          }
-        }, [&](V1& v, V1& pa, V1& pb, int, int) {
-#pragma unroll
-          for (int k = 0; k < N1; ++k) v[k] = cscale(pa[k], 2.0f * pb[k].x);
-        });
-        __syncthreads();
-        pass_c23<N, false, -1>(A, tw);
-        __syncthreads();
-        pass_r14<N, true, -1>(A, tw);
-        __syncthreads();
-        const float2* hd = a.hd + (size_t)d * N;
-        pass_r23<N, -1, 0>(A, tw, [&](V2& v, int ky, int t) {
-          const float2 gy = cmul(__ldg(&hd[ky]), ry[ky]);
-          const float fyk = (float)freqd(ky, N);
-          float ay = 0.f, ax = 0.f, an = 0.f;
-#pragma unroll
-          for (int i = 0; i < N2; ++i) {
-            const int kx = t + N1 * i, p = ky * N + kx;
-            const float2 G = cmul(gy, cmul(__ldg(&hd[kx]), rx[kx]));
-            const float2 base = cmul(cconj(v[i]), cmul(Phi[p], G));
-            const float fxk = (float)freqd(kx, N);
-            ay += fyk * base.y;
-            ax += fxk * base.y;
-            an += (fyk * fyk + fxk * fxk) * base.y;
-            const float2 c = cmulc(v[i], G);   // conj(G) Q
-            fb[p] = (d == 0) ? c : cadd(fb[p], c);
-          }
-          gacc[3 * d] += ay;
-          gacc[3 * d + 1] += ax;
-          gacc[3 * d + 2] += an;
-        });
-        __syncthreads();
-      }
-      // phibar_{L-1} = IDFT_-{sum_d conj(G_d) Q_d}
-      pass_r23<N, 0, +1>(A, tw, [&](V2& v, int ky, int t) {
-#pragma unroll
-        for (int i = 0; i < N2; ++i) v[i] = cscale(fb[ky * N + t + N1 * i], invNN);
-      });
-      __syncthreads();
-      pass_r14<N, false, +1>(A, tw);
-      __syncthreads();
-      pass_c23<N, true, +1>(A, tw);
-      __syncthreads();
-    }
-
-    for (int s = ncp - 1; s >= 0; --s) {
-      const int j0 = s * cp, j1 = min(j0 + cp, L) - 1;
-      if (s != ncp - 1 && j1 > j0) {
-        float2* pk = a.park + (size_t)b * N * LD;
-        for (int i = threadIdx.x; i < N * LD; i += NT) pk[i] = A[i];
-        __syncthreads();
-        // recompute psi_{j0+1..j1} from the checkpoint psi_{j0}
-        for (int j = j0; j < j1; ++j) {
-          if (j == j0) {
-            auto T0 = pre_T(j);
-            pass_c14<N, 0, -1, false, true>(A, tw, [&](V1& pa, V1& pb, int x, int t) {
-              T0(pa, pb, x, t);
-#pragma unroll
-              for (int k = 0; k < N1; ++k) pb[k] = ck[(size_t)s * NN + (N2 * k + t) * N + x];
-            }, [&](V1& v, V1& pa, V1& pb, int, int) {
-#pragma unroll
-              for (int k = 0; k < N1; ++k) v[k] = cmul(pb[k], pa[k]);
-            });
-          } else {
-            pass_c14<N, +1, -1, true, true>(A, tw, pre_T(j), [&, j](V1& v, V1& pa, V1&, int x, int t) {
-#pragma unroll
-              for (int k = 0; k < N1; ++k) {
-                sg[(size_t)(j - j0) * NN + (N2 * k + t) * N + x] = v[k];
-                v[k] = cmul(v[k], pa[k]);
-              }
-            });
-          }
-          __syncthreads();
-          propagate_tail(false, j, want_gap ? spsg + (size_t)(j + 1 - j0) * NN : nullptr, nullptr);
-        }
-        pass_c14<N, +1, 0, true, false>(A, tw, NoPre(), [&](V1& v, V1&, V1&, int x, int t) {
-#pragma unroll
-          for (int k = 0; k < N1; ++k) sg[(size_t)(j1 - j0) * NN + (N2 * k + t) * N + x] = v[k];
-        });
-        __syncthreads();
-        for (int i = threadIdx.x; i < N * LD; i += NT) A[i] = pk[i];
-        __syncthreads();
-      }
-      for (int j = j1; j >= j0; --j) {
-        const bool first = (j == 0);
-        // prefetch T_j and psi_j (checkpoint or recomputed segment)
-        auto pre = [&, j](V1& pa, V1& pb, int x, int t) {
-          const float2* src = (j == j0) ? ck + (size_t)s * NN : sg + (size_t)(j - j0) * NN;
-#pragma unroll
-          for (int k = 0; k < N1; ++k) {
-            pa[k] = tload(j, N2 * k + t, x);
-            pb[k] = src[(N2 * k + t) * N + x];
-          }
-        };
-        float2* q0 = (!FAR && first && a.qacc) ? a.qacc + ((size_t)b * M + m) * NN : nullptr;
-        auto op = [&, j, q0](V1& v, V1& pa, V1& pb, int x, int t) {
-#pragma unroll
-          for (int k = 0; k < N1; ++k) {
-            const int y = N2 * k + t;
-            const float2 pbar = cmulc(v[k], pa[k]);     // psibar_j = conj(T_j) phibar_j
-            if (want_obj) {
-              const int gy = p0y + y, gx = p0x + x, gz = FAR ? j : b * L + j;
-              if (gy >= 0 && gy < Ly && gx >= 0 && gx < Lx) {
-                const float2 z = cmulc(pbar, pb[k]);    // psibar conj(psi)
-                const size_t o = ((size_t)gz * Ly + gy) * Lx + gx;
-                atomicAdd(a.gd + o, (double)(kdz * z.y));
-                atomicAdd(a.gb + o, (double)(-kdz * z.x));
-              }
-            }
-            v[k] = pbar;
-            if (q0) q0[y * N + x] = pbar;               // near field: illumination gradient
-          }
-        };
-        if (FAR && j == L - 1) pass_c14<N, -1, -1, true, true>(A, tw, pre, op);
-        else if (!FAR && first) pass_c14<N, +1, 0, true, false>(A, tw, pre, op);
-        else pass_c14<N, +1, -1, true, true>(A, tw, pre, op);
-        __syncthreads();
-        if (!first) {
-          const float2* sp_in = !want_gap ? nullptr : (j == j0) ? spck + (size_t)s * NN : spsg + (size_t)(j - j0) * NN;
-          propagate_tail(true, j - 1, nullptr, sp_in);
-          continue;
-        }
-        if (!FAR) continue;
-        // far field, j = 0: Q = DFT_-[psibar_0] -> probe and position gradients
-        pass_c23<N, false, -1>(A, tw);
-        __syncthreads();
-        pass_r14<N, true, -1>(A, tw);
-        __syncthreads();
-        const float2* ph = a.phat + (size_t)m * NN;
-        float2* q = a.qacc ? a.qacc + ((size_t)b * M + m) * NN : nullptr;
-        pass_r23<N, -1, 0>(A, tw, [&](V2& v, int ky, int t) {
-          const float2 r_y = ry[ky];
-          const float fyk = (float)freqd(ky, N);
-          float ay = 0.f, ax = 0.f;
-#pragma unroll
-          for (int i = 0; i < N2; ++i) {
-            const int kx = t + N1 * i, p = ky * N + kx;
-            const float2 r = cmul(r_y, rx[kx]);
-            const float2 base = cmul(cconj(v[i]), cmul(__ldg(&ph[p]), r));
-            ay += fyk * base.y;
-            ax += (float)freqd(kx, N) * base.y;
-            if (q) q[p] = cmulc(v[i], r);
-          }
-          gacc[0] += ay;
-          gacc[1] += ax;
-        });
-        __syncthreads();
-      }
-    }
-  }
-  if (a.gpos || a.gnf) {
-    // dL/ds_a = (2 pi / N^2) sum f_a Im(base);  dL/dN_F = (pi / (N_F^2 N^2)) sum |f|^2 Im(base)
-    const double pi = 3.14159265358979323846, sc = 2.0 * pi / (double)NN;
-    for (int d = 0; d < nd; ++d) {
-      const double gy = block_sum<NT>(gacc[3 * d], red);
-      const double gx = block_sum<NT>(gacc[3 * d + 1], red);
-      const double gn = FAR ? 0.0 : block_sum<NT>(gacc[3 * d + 2], red);
-      if (threadIdx.x == 0) {
-        if (a.gpos) {
-          a.gpos[((size_t)b * nd + d) * 2] = (float)(sc * gy);
-          a.gpos[((size_t)b * nd + d) * 2 + 1] = (float)(sc * gx);
-        }
-        if (!FAR && a.gnf) a.gnf[(size_t)b * nd + d] = (float)(pi * gn / (a.nf[d] * a.nf[d] * (double)NN));
-      }
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------- probe DFT
 template <int N>
@@ -663,12 +131,6 @@ __global__ void __launch_bounds__(Geo<N>::NT) k_probe_grad(const float2* __restr
 }
 
 // ---------------------------------------------------------------------------- launchers
-// field + tw, hy, hx, ry, rx tables + one double per warp for block reductions
-template <int N>
-static constexpr int path_smem_bytes_t() {
-  return (N * (N + 1) + 5 * N) * (int)sizeof(float2) + (Geo<N>::NT / 32) * (int)sizeof(double);
-}
-
 int path_smem_bytes(int N) {
   switch (N) {
     case 8: return path_smem_bytes_t<8>();
@@ -680,18 +142,12 @@ int path_smem_bytes(int N) {
   }
 }
 
-template <int N, int FAR>
-static cudaError_t launch_path_t(const PathArgs& a, cudaStream_t s) {
-  const int smem = path_smem_bytes(N);
-  k_path<N, FAR><<<a.B, Geo<N>::NT, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_path(const PathArgs& a, int farfield, cudaStream_t s) {
+  if (a.hyj) return launch_path_gaps(a, farfield, s);   // variable slice spacing
   switch (a.N) {
-#define ADORYM_CASE(n)                                                        \
-  case n:                                                                     \
-    return farfield ? launch_path_t<n, 1>(a, s) : launch_path_t<n, 0>(a, s);
+#define ADORYM_CASE(n)                                                                      \
+  case n:                                                                                   \
+    return farfield ? launch_path_t<n, 1, false>(a, s) : launch_path_t<n, 0, false>(a, s);
     ADORYM_CASE(8)
     ADORYM_CASE(16)
     ADORYM_CASE(32)
@@ -754,7 +210,8 @@ cudaError_t launch_probe_grad(int N, int M, int B, int farfield, const float2* q
 
 template <int N, int FAR>
 static cudaError_t prepare_t() {
-  cudaError_t e = cudaFuncSetAttribute(k_path<N, FAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, path_smem_bytes(N));
+  cudaError_t e = prepare_path_t<N, FAR, false>();
+  if (e == cudaSuccess) e = prepare_path_gaps(N, FAR);
   const int small = (N * (N + 1) + N) * (int)sizeof(float2);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_probe_hat<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, small);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_probe_grad<N, FAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, small);

@@ -94,6 +94,9 @@ struct TPArgs {
 // launchers (return cudaGetLastError())
 cudaError_t launch_probe_hat(int N, int M, const float2* probe, float2* phat, const float2* tw, cudaStream_t s);
 cudaError_t launch_path(const PathArgs& a, int farfield, cudaStream_t s);
+// the variable-spacing instantiation (a.hyj != nullptr), compiled in its own translation unit
+cudaError_t launch_path_gaps(const PathArgs& a, int farfield, cudaStream_t s);
+cudaError_t prepare_path_gaps(int N, int farfield);
 // g_gap[j] = sum_b gapp[b][j][k] over b and k < parts (fixed order)
 cudaError_t launch_gap_final(const double* gapp, int B, int ngap, int parts, float* g_gap, cudaStream_t s);
 cudaError_t launch_probe_grad(int N, int M, int B, int farfield, const float2* qacc, float2* qsum, float2* g_probe,
