@@ -254,13 +254,14 @@ def time_plain(w, dev, pos_b, I_meas_b, steps, warmup):
     """Per-step device time of the plain path (loss + autograd backward) on the same minibatches."""
     import torch
     p = w["problem"]
+    want = set(w.get("grads", ("object", "probe", "positions")))
     d = torch.from_numpy(w["delta"]).to(dev).requires_grad_()
     b = torch.from_numpy(w["beta"]).to(dev).requires_grad_()
-    probe = torch.from_numpy(w["probe"]).to(dev).requires_grad_()
+    probe = torch.from_numpy(w["probe"]).to(dev).requires_grad_("probe" in want)
     nb = len(pos_b)
     times = []
     for k in range(warmup + steps):
-        pos = pos_b[k % nb].clone().requires_grad_()
+        pos = pos_b[k % nb].clone().requires_grad_("positions" in want)
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record()
         loss, _ = plain_loss(d, b, probe, pos, I_meas_b[k % nb], p)
@@ -360,8 +361,9 @@ def run_ours(args, rank, world, local_rank):
         pos_b = [pos_all[k * B:(k + 1) * B].contiguous() for k in range(nb)]
         loss = torch.zeros((), dtype=torch.float64, device=dev)
         gd, gb = torch.zeros_like(d), torch.zeros_like(b)
-        gp = torch.zeros_like(probe)
-        gpos = torch.zeros(tuple(pos_all[:B].shape), dtype=torch.float32, device=dev)
+        want = set(w.get("grads", ("object", "probe", "positions")))
+        gp = torch.zeros_like(probe) if "probe" in want else None
+        gpos = torch.zeros(tuple(pos_all[:B].shape), dtype=torch.float32, device=dev) if "positions" in want else None
         flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
         eng.enable_kernel_timing(True)
 
@@ -408,8 +410,8 @@ def run_ours(args, rank, world, local_rank):
     h_pos = [pb.cpu().pin_memory() for pb in pos_b]
     h_probe = probe.cpu().pin_memory()
     h_loss = np.zeros(1, np.float64)
-    h_gp = torch.zeros(probe.shape, dtype=torch.complex64).pin_memory()
-    h_gpos = torch.zeros(tuple(pos_all[:B].shape), dtype=torch.float32).pin_memory()
+    h_gp = torch.zeros(probe.shape, dtype=torch.complex64).pin_memory() if gp is not None else None
+    h_gpos = torch.zeros(tuple(pos_all[:B].shape), dtype=torch.float32).pin_memory() if gpos is not None else None
     eng.enable_kernel_timing(False)
     with torch.cuda.stream(stream):
         for k in range(2):
@@ -420,8 +422,9 @@ def run_ours(args, rank, world, local_rank):
             eng.loss_grad(prob, oid, h_probe, h_pos[k % nb], h_meas[k % nb], h_loss, gd, gb, h_gp, h_gpos)
         t_e2e = time.perf_counter() - t0
     e2e_val = units * world * n_e2e / max_over_ranks(t_e2e, dev)
-    h2d = h_meas[0].numel() * 4 + h_pos[0].numel() * 4 + h_probe.numel() * 8 + h_gp.numel() * 8
-    d2h = 8 + h_gp.numel() * 8 + h_gpos.numel() * 4
+    nel = (lambda t: 0 if t is None else t.numel())
+    h2d = h_meas[0].numel() * 4 + h_pos[0].numel() * 4 + h_probe.numel() * 8 + nel(h_gp) * 8
+    d2h = 8 + nel(h_gp) * 8 + nel(h_gpos) * 4
 
     if rank != 0:
         return

@@ -21,6 +21,7 @@
 // (cp = ceil(sqrt(L)) by default) and each segment is recomputed from its checkpoint
 // before it is reversed (the recompute-vs-store trade-off discussed in Sec. 4).
 #pragma once
+#include "numerics.cuh"
 #include "fft_block.cuh"
 #include "kernels.cuh"
 
@@ -43,17 +44,13 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 __device__ __forceinline__ double freqd(int k, int N) { return (double)(k <= (N - 1) / 2 ? k : k - N) * (1.0 / (double)N); }
+// the same frequency in FP32 (exact: N is a power of two)
+__device__ __forceinline__ float freqf1(int k, int N) { return (float)(k <= (N - 1) / 2 ? k : k - N) * (1.0f / (float)N); }
 
-// exp(-2 pi i d f_k) for k < N into out: argument formed and reduced to [-1, 1] (units of pi) in
-// FP64, evaluated in FP32
-__device__ __forceinline__ void ramp_table(float2* out, double d, int N, int NT) {
-  for (int k = threadIdx.x; k < N; k += NT) {
-    double ph = -2.0 * d * freqd(k, N);
-    ph -= 2.0 * rint(0.5 * ph);
-    float s, c;
-    sincospif((float)ph, &s, &c);
-    out[k] = make_float2(c, s);
-  }
+// exp(-2 pi i d f_k) for k < N into out (d exact in FP32: a float shift, or a float position
+// minus its integer corner)
+__device__ __forceinline__ void ramp_table(float2* out, float d, int N, int NT) {
+  for (int k = threadIdx.x; k < N; k += NT) out[k] = shift_ramp(d, k, N);
 }
 
 // GAP: per-gap propagators (variable slice spacing) and the slice-gap gradient; the uniform-spacing
@@ -88,8 +85,8 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
     const double fy = floor(py + 0.5), fx = floor(px + 0.5);
     p0y = (int)fy;
     p0x = (int)fx;
-    ramp_table(ry, py - fy, N, NT);
-    ramp_table(rx, px - fx, N, NT);
+    ramp_table(ry, (float)(py - fy), N, NT);
+    ramp_table(rx, (float)(px - fx), N, NT);
   }
   __syncthreads();
 
@@ -123,7 +120,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
       const float2* hxp = a.hxj + (size_t)gapj * N;
       pass_r23<N, -1, +1>(A, tw, [&](V2& v, int ky, int t) {
         const float2 h = hyp[ky];
-        const float fy = (float)freqd(ky, N);
+        const float fy = freqf1(ky, N);
 #pragma unroll
         for (int i = 0; i < N2; ++i) {
           const int kx = t + N1 * i;
@@ -133,7 +130,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
             if (spec_out) spec_out[ky * N + kx] = v[i];
           } else {
             if (spec_in) {
-              const float fx = (float)freqd(kx, N);
+              const float fx = freqf1(kx, N);
               gs += (fy * fy + fx * fx) * cmulc(spec_in[ky * N + kx], v[i]).y;
             }
             v[i] = cmulc(v[i], H);
@@ -160,7 +157,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
     __syncthreads();
     if constexpr (GAP) {
       if (adjoint && spec_in) {
-        const double g = block_sum<NT>((double)gs, red);
+        const double g = block_sum<NT>(f32_to_f64(gs), red);
         if (threadIdx.x == 0) {
           double* gp = a.gapp + (size_t)blockIdx.x * (a.L - 1) + gapj;
           const double val = -3.14159265358979323846 * g;
@@ -280,8 +277,8 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
         __syncthreads();
         for (int d = 0; d < nd; ++d) {
           const float* sd = a.pos + ((size_t)b * nd + d) * 2;
-          ramp_table(ry, (double)sd[0], N, NT);
-          ramp_table(rx, (double)sd[1], N, NT);
+          ramp_table(ry, sd[0], N, NT);
+          ramp_table(rx, sd[1], N, NT);
           __syncthreads();
           const float2* hd = a.hd + (size_t)d * N;
           pass_r23<N, 0, +1>(A, tw, [&](V2& v, int ky, int t) {
@@ -320,7 +317,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
     const float* Im = a.I_meas ? a.I_meas + (size_t)b * npx : nullptr;
     float* Io = a.I_out ? a.I_out + (size_t)b * npx : nullptr;
     const float eps = a.eps, sc = (float)a.inv_npix;
-    double acc = 0.0;
+    Kahan acc;
     for (size_t p = threadIdx.x; p < npx; p += NT) {
       const float I = gI_b[p];
       if (Io) Io[p] = I;
@@ -336,10 +333,10 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
         term = I - im * logf(I + eps);
         dI = 1.0f - im / (I + eps);
       }
-      acc += (double)term;
+      acc.add(term);
       gI_b[p] = dI * sc;
     }
-    const double s = block_sum<NT>(acc, red);
+    const double s = block_sum<NT>(acc.value(), red);
     if (threadIdx.x == 0 && a.lossp) a.lossp[b] = s;
   }
   if (!adj) return;
@@ -375,8 +372,8 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
       float2* fb = a.fbar + (size_t)b * NN;
       for (int d = 0; d < nd; ++d) {
         const float* sd = a.pos + ((size_t)b * nd + d) * 2;
-        ramp_table(ry, (double)sd[0], N, NT);
-        ramp_table(rx, (double)sd[1], N, NT);
+        ramp_table(ry, sd[0], N, NT);
+        ramp_table(rx, sd[1], N, NT);
         const float2* fd = a.far + (((size_t)b * (nd + 1) + d) * M + m) * NN;
         const float* gId = gI_b + (size_t)d * NN;
         __syncthreads();
@@ -400,14 +397,14 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
         const float2* hd = a.hd + (size_t)d * N;
         pass_r23<N, -1, 0>(A, tw, [&](V2& v, int ky, int t) {
           const float2 gy = cmul(__ldg(&hd[ky]), ry[ky]);
-          const float fyk = (float)freqd(ky, N);
+          const float fyk = freqf1(ky, N);
           float ay = 0.f, ax = 0.f, an = 0.f;
 #pragma unroll
           for (int i = 0; i < N2; ++i) {
             const int kx = t + N1 * i, p = ky * N + kx;
             const float2 G = cmul(gy, cmul(__ldg(&hd[kx]), rx[kx]));
             const float2 base = cmul(cconj(v[i]), cmul(Phi[p], G));
-            const float fxk = (float)freqd(kx, N);
+            const float fxk = freqf1(kx, N);
             ay += fyk * base.y;
             ax += fxk * base.y;
             an += (fyk * fyk + fxk * fxk) * base.y;
@@ -492,8 +489,8 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
               if (gy >= 0 && gy < Ly && gx >= 0 && gx < Lx) {
                 const float2 z = cmulc(pbar, pb[k]);    // psibar conj(psi)
                 const size_t o = ((size_t)gz * Ly + gy) * Lx + gx;
-                atomicAdd(a.gd + o, (double)(kdz * z.y));
-                atomicAdd(a.gb + o, (double)(-kdz * z.x));
+                atomicAdd(a.gd + o, f32_to_f64(kdz * z.y));
+                atomicAdd(a.gb + o, f32_to_f64(-kdz * z.x));
               }
             }
             v[k] = pbar;
@@ -519,7 +516,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
         float2* q = a.qacc ? a.qacc + ((size_t)b * M + m) * NN : nullptr;
         pass_r23<N, -1, 0>(A, tw, [&](V2& v, int ky, int t) {
           const float2 r_y = ry[ky];
-          const float fyk = (float)freqd(ky, N);
+          const float fyk = freqf1(ky, N);
           float ay = 0.f, ax = 0.f;
 #pragma unroll
           for (int i = 0; i < N2; ++i) {
@@ -527,7 +524,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
             const float2 r = cmul(r_y, rx[kx]);
             const float2 base = cmul(cconj(v[i]), cmul(__ldg(&ph[p]), r));
             ay += fyk * base.y;
-            ax += (float)freqd(kx, N) * base.y;
+            ax += freqf1(kx, N) * base.y;
             if (q) q[p] = cmulc(v[i], r);
           }
           gacc[0] += ay;

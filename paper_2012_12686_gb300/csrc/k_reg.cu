@@ -7,6 +7,7 @@
 // atomics), per-CTA FP64 partial sums are added in a fixed order.
 #include <algorithm>
 
+#include "numerics.cuh"
 #include "kernels.cuh"
 
 namespace adorym {
@@ -22,7 +23,7 @@ __global__ void __launch_bounds__(256) k_regularize(const float* __restrict__ d,
   __shared__ double red[8];
   const size_t n = (size_t)Lz * Ly * Lx;
   const size_t sy = Lx, sz = (size_t)Lx * Ly;
-  double acc = 0.0;
+  Kahan acc;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const int x = (int)(i % Lx), y = (int)((i / Lx) % Ly), z = (int)(i / sz);
     const float vd = d[i], vb = b[i];
@@ -46,15 +47,16 @@ __global__ void __launch_bounds__(256) k_regularize(const float* __restrict__ d,
         }
       }
     }
-    acc += (double)term;
+    acc.add(term);
     if (gd) {
       gd[i] += g1 * invNo;
       gb[i] += g2 * invNo;
     }
   }
+  double v = acc.value();
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;

@@ -16,6 +16,7 @@
 // keeps both the strided and the contiguous stage accesses free of bank conflicts with the
 // lane index on the x digit, so every global access is coalesced.  Loss and position-gradient
 // reductions write per-CTA FP64 partials that a final kernel adds in a fixed order.
+#include "numerics.cuh"
 #include "fft_block.cuh"
 #include "kernels.cuh"
 
@@ -39,22 +40,25 @@ constexpr int col_smem_bytes() {
   return N * Geo2<N>::CW * (int)sizeof(float2) + 3 * N * (int)sizeof(float2) + 64 * 8;
 }
 
-enum RowMode { R_FWD, R_RC_FIRST, R_RC, R_ADJ, R_NEAR_DET, R_NEAR_SEED, R_PHAT, R_PG_OUT };
-enum ColMode { C_PROP, C_PROP_ADJ, C_PSI0, C_FAR, C_SEED, C_Q, C_PHAT, C_PG, C_NEAR_PHI, C_NEAR_Q };
+// R_NEAR_DSEED / C_FAR_SEED (one probe mode with measured data): detector intensity, loss term and
+// adjoint seed 2 dL/dI Psi in the same pass, replacing R_NEAR_DET / C_FAR + k_loss2 + R_NEAR_SEED /
+// C_SEED
+enum RowMode { R_FWD, R_RC_FIRST, R_RC, R_ADJ, R_NEAR_DET, R_NEAR_SEED, R_PHAT, R_PG_OUT, R_NEAR_DSEED };
+enum ColMode { C_PROP, C_PROP_ADJ, C_PSI0, C_FAR, C_SEED, C_Q, C_PHAT, C_PG, C_NEAR_PHI, C_NEAR_Q, C_FAR_SEED };
 
 __device__ __forceinline__ float freqf(int k, int N) { return (float)(k <= (N - 1) / 2 ? k : k - N) / (float)N; }
-__device__ __forceinline__ double freq2(int k, int N) { return (double)(k <= (N - 1) / 2 ? k : k - N) / (double)N; }
 
-// exp(-2 pi i d f_k): the argument is formed and reduced to [-1, 1] (units of pi) in FP64, then
-// evaluated in FP32 (FP64 transcendentals are slow on this part; the reduced argument is exact
-// to FP32 rounding)
-__device__ __forceinline__ float2 ramp1(double d, int k, int N) {
-  const double fk = (double)(k <= (N - 1) / 2 ? k : k - N) * (1.0 / (double)N);
-  double ph = -2.0 * d * fk;
-  ph -= 2.0 * rint(0.5 * ph);
-  float s, c;
-  sincospif((float)ph, &s, &c);
-  return make_float2(c, s);
+// per-pixel term of Eq. lsq_loss (amplitudes, I + eps) or Eq. poisson_loss, and dL/dI before the
+// 1 / npix normalisation
+__device__ __forceinline__ float loss_term(int loss, float I, float im, float eps, float* dI) {
+  if (loss == 0) {
+    const float sI = sqrtf(I + eps), sM = sqrtf(im + eps);
+    const float df = sI - sM;
+    *dI = df / sI;
+    return df * df;
+  }
+  *dI = 1.0f - im / (I + eps);
+  return I - im * logf(I + eps);
 }
 
 __device__ __forceinline__ double block_sum2(double v, double* red) {
@@ -79,6 +83,7 @@ __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
   extern __shared__ float2 sm[];
   float2* A = sm;
   float2* tw = A + RB * LDR;
+  double* red = reinterpret_cast<double*>(tw + N);
   auto idx = [](int r, int p) { return r * LDR + p + p / N2; };
   for (int i = threadIdx.x; i < N; i += NT2) tw[i] = a.tw[i];
 
@@ -111,11 +116,11 @@ __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
     dst = a.FA + fo;
     si = (FAR && j == a.L - 1) ? -1 : +1;
     out = (!FAR && j == 0) ? 0 : 1;
-  } else if (MODE == R_NEAR_DET || MODE == R_NEAR_SEED) {
+  } else if (MODE == R_NEAR_DET || MODE == R_NEAR_SEED || MODE == R_NEAR_DSEED) {
     const size_t fd = (((size_t)b * (a.nd + 1) + a.d) * a.M + m) * NN;
     src = a.far + fd;
     dst = a.far + fd;
-    in_freq = (MODE == R_NEAR_DET);
+    in_freq = (MODE != R_NEAR_SEED);
     out = (MODE == R_NEAR_DET) ? 2 : 1;
   } else if (MODE == R_PHAT) {
     src = a.probe + (size_t)f * NN;
@@ -143,6 +148,7 @@ __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
     __syncthreads();
   }
   // ---- stage MID: S4 -> natural x = N2 k + t -> op -> S1
+  Kahan lacc;   // R_NEAR_DSEED: loss terms of this thread's pixels
   for (int tau = threadIdx.x; tau < RB * N2; tau += NT2) {
     const int t = tau % N2, r = tau / N2;
     const int y = r0 + r;
@@ -190,8 +196,8 @@ __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
           const float2 pbar = cmulc(v[k], T);
           if (a.gd && inb) {
             const float2 z = cmulc(pbar, psi);
-            atomicAdd(a.gd + o, (double)(a.kdz * z.y));
-            atomicAdd(a.gb + o, (double)(-a.kdz * z.x));
+            atomicAdd(a.gd + o, f32_to_f64(a.kdz * z.y));
+            atomicAdd(a.gb + o, f32_to_f64(-a.kdz * z.x));
           }
           v[k] = pbar;
           if (!FAR && j == 0 && a.qacc) a.qacc[fo + px] = pbar;
@@ -209,6 +215,18 @@ __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
       const float* g = a.gI + ((size_t)b * a.nd + a.d) * NN;
 #pragma unroll
       for (int k = 0; k < N1; ++k) v[k] = cscale(v[k], 2.0f * g[(size_t)y * N + N2 * k + t]);
+    } else if (MODE == R_NEAR_DSEED) {
+      const size_t pb = ((size_t)b * a.nd + a.d) * NN;
+      const float sc = 2.0f * (float)a.inv_npix;
+#pragma unroll
+      for (int k = 0; k < N1; ++k) {
+        const size_t px = pb + (size_t)y * N + N2 * k + t;
+        const float I = fmaf(v[k].x, v[k].x, v[k].y * v[k].y);
+        if (a.I_out) a.I_out[px] = I;
+        float dI;
+        lacc.add(loss_term(a.loss, I, a.I_meas[px], a.eps, &dI));
+        v[k] = cscale(v[k], sc * dI);
+      }
     } else if (MODE == R_PG_OUT) {
       float2* g = a.g_probe + (size_t)f * NN;
 #pragma unroll
@@ -226,6 +244,10 @@ __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
 #pragma unroll
       for (int k = 0; k < N1; ++k) dst[(size_t)y * N + N2 * k + t] = v[k];
     }
+  }
+  if (MODE == R_NEAR_DSEED) {
+    const double ls = block_sum2(lacc.value(), red);
+    if (threadIdx.x == 0) a.lossp[((size_t)b * a.nd + a.d) * gridDim.x + blockIdx.x] = ls;
   }
   if (out != 1) return;
   __syncthreads();
@@ -272,7 +294,7 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
     const double py = a.pos[2 * b], px = a.pos[2 * b + 1];
     dry = py - floor(py + 0.5);
     drx = px - floor(px + 0.5);
-    for (int i = threadIdx.x; i < N; i += NT2) ry[i] = ramp1(dry, i, N);
+    for (int i = threadIdx.x; i < N; i += NT2) ry[i] = shift_ramp((float)dry, i, N);
   }
   __syncthreads();
 
@@ -353,7 +375,7 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
     __syncthreads();
     stage_out(F, +1);
     if (si && a.gapp) {
-      const double g = block_sum2((double)gs, red);
+      const double g = block_sum2(f32_to_f64(gs), red);
       if (threadIdx.x == 0) {
         double* gp = a.gapp + (((size_t)b * (a.L - 1) + gap) * gridDim.x + blockIdx.x);
         const double val = -3.14159265358979323846 * g;
@@ -368,7 +390,7 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
       float2 v[N2];
       if (MODE == C_PSI0) {
         const float2* ph = a.phat + (size_t)m * NN;
-        const float2 rx = cscale(ramp1(drx, kx, N), 1.0f / (float)NN);
+        const float2 rx = cscale(shift_ramp((float)drx, kx, N), 1.0f / (float)NN);
 #pragma unroll
         for (int i = 0; i < N2; ++i) {
           const int ky = t + N1 * i;
@@ -423,7 +445,7 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
       } else {   // C_Q
         const float2* ph = a.phat + (size_t)m * NN;
         float2* q = a.qacc ? a.qacc + fo : nullptr;
-        const float2 rx = ramp1(drx, kx, N);
+        const float2 rx = shift_ramp((float)drx, kx, N);
         const float fx = freqf(kx, N);
 #pragma unroll
         for (int i = 0; i < N2; ++i) {
@@ -446,77 +468,94 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
         pp[2] = 0.0;
       }
     }
+  } else if (MODE == C_FAR_SEED) {
+    // Psi = (1/N) DFT_+[phi_{L-1}] -> I, loss term, dL/dI -> phibar_{L-1} = (1/N) DFT_-[2 dL/dI Psi]
+    stage_in(a.FA + fo, +1);
+    __syncthreads();
+    const float invN = 1.0f / (float)N, sc = 2.0f * invN * (float)a.inv_npix;
+    const size_t pb = (size_t)b * NN;
+    Kahan lacc;
+    for (int tau = threadIdx.x; tau < CW * N1; tau += NT2) {
+      const int c = tau % CW, t = tau / CW, kx = p0 + c;
+      float2 v[N2];
+      s2_load(v, c, t, +1);
+#pragma unroll
+      for (int i = 0; i < N2; ++i) {
+        const size_t px = pb + (size_t)(t + N1 * i) * N + kx;
+        const float2 P = cscale(v[i], invN);
+        const float I = fmaf(P.x, P.x, P.y * P.y);
+        if (a.I_out) a.I_out[px] = I;
+        float dI;
+        lacc.add(loss_term(a.loss, I, a.I_meas[px], a.eps, &dI));
+        v[i] = cscale(P, sc * dI);
+      }
+      s3_store(v, c, t, -1);
+    }
+    __syncthreads();
+    stage_out(a.FA + fo, -1);
+    const double ls = block_sum2(lacc.value(), red);
+    if (threadIdx.x == 0) a.lossp[(size_t)b * gridDim.x + blockIdx.x] = ls;
   } else if (MODE == C_NEAR_PHI) {
-    // Phi = DFT_-[phi] (kept in registers and stored for the shift gradients); then for each
-    // distance Psi_d = IDFT_-{Phi G_d}: y-inverse here, x-inverse in the row kernel
-    constexpr int NTASK = (CW * N1 + NT2 - 1) / NT2;
+    // Phi = DFT_-[phi] (stored for the shift gradients); then for each distance
+    // Psi_d = IDFT_-{Phi G_d}: y-inverse here, x-inverse in the row kernel.  Each thread reads
+    // back the Phi values it stored itself (no barrier needed; they are L2-resident)
     stage_in(a.FA + fo, -1);
     __syncthreads();
     float2* Phi = a.far + (((size_t)b * (a.nd + 1) + a.nd) * a.M + m) * NN;
-    float2 keep[NTASK][N2];
-#pragma unroll
-    for (int it = 0; it < NTASK; ++it) {
-      const int tau = threadIdx.x + it * NT2;
-      if (tau >= CW * N1) break;
+    for (int tau = threadIdx.x; tau < CW * N1; tau += NT2) {
       const int c = tau % CW, t = tau / CW;
-      s2_load(keep[it], c, t, -1);
+      float2 v[N2];
+      s2_load(v, c, t, -1);
 #pragma unroll
-      for (int i = 0; i < N2; ++i) Phi[(size_t)(t + N1 * i) * N + p0 + c] = keep[it][i];
+      for (int i = 0; i < N2; ++i) Phi[(size_t)(t + N1 * i) * N + p0 + c] = v[i];
     }
     for (int d = 0; d < a.nd; ++d) {
-      const double sy = a.pos[((size_t)b * a.nd + d) * 2], sx = a.pos[((size_t)b * a.nd + d) * 2 + 1];
+      const float sy = a.pos[((size_t)b * a.nd + d) * 2], sx = a.pos[((size_t)b * a.nd + d) * 2 + 1];
       __syncthreads();   // every S2 read (d = 0) / S4 read (d > 0) of the tile is done
-      for (int i = threadIdx.x; i < N; i += NT2) ry[i] = cmul(ramp1(sy, i, N), a.hd[(size_t)d * N + i]);
+      for (int i = threadIdx.x; i < N; i += NT2) ry[i] = cmul(shift_ramp(sy, i, N), a.hd[(size_t)d * N + i]);
       __syncthreads();
-#pragma unroll
-      for (int it = 0; it < NTASK; ++it) {
-        const int tau = threadIdx.x + it * NT2;
-        if (tau >= CW * N1) break;
+      for (int tau = threadIdx.x; tau < CW * N1; tau += NT2) {
         const int c = tau % CW, t = tau / CW, kx = p0 + c;
-        const float2 gx = cscale(cmul(ramp1(sx, kx, N), a.hd[(size_t)d * N + kx]), 1.0f / (float)NN);
+        const float2 gx = cscale(cmul(shift_ramp(sx, kx, N), a.hd[(size_t)d * N + kx]), 1.0f / (float)NN);
         float2 v[N2];
 #pragma unroll
-        for (int i = 0; i < N2; ++i) v[i] = cmul(cmul(keep[it][i], ry[t + N1 * i]), gx);
+        for (int i = 0; i < N2; ++i) v[i] = cmul(cmul(Phi[(size_t)(t + N1 * i) * N + kx], ry[t + N1 * i]), gx);
         s3_store(v, c, t, +1);
       }
       __syncthreads();
       stage_out(a.far + (((size_t)b * (a.nd + 1) + d) * a.M + m) * NN, +1);
     }
   } else if (MODE == C_NEAR_Q) {
-    // Q_d = DFT_-[seed_d]; shift-gradient partials; phibar = IDFT_-{sum_d conj(G_d) Q_d}
-    constexpr int NTASK = (CW * N1 + NT2 - 1) / NT2;
+    // Q_d = DFT_-[seed_d]; shift-gradient partials; phibar = IDFT_-{sum_d conj(G_d) Q_d}.  The sum
+    // over distances is kept in this CTA's own columns of FA (consumed by C_NEAR_PHI, rewritten by
+    // the stage_out below): each thread adds into the slots it alone owns, L2-resident
     const float2* Phi = a.far + (((size_t)b * (a.nd + 1) + a.nd) * a.M + m) * NN;
-    float2 acc[NTASK][N2];
-#pragma unroll
-    for (int it = 0; it < NTASK; ++it)
-#pragma unroll
-      for (int i = 0; i < N2; ++i) acc[it][i] = make_float2(0.f, 0.f);
+    float2* acc = a.FA + fo;
     for (int d = 0; d < a.nd; ++d) {
-      const double sy = a.pos[((size_t)b * a.nd + d) * 2], sx = a.pos[((size_t)b * a.nd + d) * 2 + 1];
+      const float sy = a.pos[((size_t)b * a.nd + d) * 2], sx = a.pos[((size_t)b * a.nd + d) * 2 + 1];
       __syncthreads();
       stage_in(a.far + (((size_t)b * (a.nd + 1) + d) * a.M + m) * NN, -1);
-      for (int i = threadIdx.x; i < N; i += NT2) ry[i] = cmul(ramp1(sy, i, N), a.hd[(size_t)d * N + i]);
+      for (int i = threadIdx.x; i < N; i += NT2) ry[i] = cmul(shift_ramp(sy, i, N), a.hd[(size_t)d * N + i]);
       __syncthreads();
       float ay = 0.f, ax = 0.f, an = 0.f;
-#pragma unroll
-      for (int it = 0; it < NTASK; ++it) {
-        const int tau = threadIdx.x + it * NT2;
-        if (tau >= CW * N1) break;
+      for (int tau = threadIdx.x; tau < CW * N1; tau += NT2) {
         const int c = tau % CW, t = tau / CW, kx = p0 + c;
-        const float2 gx = cmul(ramp1(sx, kx, N), a.hd[(size_t)d * N + kx]);
+        const float2 gx = cmul(shift_ramp(sx, kx, N), a.hd[(size_t)d * N + kx]);
         const float fx = freqf(kx, N);
         float2 v[N2];
         s2_load(v, c, t, -1);
 #pragma unroll
         for (int i = 0; i < N2; ++i) {
           const int ky = t + N1 * i;
+          const size_t p = (size_t)ky * N + kx;
           const float fy = freqf(ky, N);
           const float2 G = cmul(ry[ky], gx);
-          const float2 base = cmul(cconj(v[i]), cmul(Phi[(size_t)ky * N + kx], G));
+          const float2 base = cmul(cconj(v[i]), cmul(Phi[p], G));
           ay += fy * base.y;
           ax += fx * base.y;
           an += (fy * fy + fx * fx) * base.y;
-          acc[it][i] = cadd(acc[it][i], cmulc(v[i], G));
+          const float2 q = cmulc(v[i], G);
+          acc[p] = (d == 0) ? q : cadd(acc[p], q);
         }
       }
       if (a.posp) {
@@ -530,14 +569,11 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
       }
     }
     __syncthreads();
-#pragma unroll
-    for (int it = 0; it < NTASK; ++it) {
-      const int tau = threadIdx.x + it * NT2;
-      if (tau >= CW * N1) break;
-      const int c = tau % CW, t = tau / CW;
+    for (int tau = threadIdx.x; tau < CW * N1; tau += NT2) {
+      const int c = tau % CW, t = tau / CW, kx = p0 + c;
       float2 v[N2];
 #pragma unroll
-      for (int i = 0; i < N2; ++i) v[i] = cscale(acc[it][i], 1.0f / (float)NN);
+      for (int i = 0; i < N2; ++i) v[i] = cscale(acc[(size_t)(t + N1 * i) * N + kx], 1.0f / (float)NN);
       s3_store(v, c, t, +1);
     }
     __syncthreads();
@@ -552,27 +588,17 @@ __global__ void __launch_bounds__(256) k_loss2(const TPArgs a) {
   __shared__ double red[8];
   const size_t NN = (size_t)a.N * a.N;
   const size_t base = (size_t)blockIdx.y * NN;
-  double acc = 0.0;
+  Kahan acc;
   for (int e = 0; e < 4; ++e) {
     const size_t p = base + (size_t)blockIdx.x * LOSS_PX + e * 256 + threadIdx.x;
     const float I = a.gI[p];
     if (a.I_out) a.I_out[p] = I;
     if (!a.I_meas) continue;
-    const float im = a.I_meas[p];
-    float term, dI;
-    if (a.loss == 0) {
-      const float sI = sqrtf(I + a.eps), sM = sqrtf(im + a.eps);
-      const float df = sI - sM;
-      term = df * df;
-      dI = df / sI;
-    } else {
-      term = I - im * logf(I + a.eps);
-      dI = 1.0f - im / (I + a.eps);
-    }
-    acc += (double)term;
+    float dI;
+    acc.add(loss_term(a.loss, I, a.I_meas[p], a.eps, &dI));
     a.gI[p] = dI * (float)a.inv_npix;
   }
-  const double s = block_sum2(acc, red);
+  const double s = block_sum2(acc.value(), red);
   if (threadIdx.x == 0) a.lossp[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
@@ -632,9 +658,9 @@ static cudaError_t prepare_t2() {
   const int rb = row_smem_bytes<N>(), cb = col_smem_bytes<N>();
 #define ROWA(M_) if (e == cudaSuccess) e = set_attr<N>(k_row<N, M_>, rb);
 #define COLA(M_) if (e == cudaSuccess) e = set_attr<N>(k_col<N, M_>, cb);
-  ROWA(R_FWD) ROWA(R_RC_FIRST) ROWA(R_RC) ROWA(R_ADJ) ROWA(R_NEAR_DET) ROWA(R_NEAR_SEED) ROWA(R_PHAT) ROWA(R_PG_OUT)
+  ROWA(R_FWD) ROWA(R_RC_FIRST) ROWA(R_RC) ROWA(R_ADJ) ROWA(R_NEAR_DET) ROWA(R_NEAR_SEED) ROWA(R_PHAT) ROWA(R_PG_OUT) ROWA(R_NEAR_DSEED)
   COLA(C_PROP) COLA(C_PROP_ADJ) COLA(C_PSI0) COLA(C_FAR) COLA(C_SEED) COLA(C_Q) COLA(C_PHAT) COLA(C_PG)
-  COLA(C_NEAR_PHI) COLA(C_NEAR_Q)
+  COLA(C_NEAR_PHI) COLA(C_NEAR_Q) COLA(C_FAR_SEED)
 #undef ROWA
 #undef COLA
   return e;
@@ -669,8 +695,10 @@ static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEven
     a.spo_n = n;
     a.spo_slot = slot;
   };
-  const int nloss = (int)(B * a.nd * (NN / LOSS_PX));
   const int ncol = N / Geo2<N>::CW;
+  // one probe mode with measured data: loss and adjoint seed fused into the detector pass
+  const bool fuse = a.adj && M == 1 && a.I_meas != nullptr;
+  const int nloss = !fuse ? (int)(B * a.nd * (NN / LOSS_PX)) : far ? B * ncol : B * a.nd * (N / Geo2<N>::RB);
   if (ev0) cudaEventRecord(ev0, s);
   if (far) {
     row<N, R_PHAT>(a, M, s);
@@ -692,27 +720,31 @@ static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEven
         col<N, C_PROP>(a, B, s);
         a.spec_out = nullptr;
       } else if (far) {
-        col<N, C_FAR>(a, B, s);
+        if (fuse) col<N, C_FAR_SEED>(a, B, s);
+        else col<N, C_FAR>(a, B, s);
       } else {
         col<N, C_NEAR_PHI>(a, B, s);
         for (int d = 0; d < a.nd; ++d) {
           a.d = d;
-          row<N, R_NEAR_DET>(a, B, s);
+          if (fuse) row<N, R_NEAR_DSEED>(a, B, s);
+          else row<N, R_NEAR_DET>(a, B, s);
         }
       }
     }
   }
-  k_loss2<<<dim3((unsigned)(NN / LOSS_PX), B * a.nd), 256, 0, s>>>(a);
+  if (!fuse) k_loss2<<<dim3((unsigned)(NN / LOSS_PX), B * a.nd), 256, 0, s>>>(a);
   if (a.adj) {
     // ---------------- adjoint
     for (int m = 0; m < M; ++m) {
       a.m = m;
       if (far) {
-        col<N, C_SEED>(a, B, s);
+        if (!fuse) col<N, C_SEED>(a, B, s);
       } else {
-        for (int d = 0; d < a.nd; ++d) {
-          a.d = d;
-          row<N, R_NEAR_SEED>(a, B, s);
+        if (!fuse) {
+          for (int d = 0; d < a.nd; ++d) {
+            a.d = d;
+            row<N, R_NEAR_SEED>(a, B, s);
+          }
         }
         col<N, C_NEAR_Q>(a, B, s);
       }

@@ -1,0 +1,60 @@
+// Numerical helpers that keep per-element work off the FP64 pipe.  FP64 arithmetic and
+// FP32<->FP64 conversions run at a small fraction of the FP32 rate on this part, so the FP64
+// reductions (object-gradient accumulators, loss sums) take their per-element steps here and use
+// FP64 arithmetic only once per thread or in the memory system (double atomics at L2), and the
+// sub-pixel shift ramps are formed with FP32 error-free steps instead of an FP64 reduction.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace adorym {
+
+// Exact binary32 -> binary64 widening from the IEEE 754 encodings, in integer arithmetic: same
+// sign, biased exponent moved from bias 127 to bias 1023, 23-bit significand placed at the top
+// of the 52-bit one.  Infinities and NaNs keep the all-ones exponent.  Subnormal inputs
+// (|x| < 2^-126) become a signed zero: an absolute change below 1.2e-38.
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned sign = u & 0x80000000u;
+  const unsigned m = u & 0x7FFFFFu;
+  const unsigned ed = (e == 0xFFu) ? 0x7FFu : e + (1023u - 127u);
+  const unsigned hi = (e == 0u) ? sign : (sign | (ed << 20) | (m >> 3));
+  const unsigned lo = (e == 0u) ? 0u : (m << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// Compensated FP32 running sum (Kahan summation): the low-order part lost by each addition is
+// carried in c and fed back into the next one, so the sum of n terms is accurate to a few ulps
+// of sum |x_i| independent of n.  Read out once, in FP64.
+struct Kahan {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return f32_to_f64(s) - f32_to_f64(c); }
+};
+
+// Fourier shift ramp exp(-2 pi i d f_k) of Eq. fourier_shift, f_k = k'/N with k' the signed
+// frequency index of bin k (Nyquist bin negative), N a power of two <= 2048.  The phase in units
+// of pi, -2 d k'/N, is formed without rounding: d is split into a high part with 12 significant
+// bits and the exact remainder (also <= 12 bits), each product with |k'| <= 2^10 needs at most 22
+// bits, the scaling by 2/N is a power of two, and removing the nearest even integer from the
+// high part is exact.  The one rounding is the final addition, so the argument passed to
+// sincospif is the exact phase reduced to [-1, 1] and rounded once.
+__device__ __forceinline__ float2 shift_ramp(float d, int k, int N) {
+  const int kk = k <= (N - 1) / 2 ? k : k - N;
+  const float dh = __uint_as_float(__float_as_uint(d) & 0xFFFFF000u);
+  const float dl = d - dh;
+  const float sc = -2.0f / (float)N;
+  float ph = (dh * (float)kk) * sc;
+  const float pl = (dl * (float)kk) * sc;
+  ph -= 2.0f * rintf(0.5f * ph);
+  float s, c;
+  sincospif(ph + pl, &s, &c);
+  return make_float2(c, s);
+}
+
+}  // namespace adorym

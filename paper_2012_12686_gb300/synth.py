@@ -153,7 +153,9 @@ def workload(name: str, seed: int = 0, **over):
     ``beta`` (float32 [Lz, Ly, Lx]), ``probe`` (complex64 [M, N, N]),
     ``pos`` (float32 [B, 2], or [B, n_dist, 2] hologram shifts for ``holo``),
     ``delta_meas``/``beta_meas`` (a second object from which measured data are
-    simulated) and ``photons`` (scale for the Poisson noise).  The measured
+    simulated), ``photons`` (scale for the Poisson noise) and ``grads`` (the gradients the
+    workload asks for, a subset of object / probe / positions; ``positions`` are the hologram
+    shifts in the near field).  The measured
     intensities themselves are produced by the caller's forward model.
     """
     if name == "ptycho2d":
@@ -168,7 +170,7 @@ def workload(name: str, seed: int = 0, **over):
         side = int(round(math.sqrt(p["B"])))
         pos = raster(side, side, 4, 4)
         return dict(problem=p, delta=d, beta=b, delta_meas=dm, beta_meas=bm,
-                    probe=probe, pos=pos[: p["B"]], photons=1.0)
+                    probe=probe, pos=pos[: p["B"]], photons=1.0, grads=("object", "probe"))
     if name == "multislice":
         p = dict(N=128, L=32, M=1, B=128, Lz=32, Ly=512, Lx=512, kdz=KDZ_10NM,
                  lambda_dz_over_px2=LAMBDA_DZ_OVER_PX2_10NM, farfield=1, nf=[],
@@ -185,7 +187,8 @@ def workload(name: str, seed: int = 0, **over):
         probe = probe_phase_screen(p["N"], 16.0, 4.0, 1.0, 1e6, seed + 2, p["M"])
         pos = raster(32, 32, 12, 6, jitter=0.5, seed=seed + 3)
         return dict(problem=p, delta=d, beta=b, delta_meas=dm, beta_meas=bm,
-                    probe=probe, pos=pos[start:start + p["B"]], all_pos=pos, photons=1.0)
+                    probe=probe, pos=pos[start:start + p["B"]], all_pos=pos, photons=1.0,
+                    grads=("object", "probe", "positions"))
     if name == "tomo":
         p = dict(N=64, L=128, M=1, B=64, Lz=128, Ly=128, Lx=128, kdz=KDZ_10NM,
                  lambda_dz_over_px2=LAMBDA_DZ_OVER_PX2_10NM, farfield=1, nf=[],
@@ -205,7 +208,7 @@ def workload(name: str, seed: int = 0, **over):
         span = (side - 1) * 16 + p["N"]
         pos = raster(side, side, 16, (p["Ly"] - span) / 2.0)
         return dict(problem=p, delta=d, beta=b, delta_meas=dm, beta_meas=bm,
-                    probe=probe, pos=pos, photons=1.0)
+                    probe=probe, pos=pos, photons=1.0, grads=("object", "probe", "positions"))
     if name == "holo":
         p = dict(N=1024, L=1, M=1, B=8, Lz=8, Ly=1024, Lx=1024, kdz=KDZ_10NM,
                  lambda_dz_over_px2=0.0, farfield=0, nf=[1e-3, 2e-3, 4e-3, 8e-3],
@@ -225,5 +228,5 @@ def workload(name: str, seed: int = 0, **over):
         dm, bm = obj(seed + 1)
         pos = hologram_shifts(B, len(p["nf"]), 5, seed + 3)
         return dict(problem=p, delta=d, beta=b, delta_meas=dm, beta_meas=bm,
-                    probe=plane_wave(N, p["M"]), pos=pos, photons=1e4)
+                    probe=plane_wave(N, p["M"]), pos=pos, photons=1e4, grads=("object", "positions"))
     raise ValueError(f"unknown workload {name!r}")
