@@ -237,7 +237,9 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
                                     (float)sth, box, s),
                 "transmission")))
     return rc;
-  if (pl.want_obj) {
+  // near field with one probe mode: one term per voxel and call, added in place by the kernels
+  const bool direct = pl.want_obj && !pl.far && p.M == 1;
+  if (pl.want_obj && !direct) {
     // the scatter-add over overlapping positions is a reduction: accumulate it in FP64
     double* acc = reinterpret_cast<double*>(W(pl.off_grot));
     if ((rc = chk(launch_zero_box(acc, acc + V, p.Lz, p.Ly, p.Lx, box, s), "zero"))) return rc;
@@ -297,6 +299,8 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
       }
       t.gd = pl.want_obj ? gd : nullptr;
       t.gb = pl.want_obj ? gb : nullptr;
+      t.gdf = direct ? c.gd : nullptr;
+      t.gbf = direct ? c.gb : nullptr;
       t.gpos = pl.want_pos ? c.g_pos : nullptr;
       t.g_probe = pl.want_probe ? c.g_probe : nullptr;
       t.loss_out = c.loss;
@@ -341,6 +345,8 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
       a.qacc = pl.want_probe ? reinterpret_cast<float2*>(W(pl.off_qacc)) : nullptr;
       a.gd = pl.want_obj ? gd : nullptr;
       a.gb = pl.want_obj ? gb : nullptr;
+      a.gdf = direct ? c.gd : nullptr;
+      a.gbf = direct ? c.gb : nullptr;
       a.gpos = pl.want_pos ? c.g_pos : nullptr;
       a.gnf = pl.want_nf ? c.g_nf : nullptr;
       for (int d = 0; d < 4; ++d) a.nf[d] = p.nf[d];
@@ -366,7 +372,7 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
         return rc;
     }
   }
-  if (pl.want_obj) {
+  if (pl.want_obj && !direct) {
     if (pl.tomo)
       rc = chk(launch_rotate_adj(gd, gb, c.gd, c.gb, p.Lz, p.Ly, p.Lx, (float)cth, (float)sth, box, s), "rotate_adj");
     else

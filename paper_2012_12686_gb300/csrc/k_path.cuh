@@ -93,17 +93,31 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
   const int Ly = a.Ly, Lx = a.Lx;
   const float kdz = a.kdz;
   int cur_mode = 0;   // probe mode being processed (partials of mode 0 overwrite, later modes add)
-  // transmission T_j at patch pixel (y, x); voxels outside the volume are vacuum (T = 1)
+  // transmission T_j at patch pixel (y, x); voxels outside the volume are vacuum (T = 1).  A patch
+  // that lies inside the volume (the usual case; CTA-uniform) skips the per-pixel bounds tests.
+  const bool interior = p0y >= 0 && p0x >= 0 && p0y + N <= Ly && p0x + N <= Lx;
+  const size_t slab = (size_t)Ly * Lx;
   auto tload = [&](int j, int y, int x) -> float2 {
     const int gy = p0y + y, gx = p0x + x, gz = FAR ? j : b * L + j;
     if (gy >= 0 && gy < Ly && gx >= 0 && gx < Lx) return __ldg(a.T + ((size_t)gz * Ly + gy) * Lx + gx);
     return make_float2(1.f, 0.f);
   };
-  auto pre_T = [&](int j) {
-    return [&, j](V1& pa, V1&, int x, int t) {
+  // offset of patch pixel (t, x) of slice j in the volume (interior patches)
+  auto voff = [&](int j, int t, int x) -> size_t {
+    return (size_t)(FAR ? j : b * L + j) * slab + (size_t)(p0y + t) * Lx + (p0x + x);
+  };
+  auto tloads = [&](V1& pa, int j, int x, int t) {
+    if (interior) {
+      const float2* p = a.T + voff(j, t, x);
+#pragma unroll
+      for (int k = 0; k < N1; ++k) pa[k] = __ldg(p + (size_t)(N2 * k) * Lx);
+    } else {
 #pragma unroll
       for (int k = 0; k < N1; ++k) pa[k] = tload(j, N2 * k + t, x);
-    };
+    }
+  };
+  auto pre_T = [&](int j) {
+    return [&, j](V1& pa, V1&, int x, int t) { tloads(pa, j, x, t); };
   };
   // the rest of a propagation step after C14: C2, R1, R23(H_gap or conj H_gap), R4, C3.  With
   // variable spacing (GAP) the propagator factors of gap `gapj` come from the per-gap tables;
@@ -344,7 +358,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
 
   // ------------------------------------------------------------------ adjoint
   double gacc[3 * 4] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};   // per distance: shift y, x; N_F
-  const bool want_obj = a.gd != nullptr;
+  const bool want_obj = a.gd != nullptr;   // FP64 accumulators (else a.gdf or nothing)
   for (int m = 0; m < M; ++m) {
     cur_mode = m;
     float2* ck = ck_b + (size_t)m * ncp * NN;
@@ -472,23 +486,33 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
         // prefetch T_j and psi_j (checkpoint or recomputed segment)
         auto pre = [&, j](V1& pa, V1& pb, int x, int t) {
           const float2* src = (j == j0) ? ck + (size_t)s * NN : sg + (size_t)(j - j0) * NN;
+          tloads(pa, j, x, t);
 #pragma unroll
-          for (int k = 0; k < N1; ++k) {
-            pa[k] = tload(j, N2 * k + t, x);
-            pb[k] = src[(N2 * k + t) * N + x];
-          }
+          for (int k = 0; k < N1; ++k) pb[k] = src[(N2 * k + t) * N + x];
         };
         float2* q0 = (!FAR && first && a.qacc) ? a.qacc + ((size_t)b * M + m) * NN : nullptr;
         auto op = [&, j, q0](V1& v, V1& pa, V1& pb, int x, int t) {
+          const size_t o0 = interior ? voff(j, t, x) : 0;
 #pragma unroll
           for (int k = 0; k < N1; ++k) {
             const int y = N2 * k + t;
             const float2 pbar = cmulc(v[k], pa[k]);     // psibar_j = conj(T_j) phibar_j
-            if (want_obj) {
-              const int gy = p0y + y, gx = p0x + x, gz = FAR ? j : b * L + j;
-              if (gy >= 0 && gy < Ly && gx >= 0 && gx < Lx) {
-                const float2 z = cmulc(pbar, pb[k]);    // psibar conj(psi)
-                const size_t o = ((size_t)gz * Ly + gy) * Lx + gx;
+            if (!FAR && a.gdf) {
+              // near field, one mode: this thread owns voxel (b L + j, y, x) for the whole call
+              const float2 z = cmulc(pbar, pb[k]);
+              const size_t o = voff(j, t, x) + (size_t)(N2 * k) * Lx;
+              a.gdf[o] += kdz * z.y;
+              a.gbf[o] -= kdz * z.x;
+            } else if (want_obj) {
+              const float2 z = cmulc(pbar, pb[k]);      // psibar conj(psi)
+              size_t o = o0 + (size_t)(N2 * k) * Lx;
+              bool in = interior;
+              if (!interior) {
+                const int gy = p0y + y, gx = p0x + x, gz = FAR ? j : b * L + j;
+                in = gy >= 0 && gy < Ly && gx >= 0 && gx < Lx;
+                o = ((size_t)gz * Ly + gy) * Lx + gx;
+              }
+              if (in) {
                 atomicAdd(a.gd + o, f32_to_f64(kdz * z.y));
                 atomicAdd(a.gb + o, f32_to_f64(-kdz * z.x));
               }

@@ -194,7 +194,12 @@ __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
         } else {   // R_ADJ
           const float2 psi = (j == a.j0) ? ck[(size_t)a.s * NN + px] : sg[(size_t)(j - a.j0) * NN + px];
           const float2 pbar = cmulc(v[k], T);
-          if (a.gd && inb) {
+          if (a.gdf) {
+            // near field, one mode: this thread owns the voxel for the whole call
+            const float2 z = cmulc(pbar, psi);
+            a.gdf[o] += a.kdz * z.y;
+            a.gbf[o] -= a.kdz * z.x;
+          } else if (a.gd && inb) {
             const float2 z = cmulc(pbar, psi);
             atomicAdd(a.gd + o, f32_to_f64(a.kdz * z.y));
             atomicAdd(a.gb + o, f32_to_f64(-a.kdz * z.x));

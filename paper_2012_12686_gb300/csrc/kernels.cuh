@@ -35,6 +35,10 @@ struct PathArgs {
   float2* qacc;           // [B][M][N*N] per-position probe-gradient partials (Fourier space)
   double* gd;             // FP64 object-gradient accumulator [Lz][Ly][Lx] (+=), or null
   double* gb;
+  // near field with one probe mode: every voxel receives exactly one term per call, so it is
+  // added straight into the caller's FP32 gradient (no accumulator, no atomics); else null
+  float* gdf;
+  float* gbf;
   float* gpos;            // [B][2] or [B][n_dist][2] (overwritten), or null
   float* gnf;             // near field: [B][n_dist] dL/dN_F (overwritten), or null
   double nf[4];           // near field: Fresnel numbers
@@ -76,6 +80,8 @@ struct TPArgs {
   float2* tmp;             // [M][N*N]
   double* gd;              // FP64 object-gradient accumulator
   double* gb;
+  float* gdf;              // direct FP32 object gradient (near field, one probe mode), else null
+  float* gbf;
   float* gpos;
   float* gnf;
   double nf[4];
