@@ -446,8 +446,7 @@ def run_ours(args, rank, world, local_rank):
                 "kernel": "k_row/k_col two-pass sequence" if N >= 256 else f"k_path<{N},near>",
                 "bytes_per_unit": bpu}
     hbm_ach = units * bytes_per_unit(N, L, cp) / (k_ms * 1e-3) / 1e9
-    src = open(os.path.join(ROOT, "paper_2012_12686_gb300", "csrc", "k_path.cu"), "rb").read() + \
-        open(os.path.join(ROOT, "paper_2012_12686_gb300", "csrc", "fft_block.cuh"), "rb").read()
+    src = kernel_source_bytes()
     traffic = profiled_traffic(hashlib.sha256(src).hexdigest()[:16])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
@@ -600,6 +599,15 @@ def run_serve(args):
                                     "throughput": float(units.sum() / (fin - arrivals[0])),
                                     "how": "measured service time per template, replayed on the same arrivals"}}
     print(json.dumps(line), flush=True)
+
+
+KERNEL_SOURCES = ("k_path.cuh", "fft_block.cuh", "numerics.cuh", "kernels.cuh")
+
+
+def kernel_source_bytes() -> bytes:
+    """Source of the fused shared-memory kernel (the files its code is compiled from)."""
+    d = os.path.join(ROOT, "paper_2012_12686_gb300", "csrc")
+    return b"".join(open(os.path.join(d, f), "rb").read() for f in KERNEL_SOURCES)
 
 
 def profiled_traffic(src_hash: str):
