@@ -47,6 +47,16 @@ int validate(const adorym_problem& p, const char** err) {
 
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// SMs of the current device (0 when there is none)
+static int device_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
 int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan* pl, const char** err) {
   int rc = validate(p, err);
   if (rc) return rc;
@@ -90,9 +100,12 @@ int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan
     q.off_gI = take(B * q.nd * NN * sizeof(float));
     q.off_lossp = take(B * q.nd * (NN / 1024) * sizeof(double));
   } else {
+    // a batch that fills at most half the SMs gives each position a second CTA that recomputes
+    // the next segment while the first reverses the current one (needs two segment slot sets)
+    q.pipe = adj && !q.gaps && q.ncp > 1 && q.cp > 1 && 2 * (long long)B <= device_sms();
     if (adj) {
       q.off_ckpt = take(B * M * q.ncp * NN * f2);
-      q.off_seg = take(B * M * q.cp * NN * f2);
+      q.off_seg = take(B * M * (q.pipe ? 2 : 1) * q.cp * NN * f2);
       q.off_park = take(B * N * (N + 1) * f2);
       if (!q.far) q.off_fbar = take(B * NN * f2);
       q.off_qacc = take(B * M * NN * f2);
@@ -322,6 +335,7 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
     a.loss = p.loss;
     a.adj = pl.adj ? 1 : 0;
     a.n_dist = pl.nd;
+    a.pipe = pl.pipe ? 1 : 0;
     a.eps = (float)p.eps;
     a.kdz = (float)p.kdz;
     a.inv_npix = 1.0 / ((double)p.B * pl.nd * (double)pl.NN);

@@ -30,6 +30,7 @@ struct Plan {
   bool far = true, tomo = false, adj = false;
   bool want_obj = false, want_probe = false, want_pos = false, want_loss = false, want_nf = false;
   bool gaps = false, want_gaps = false;   // variable slice spacing / its gradient
+  bool pipe = false;   // shared-memory path: two-CTA clusters (adjoint + segment recompute)
   size_t NN = 0;
   size_t off_phat = 0, off_ckpt = 0, off_seg = 0, off_park = 0, off_far = 0, off_gI = 0, off_fbar = 0,
          off_lossp = 0, off_qacc = 0, off_qsum = 0, off_T = 0, off_grot = 0, off_loss = 0;

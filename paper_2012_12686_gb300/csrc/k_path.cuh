@@ -20,6 +20,12 @@
 // The psi_j needed by the adjoint are not kept: psi is checkpointed every cp slices
 // (cp = ceil(sqrt(L)) by default) and each segment is recomputed from its checkpoint
 // before it is reversed (the recompute-vs-store trade-off discussed in Sec. 4).
+//
+// Pipelined variant (PIPE, batches of at most half the SM count): each position gets a cluster of
+// two CTAs.  Rank 0 runs the forward, the loss and the adjoint sweep; rank 1 recomputes segment
+// s-1 from its checkpoint while rank 0 reverses segment s, into the other half of a
+// double-buffered segment store, so the recompute leaves the critical path.  The two meet at one
+// hardware cluster barrier per segment (no spin-waits).
 #pragma once
 #include "numerics.cuh"
 #include "fft_block.cuh"
@@ -53,10 +59,17 @@ __device__ __forceinline__ void ramp_table(float2* out, float d, int N, int NT) 
   for (int k = threadIdx.x; k < N; k += NT) out[k] = shift_ramp(d, k, N);
 }
 
+// both CTAs of a cluster arrive, then wait: global and shared writes made before the barrier by
+// either CTA are visible to both after it
+__device__ __forceinline__ void cluster_barrier() {
+  __threadfence();
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // GAP: per-gap propagators (variable slice spacing) and the slice-gap gradient; the uniform-spacing
-// instantiation carries none of that code
-template <int N, int FAR, bool GAP>
-__global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArgs a) {
+// instantiation carries none of that code.  PIPE: the two-CTA cluster form described above.
+template <int N, int FAR, bool GAP, bool PIPE>
+__device__ __forceinline__ void path_body(const PathArgs& a) {
   using F = Field<N>;
   constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD, NT = F::NT;
   constexpr size_t NN = (size_t)N * N;
@@ -71,7 +84,9 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
   float2* rx = ry + N;
   double* red = reinterpret_cast<double*>(rx + N);
 
-  const int b = blockIdx.x;
+  static_assert(!(GAP && PIPE), "the pipelined form has no slice-gap gradient");
+  const int b = PIPE ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int rank = PIPE ? (int)(blockIdx.x & 1) : 0;   // cluster of two CTAs along x
   const int M = a.M, L = a.L, cp = a.cp, ncp = a.ncp;
   for (int i = threadIdx.x; i < N; i += NT) {
     tw[i] = a.tw[i];
@@ -186,17 +201,23 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
   const int j0_last = (ncp - 1) * cp;
   const float invN = 1.0f / (float)N, invNN = 1.0f / (float)NN;
   float2* ck_b = a.ckpt + (size_t)b * M * ncp * NN;
-  float2* seg_b = a.seg + (size_t)b * M * cp * NN;
+  // segment store: one set of cp slices per (b, m), two in the pipelined form (slot = s % 2)
+  constexpr int NSLOT = PIPE ? 2 : 1;
+  float2* seg_b = a.seg + (size_t)b * M * NSLOT * cp * NN;
+  auto seg_slot = [&](int m, int s) -> float2* {
+    return seg_b + ((size_t)m * NSLOT + (PIPE ? (s & 1) : 0)) * cp * NN;
+  };
   float* gI_b = a.gI + (size_t)b * nd * NN;
 
-  // ------------------------------------------------------------------ forward
   const bool want_gap = GAP && adj && a.gapp != nullptr;
   float2* spck_b = want_gap ? a.spck + (size_t)b * M * ncp * NN : nullptr;
   float2* spsg_b = want_gap ? a.spseg + (size_t)b * M * cp * NN : nullptr;
+  if (rank == 0) {
+  // ------------------------------------------------------------------ forward
   for (int m = 0; m < M; ++m) {
     cur_mode = m;
     float2* ck = ck_b + (size_t)m * ncp * NN;
-    float2* sg = seg_b + (size_t)m * cp * NN;
+    float2* sg = seg_slot(m, ncp - 1);   // the last segment is kept by the forward pass
     float2* spck = want_gap ? spck_b + (size_t)m * ncp * NN : nullptr;
     float2* spsg = want_gap ? spsg_b + (size_t)m * cp * NN : nullptr;
     // spectrum slot of slice jn (propagated into by gap jn - 1): checkpoint or last segment
@@ -353,7 +374,8 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
     const double s = block_sum<NT>(acc.value(), red);
     if (threadIdx.x == 0 && a.lossp) a.lossp[b] = s;
   }
-  if (!adj) return;
+  }   // rank 0: forward and loss
+  if (!adj) return;   // (the pipelined form always runs the adjoint)
   __syncthreads();
 
   // ------------------------------------------------------------------ adjoint
@@ -362,9 +384,53 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
   for (int m = 0; m < M; ++m) {
     cur_mode = m;
     float2* ck = ck_b + (size_t)m * ncp * NN;
-    float2* sg = seg_b + (size_t)m * cp * NN;
     float2* spck = want_gap ? spck_b + (size_t)m * ncp * NN : nullptr;
     float2* spsg = want_gap ? spsg_b + (size_t)m * cp * NN : nullptr;
+    // recompute psi_{j0+1..j1} of segment s from its checkpoint psi_{j0} into segment slot `sg`
+    // (the field in shared memory is overwritten)
+    auto recompute = [&](int s, float2* sg) {
+      const int j0 = s * cp, j1 = min(j0 + cp, L) - 1;
+      for (int j = j0; j < j1; ++j) {
+        if (j == j0) {
+          auto T0 = pre_T(j);
+          pass_c14<N, 0, -1, false, true>(A, tw, [&](V1& pa, V1& pb, int x, int t) {
+            T0(pa, pb, x, t);
+#pragma unroll
+            for (int k = 0; k < N1; ++k) pb[k] = __ldcg(ck + (size_t)s * NN + (N2 * k + t) * N + x);
+          }, [&](V1& v, V1& pa, V1& pb, int, int) {
+#pragma unroll
+            for (int k = 0; k < N1; ++k) v[k] = cmul(pb[k], pa[k]);
+          });
+        } else {
+          pass_c14<N, +1, -1, true, true>(A, tw, pre_T(j), [&, j](V1& v, V1& pa, V1&, int x, int t) {
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+              sg[(size_t)(j - j0) * NN + (N2 * k + t) * N + x] = v[k];
+              v[k] = cmul(v[k], pa[k]);
+            }
+          });
+        }
+        __syncthreads();
+        propagate_tail(false, j, want_gap ? spsg + (size_t)(j + 1 - j0) * NN : nullptr, nullptr);
+      }
+      pass_c14<N, +1, 0, true, false>(A, tw, NoPre(), [&](V1& v, V1&, V1&, int x, int t) {
+#pragma unroll
+        for (int k = 0; k < N1; ++k) sg[(size_t)(j1 - j0) * NN + (N2 * k + t) * N + x] = v[k];
+      });
+      __syncthreads();
+    };
+    if (PIPE) {
+      // checkpoints (and, for m > 0, the previous mode's sweep) are complete
+      cluster_barrier();
+      if (rank == 1) {
+        // recompute segment s - 1 while rank 0 reverses segment s; one barrier per segment
+        for (int s = ncp - 1; s >= 0; --s) {
+          if (s >= 1 && min((s - 1) * cp + cp, L) - 1 > (s - 1) * cp) recompute(s - 1, seg_slot(m, s - 1));
+          cluster_barrier();
+        }
+        continue;
+      }
+    }
     if (FAR) {
       // phibar_{L-1} = (1/N) DFT_-[2 gI Psi]
       const float2* fm = a.far + ((size_t)b * M + m) * NN;
@@ -445,39 +511,13 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
 
     for (int s = ncp - 1; s >= 0; --s) {
       const int j0 = s * cp, j1 = min(j0 + cp, L) - 1;
-      if (s != ncp - 1 && j1 > j0) {
+      float2* sg = seg_slot(m, s);
+      if (!PIPE && s != ncp - 1 && j1 > j0) {
+        // park the adjoint field, recompute the segment in shared memory, restore
         float2* pk = a.park + (size_t)b * N * LD;
         for (int i = threadIdx.x; i < N * LD; i += NT) pk[i] = A[i];
         __syncthreads();
-        // recompute psi_{j0+1..j1} from the checkpoint psi_{j0}
-        for (int j = j0; j < j1; ++j) {
-          if (j == j0) {
-            auto T0 = pre_T(j);
-            pass_c14<N, 0, -1, false, true>(A, tw, [&](V1& pa, V1& pb, int x, int t) {
-              T0(pa, pb, x, t);
-#pragma unroll
-              for (int k = 0; k < N1; ++k) pb[k] = ck[(size_t)s * NN + (N2 * k + t) * N + x];
-            }, [&](V1& v, V1& pa, V1& pb, int, int) {
-#pragma unroll
-              for (int k = 0; k < N1; ++k) v[k] = cmul(pb[k], pa[k]);
-            });
-          } else {
-            pass_c14<N, +1, -1, true, true>(A, tw, pre_T(j), [&, j](V1& v, V1& pa, V1&, int x, int t) {
-#pragma unroll
-              for (int k = 0; k < N1; ++k) {
-                sg[(size_t)(j - j0) * NN + (N2 * k + t) * N + x] = v[k];
-                v[k] = cmul(v[k], pa[k]);
-              }
-            });
-          }
-          __syncthreads();
-          propagate_tail(false, j, want_gap ? spsg + (size_t)(j + 1 - j0) * NN : nullptr, nullptr);
-        }
-        pass_c14<N, +1, 0, true, false>(A, tw, NoPre(), [&](V1& v, V1&, V1&, int x, int t) {
-#pragma unroll
-          for (int k = 0; k < N1; ++k) sg[(size_t)(j1 - j0) * NN + (N2 * k + t) * N + x] = v[k];
-        });
-        __syncthreads();
+        recompute(s, sg);
         for (int i = threadIdx.x; i < N * LD; i += NT) A[i] = pk[i];
         __syncthreads();
       }
@@ -488,7 +528,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
           const float2* src = (j == j0) ? ck + (size_t)s * NN : sg + (size_t)(j - j0) * NN;
           tloads(pa, j, x, t);
 #pragma unroll
-          for (int k = 0; k < N1; ++k) pb[k] = src[(N2 * k + t) * N + x];
+          for (int k = 0; k < N1; ++k) pb[k] = __ldcg(src + (N2 * k + t) * N + x);   // L2: written by the partner CTA
         };
         float2* q0 = (!FAR && first && a.qacc) ? a.qacc + ((size_t)b * M + m) * NN : nullptr;
         auto op = [&, j, q0](V1& v, V1& pa, V1& pb, int x, int t) {
@@ -556,9 +596,10 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
         });
         __syncthreads();
       }
+      if (PIPE) cluster_barrier();   // segment s consumed; rank 1 may overwrite its slot
     }
   }
-  if (a.gpos || a.gnf) {
+  if (rank == 0 && (a.gpos || a.gnf)) {
     // dL/ds_a = (2 pi / N^2) sum f_a Im(base);  dL/dN_F = (pi / (N_F^2 N^2)) sum |f|^2 Im(base)
     const double pi = 3.14159265358979323846, sc = 2.0 * pi / (double)NN;
     for (int d = 0; d < nd; ++d) {
@@ -577,6 +618,17 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArg
 }
 
 
+template <int N, int FAR, bool GAP>
+__global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArgs a) {
+  path_body<N, FAR, GAP, false>(a);
+}
+
+// the pipelined form: grid 2 B, clusters of two CTAs (rank 0 adjoint, rank 1 recompute)
+template <int N, int FAR>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path_pipe(const PathArgs a) {
+  path_body<N, FAR, false, true>(a);
+}
+
 // field + tw, hy, hx, ry, rx tables + one double per warp for block reductions
 template <int N>
 constexpr int path_smem_bytes_t() {
@@ -589,9 +641,20 @@ cudaError_t launch_path_t(const PathArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int N, int FAR>
+cudaError_t launch_path_pipe_t(const PathArgs& a, cudaStream_t s) {
+  k_path_pipe<N, FAR><<<2 * a.B, Geo<N>::NT, path_smem_bytes_t<N>(), s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int N, int FAR, bool GAP>
 cudaError_t prepare_path_t() {
   return cudaFuncSetAttribute(k_path<N, FAR, GAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, path_smem_bytes_t<N>());
+}
+
+template <int N, int FAR>
+cudaError_t prepare_path_pipe_t() {
+  return cudaFuncSetAttribute(k_path_pipe<N, FAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, path_smem_bytes_t<N>());
 }
 
 }  // namespace adorym

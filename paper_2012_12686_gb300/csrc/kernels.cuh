@@ -13,6 +13,7 @@ struct PathArgs {
   int loss;               // 0 = LSQ (Eq. lsq_loss), 1 = Poisson (Eq. poisson_loss)
   int adj;                // 1: run the adjoint (loss_grad); 0: forward only
   int n_dist;             // near field: number of sample-detector distances
+  int pipe;               // 1: two-CTA clusters per position (grid 2 B); seg holds two slot sets
   float eps, kdz;
   double inv_npix;        // 1 / (number of detector pixels in the batch)
   const float2* T;        // transmission exp(i kdz (delta + i beta)) [Lz][Ly][Lx] (rotated frame for tomography)
@@ -103,6 +104,9 @@ cudaError_t launch_path(const PathArgs& a, int farfield, cudaStream_t s);
 // the variable-spacing instantiation (a.hyj != nullptr), compiled in its own translation unit
 cudaError_t launch_path_gaps(const PathArgs& a, int farfield, cudaStream_t s);
 cudaError_t prepare_path_gaps(int N, int farfield);
+// the pipelined two-CTA-cluster instantiation (a.pipe != 0), in its own translation unit
+cudaError_t launch_path_pipe(const PathArgs& a, int farfield, cudaStream_t s);
+cudaError_t prepare_path_pipe(int N, int farfield);
 // g_gap[j] = sum_b gapp[b][j][k] over b and k < parts (fixed order)
 cudaError_t launch_gap_final(const double* gapp, int B, int ngap, int parts, float* g_gap, cudaStream_t s);
 cudaError_t launch_probe_grad(int N, int M, int B, int farfield, const float2* qacc, float2* qsum, float2* g_probe,

@@ -42,6 +42,7 @@ def _compare(case, workers=1, want=(True, True, True)):
     (16, 4, 1, 3, "lsq", 1),         # checkpoint every slice
     (32, 4, 1, 2, "poisson", 4),     # one segment
     (8, 1, 1, 1, "lsq", 0),          # smallest tile, one slice, one position
+    (16, 5, 1, 80, "poisson", 2),    # batch above half the SM count: single-CTA recompute path
 ])
 def test_farfield_parity(N, L, M, B, loss, cp):
     case = C.small_case(N=N, L=L, M=M, B=B, loss=loss, cp=cp, seed=N + L)
