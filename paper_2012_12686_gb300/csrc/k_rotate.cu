@@ -9,6 +9,7 @@
 #include <algorithm>
 
 #include "kernels.cuh"
+#include "numerics.cuh"
 
 namespace adorym {
 
@@ -153,7 +154,9 @@ __global__ void k_rotate_adj(const double* __restrict__ gdr, const double* __res
     const float xs = c * u + s * w + cx, zs = -s * u + c * w + cz;
     const int xa = max(0, (int)floorf(xs - 1.5f)), xb = min(Lx - 1, (int)ceilf(xs + 1.5f));
     const int za = max(0, (int)floorf(zs - 1.5f)), zb = min(Lz - 1, (int)ceilf(zs + 1.5f));
-    double ad = 0.0, ab = 0.0;
+    // the taps are FP64 sums over positions; each is narrowed once (integer arithmetic, round to
+    // nearest) and the <= 4 weighted taps are added in FP32, like the caller's FP32 gradient
+    float ad = 0.f, ab = 0.f;
     for (int zt = za; zt <= zb; ++zt) {
       for (int xt = xa; xt <= xb; ++xt) {
         const Tap t = tap(zt, xt, Lz, Lx, c, s);
@@ -164,15 +167,15 @@ __global__ void k_rotate_adj(const double* __restrict__ gdr, const double* __res
         if (t.fz == z) wz = 1.f - t.az;
         else if (t.fz + 1 == z) wz = t.az;
         else continue;
-        const double wt = (double)(wx * wz);
+        const float wt = wx * wz;
         const size_t o = ((size_t)zt * Ly + y) * Lx + xt;
-        ad = fma(wt, __ldg(gdr + o), ad);
-        ab = fma(wt, __ldg(gbr + o), ab);
+        ad = fmaf(wt, f64_to_f32(gdr + o), ad);
+        ab = fmaf(wt, f64_to_f32(gbr + o), ab);
       }
     }
     const size_t io = ((size_t)z * Ly + y) * Lx + x;
-    gd[io] = (float)((double)gd[io] + ad);
-    gb[io] = (float)((double)gb[io] + ab);
+    gd[io] += ad;
+    gb[io] += ab;
   }
 }
 
@@ -192,8 +195,8 @@ __global__ void k_grad_add(const double* __restrict__ ad, const double* __restri
   const Region R = region(box, Lz);
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n; i += (size_t)gridDim.x * blockDim.x) {
     const size_t io = ((size_t)(i / ((size_t)R.w * R.h)) * Ly + R.y0 + (i / R.w) % R.h) * Lx + R.x0 + i % R.w;
-    gd[io] = (float)((double)gd[io] + ad[io]);
-    gb[io] = (float)((double)gb[io] + ab[io]);
+    gd[io] += f64_to_f32(ad + io);   // narrowed in integer arithmetic, then one FP32 add
+    gb[io] += f64_to_f32(ab + io);
   }
 }
 

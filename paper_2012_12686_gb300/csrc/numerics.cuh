@@ -23,6 +23,27 @@ __device__ __forceinline__ double f32_to_f64(float x) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// binary64 -> binary32 narrowing from the IEEE 754 encodings (hi, lo = upper and lower 32 bits
+// of the double), in integer arithmetic, rounding to nearest with ties to even: the top 23 of the
+// 52 significand bits are kept, the 29 dropped bits decide the rounding (a carry moves into the
+// exponent, and past the largest finite value gives infinity).  Magnitudes below 2^-126 become a
+// signed zero (an absolute change below 1.2e-38); infinities stay infinite, NaNs become a NaN.
+__device__ __forceinline__ float f64bits_to_f32(unsigned hi, unsigned lo) {
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned ah = hi & 0x7FFFFFFFu;
+  const int e = (int)(ah >> 20) - (1023 - 127);
+  unsigned r = ((unsigned)max(e, 0) << 23) | ((ah & 0xFFFFFu) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1FFFFFFFu;
+  r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
+  if (e <= 0) r = 0u;
+  if (e >= 255) r = (ah > 0x7FF00000u || (ah == 0x7FF00000u && lo != 0u)) ? 0x7FC00000u : 0x7F800000u;
+  return __uint_as_float(sign | r);
+}
+__device__ __forceinline__ float f64_to_f32(const double* p) {   // load and narrow (read-only data)
+  const uint2 w = __ldg(reinterpret_cast<const uint2*>(p));
+  return f64bits_to_f32(w.y, w.x);
+}
+
 // Compensated FP32 running sum (Kahan summation): the low-order part lost by each addition is
 // carried in c and fed back into the next one, so the sum of n terms is accurate to a few ulps
 // of sum |x_i| independent of n.  Read out once, in FP64.
