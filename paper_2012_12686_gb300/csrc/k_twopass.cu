@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
       for (int k = 0; k < N1; ++k) v[k] = src[(size_t)y * N + N2 * k + t];
     }
     // spatial ops; x = N2 k + t
-    if (MODE == R_FWD || MODE == R_RC_FIRST || MODE == R_RC || MODE == R_ADJ) {
+    if (MODE == R_FWD || MODE == R_RC_FIRST || MODE == R_RC) {
       int p0y = 0, p0x = 0, gz = FAR ? j : b * a.L + j;
       if (FAR) {
         p0y = (int)floor((double)a.pos[2 * b] + 0.5);
@@ -191,21 +191,55 @@ __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
         } else if (MODE == R_RC) {
           sg[(size_t)(j - a.j0) * NN + px] = v[k];
           v[k] = cmul(v[k], T);
-        } else {   // R_ADJ
-          const float2 psi = (j == a.j0) ? ck[(size_t)a.s * NN + px] : sg[(size_t)(j - a.j0) * NN + px];
-          const float2 pbar = cmulc(v[k], T);
+        }
+      }
+    }
+    if (MODE == R_ADJ) {
+      int p0y = 0, p0x = 0, gz = FAR ? j : b * a.L + j;
+      if (FAR) {
+        p0y = (int)floor((double)a.pos[2 * b] + 0.5);
+        p0x = (int)floor((double)a.pos[2 * b + 1] + 0.5);
+      }
+      const int gy = p0y + y;
+      const bool row_in = gy >= 0 && gy < a.Ly;
+      const float2* psrc = (j == a.j0) ? a.ckpt + (((size_t)b * a.M + m) * a.ncp + a.s) * NN
+                                       : a.seg + (((size_t)b * a.M + m) * a.cp + (j - a.j0)) * NN;
+      // chunks of CH pixels: all loads of a chunk (T, psi and, in place, the gradient values)
+      // are issued before any of its stores, so they are in flight together
+      constexpr int CH = N1 >= 32 ? 4 : 8;
+#pragma unroll
+      for (int k0 = 0; k0 < N1; k0 += CH) {
+        float2 Tv[CH], pv[CH];
+        float gdv[CH], gbv[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          const int x = N2 * (k0 + c) + t, gx = p0x + x;
+          const bool inb = row_in && gx >= 0 && gx < a.Lx;
+          const size_t o = ((size_t)gz * a.Ly + gy) * a.Lx + gx;
+          Tv[c] = inb ? __ldg(a.T + o) : make_float2(1.f, 0.f);
+          pv[c] = __ldg(psrc + (size_t)y * N + x);
+          if (a.gdf) {
+            gdv[c] = a.gdf[o];
+            gbv[c] = a.gbf[o];
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          const int k = k0 + c, x = N2 * k + t, gx = p0x + x;
+          const bool inb = row_in && gx >= 0 && gx < a.Lx;
+          const size_t o = ((size_t)gz * a.Ly + gy) * a.Lx + gx;
+          const float2 pbar = cmulc(v[k], Tv[c]);
+          const float2 z = cmulc(pbar, pv[c]);
           if (a.gdf) {
             // near field, one mode: this thread owns the voxel for the whole call
-            const float2 z = cmulc(pbar, psi);
-            a.gdf[o] += a.kdz * z.y;
-            a.gbf[o] -= a.kdz * z.x;
+            a.gdf[o] = gdv[c] + a.kdz * z.y;
+            a.gbf[o] = gbv[c] - a.kdz * z.x;
           } else if (a.gd && inb) {
-            const float2 z = cmulc(pbar, psi);
             atomicAdd(a.gd + o, f32_to_f64(a.kdz * z.y));
             atomicAdd(a.gb + o, f32_to_f64(-a.kdz * z.x));
           }
           v[k] = pbar;
-          if (!FAR && j == 0 && a.qacc) a.qacc[fo + px] = pbar;
+          if (!FAR && j == 0 && a.qacc) a.qacc[fo + (size_t)y * N + x] = pbar;
         }
       }
     } else if (MODE == R_NEAR_DET) {
