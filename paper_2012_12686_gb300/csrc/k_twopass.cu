@@ -173,24 +173,34 @@ __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
       const bool row_in = gy >= 0 && gy < a.Ly;
       float2* ck = a.ckpt + ((size_t)b * a.M + m) * a.ncp * NN;
       float2* sg = a.seg + ((size_t)b * a.M + m) * a.cp * NN;
+      // transmission loads in chunks ahead of the checkpoint / segment stores
+      constexpr int CH = N1 >= 32 ? 8 : N1;
 #pragma unroll
-      for (int k = 0; k < N1; ++k) {
-        const int x = N2 * k + t, gx = p0x + x;
-        const bool inb = row_in && gx >= 0 && gx < a.Lx;
-        const size_t o = ((size_t)gz * a.Ly + gy) * a.Lx + gx;
-        const float2 T = inb ? __ldg(a.T + o) : make_float2(1.f, 0.f);
-        const size_t px = (size_t)y * N + x;
-        if (MODE == R_FWD) {
-          if (a.adj) {
-            if (j % a.cp == 0) ck[(size_t)(j / a.cp) * NN + px] = v[k];
-            else if (j > (a.ncp - 1) * a.cp) sg[(size_t)(j - (a.ncp - 1) * a.cp) * NN + px] = v[k];
+      for (int k0 = 0; k0 < N1; k0 += CH) {
+        float2 Tv[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          const int gx = p0x + N2 * (k0 + c) + t;
+          const bool inb = row_in && gx >= 0 && gx < a.Lx;
+          Tv[c] = inb ? __ldg(a.T + ((size_t)gz * a.Ly + gy) * a.Lx + gx) : make_float2(1.f, 0.f);
+        }
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          const int k = k0 + c;
+          const float2 T = Tv[c];
+          const size_t px = (size_t)y * N + N2 * k + t;
+          if (MODE == R_FWD) {
+            if (a.adj) {
+              if (j % a.cp == 0) ck[(size_t)(j / a.cp) * NN + px] = v[k];
+              else if (j > (a.ncp - 1) * a.cp) sg[(size_t)(j - (a.ncp - 1) * a.cp) * NN + px] = v[k];
+            }
+            v[k] = cmul(v[k], T);
+          } else if (MODE == R_RC_FIRST) {
+            v[k] = cmul(v[k], T);
+          } else if (MODE == R_RC) {
+            sg[(size_t)(j - a.j0) * NN + px] = v[k];
+            v[k] = cmul(v[k], T);
           }
-          v[k] = cmul(v[k], T);
-        } else if (MODE == R_RC_FIRST) {
-          v[k] = cmul(v[k], T);
-        } else if (MODE == R_RC) {
-          sg[(size_t)(j - a.j0) * NN + px] = v[k];
-          v[k] = cmul(v[k], T);
         }
       }
     }
@@ -255,15 +265,17 @@ __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
 #pragma unroll
       for (int k = 0; k < N1; ++k) v[k] = cscale(v[k], 2.0f * g[(size_t)y * N + N2 * k + t]);
     } else if (MODE == R_NEAR_DSEED) {
-      const size_t pb = ((size_t)b * a.nd + a.d) * NN;
+      const size_t pb = ((size_t)b * a.nd + a.d) * NN + (size_t)y * N + t;
       const float sc = 2.0f * (float)a.inv_npix;
+      float im[N1];   // measured intensities first (read-only), then the I_out stores
+#pragma unroll
+      for (int k = 0; k < N1; ++k) im[k] = __ldg(a.I_meas + pb + N2 * k);
 #pragma unroll
       for (int k = 0; k < N1; ++k) {
-        const size_t px = pb + (size_t)y * N + N2 * k + t;
         const float I = fmaf(v[k].x, v[k].x, v[k].y * v[k].y);
-        if (a.I_out) a.I_out[px] = I;
+        if (a.I_out) a.I_out[pb + N2 * k] = I;
         float dI;
-        lacc.add(loss_term(a.loss, I, a.I_meas[px], a.eps, &dI));
+        lacc.add(loss_term(a.loss, I, im[k], a.eps, &dI));
         v[k] = cscale(v[k], sc * dI);
       }
     } else if (MODE == R_PG_OUT) {
@@ -516,6 +528,9 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
     Kahan lacc;
     for (int tau = threadIdx.x; tau < CW * N1; tau += NT2) {
       const int c = tau % CW, t = tau / CW, kx = p0 + c;
+      float im[N2];   // measured intensities first (read-only), then the I_out stores
+#pragma unroll
+      for (int i = 0; i < N2; ++i) im[i] = __ldg(a.I_meas + pb + (size_t)(t + N1 * i) * N + kx);
       float2 v[N2];
       s2_load(v, c, t, +1);
 #pragma unroll
@@ -525,7 +540,7 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
         const float I = fmaf(P.x, P.x, P.y * P.y);
         if (a.I_out) a.I_out[px] = I;
         float dI;
-        lacc.add(loss_term(a.loss, I, a.I_meas[px], a.eps, &dI));
+        lacc.add(loss_term(a.loss, I, im[i], a.eps, &dI));
         v[i] = cscale(P, sc * dI);
       }
       s3_store(v, c, t, -1);
