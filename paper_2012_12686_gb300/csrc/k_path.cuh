@@ -353,11 +353,23 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
     float* Io = a.I_out ? a.I_out + (size_t)b * npx : nullptr;
     const float eps = a.eps, sc = (float)a.inv_npix;
     Kahan acc;
-    for (size_t p = threadIdx.x; p < npx; p += NT) {
-      const float I = gI_b[p];
+    constexpr int U = 4;   // pixels per thread whose loads are issued ahead of their stores
+    for (size_t p0 = threadIdx.x; p0 < npx; p0 += (size_t)U * NT) {
+      float Iv[U], mv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const size_t p = p0 + (size_t)u * NT;
+        Iv[u] = p < npx ? gI_b[p] : 0.f;
+        mv[u] = (Im && p < npx) ? __ldg(Im + p) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+      const size_t p = p0 + (size_t)u * NT;
+      if (p >= npx) break;
+      const float I = Iv[u];
       if (Io) Io[p] = I;
       if (!Im) continue;
-      const float im = Im[p];
+      const float im = mv[u];
       float term, dI;
       if (a.loss == 0) {
         const float sI = sqrtf(I + eps), sM = sqrtf(im + eps);
@@ -370,6 +382,7 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
       }
       acc.add(term);
       gI_b[p] = dI * sc;
+      }
     }
     const double s = block_sum<NT>(acc.value(), red);
     if (threadIdx.x == 0 && a.lossp) a.lossp[b] = s;

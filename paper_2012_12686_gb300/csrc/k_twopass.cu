@@ -598,18 +598,28 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
         const float fx = freqf(kx, N);
         float2 v[N2];
         s2_load(v, c, t, -1);
+        // Phi and the running sum in chunks, loaded ahead of the chunk's stores
+        constexpr int CH = 8;
 #pragma unroll
-        for (int i = 0; i < N2; ++i) {
-          const int ky = t + N1 * i;
-          const size_t p = (size_t)ky * N + kx;
-          const float fy = freqf(ky, N);
-          const float2 G = cmul(ry[ky], gx);
-          const float2 base = cmul(cconj(v[i]), cmul(Phi[p], G));
-          ay += fy * base.y;
-          ax += fx * base.y;
-          an += (fy * fy + fx * fx) * base.y;
-          const float2 q = cmulc(v[i], G);
-          acc[p] = (d == 0) ? q : cadd(acc[p], q);
+        for (int i0 = 0; i0 < N2; i0 += CH) {
+          float2 ph[CH], ac[CH];
+#pragma unroll
+          for (int e = 0; e < CH; ++e) {
+            const size_t p = (size_t)(t + N1 * (i0 + e)) * N + kx;
+            ph[e] = __ldg(Phi + p);
+            ac[e] = (d == 0) ? make_float2(0.f, 0.f) : acc[p];
+          }
+#pragma unroll
+          for (int e = 0; e < CH; ++e) {
+            const int i = i0 + e, ky = t + N1 * i;
+            const float fy = freqf(ky, N);
+            const float2 G = cmul(ry[ky], gx);
+            const float2 base = cmul(cconj(v[i]), cmul(ph[e], G));
+            ay += fy * base.y;
+            ax += fx * base.y;
+            an += (fy * fy + fx * fx) * base.y;
+            acc[(size_t)ky * N + kx] = cadd(ac[e], cmulc(v[i], G));
+          }
         }
       }
       if (a.posp) {
