@@ -40,11 +40,12 @@ constexpr int col_smem_bytes() {
   return N * Geo2<N>::CW * (int)sizeof(float2) + 3 * N * (int)sizeof(float2) + 64 * 8;
 }
 
-// R_NEAR_DSEED / C_FAR_SEED (one probe mode with measured data): detector intensity, loss term and
+// R_NEAR_DSEED / C_FAR_SEED (one probe mode with measured data; the _P forms for the Poisson loss,
+// so that each kernel carries one loss's code): detector intensity, loss term and
 // adjoint seed 2 dL/dI Psi in the same pass, replacing R_NEAR_DET / C_FAR + k_loss2 + R_NEAR_SEED /
 // C_SEED
-enum RowMode { R_FWD, R_RC_FIRST, R_RC, R_ADJ, R_NEAR_DET, R_NEAR_SEED, R_PHAT, R_PG_OUT, R_NEAR_DSEED };
-enum ColMode { C_PROP, C_PROP_ADJ, C_PSI0, C_FAR, C_SEED, C_Q, C_PHAT, C_PG, C_NEAR_PHI, C_NEAR_Q, C_FAR_SEED };
+enum RowMode { R_FWD, R_RC_FIRST, R_RC, R_ADJ, R_NEAR_DET, R_NEAR_SEED, R_PHAT, R_PG_OUT, R_NEAR_DSEED, R_NEAR_DSEED_P };
+enum ColMode { C_PROP, C_PROP_ADJ, C_PSI0, C_FAR, C_SEED, C_Q, C_PHAT, C_PG, C_NEAR_PHI, C_NEAR_Q, C_FAR_SEED, C_FAR_SEED_P };
 
 __device__ __forceinline__ float freqf(int k, int N) { return (float)(k <= (N - 1) / 2 ? k : k - N) / (float)N; }
 
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
     dst = a.FA + fo;
     si = (FAR && j == a.L - 1) ? -1 : +1;
     out = (!FAR && j == 0) ? 0 : 1;
-  } else if (MODE == R_NEAR_DET || MODE == R_NEAR_SEED || MODE == R_NEAR_DSEED) {
+  } else if (MODE == R_NEAR_DET || MODE == R_NEAR_SEED || MODE == R_NEAR_DSEED || MODE == R_NEAR_DSEED_P) {
     const size_t fd = (((size_t)b * (a.nd + 1) + a.d) * a.M + m) * NN;
     src = a.far + fd;
     dst = a.far + fd;
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
       const float* g = a.gI + ((size_t)b * a.nd + a.d) * NN;
 #pragma unroll
       for (int k = 0; k < N1; ++k) v[k] = cscale(v[k], 2.0f * g[(size_t)y * N + N2 * k + t]);
-    } else if (MODE == R_NEAR_DSEED) {
+    } else if (MODE == R_NEAR_DSEED || MODE == R_NEAR_DSEED_P) {
       const size_t pb = ((size_t)b * a.nd + a.d) * NN + (size_t)y * N + t;
       const float sc = 2.0f * (float)a.inv_npix;
       float im[N1];   // measured intensities first (read-only), then the I_out stores
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
         const float I = fmaf(v[k].x, v[k].x, v[k].y * v[k].y);
         if (a.I_out) a.I_out[pb + N2 * k] = I;
         float dI;
-        lacc.add(loss_term(a.loss, I, im[k], a.eps, &dI));
+        lacc.add(loss_term(MODE == R_NEAR_DSEED_P ? 1 : 0, I, im[k], a.eps, &dI));
         v[k] = cscale(v[k], sc * dI);
       }
     } else if (MODE == R_PG_OUT) {
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
       for (int k = 0; k < N1; ++k) dst[(size_t)y * N + N2 * k + t] = v[k];
     }
   }
-  if (MODE == R_NEAR_DSEED) {
+  if (MODE == R_NEAR_DSEED || MODE == R_NEAR_DSEED_P) {
     const double ls = block_sum2(lacc.value(), red);
     if (threadIdx.x == 0) a.lossp[((size_t)b * a.nd + a.d) * gridDim.x + blockIdx.x] = ls;
   }
@@ -519,7 +520,7 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
         pp[2] = 0.0;
       }
     }
-  } else if (MODE == C_FAR_SEED) {
+  } else if (MODE == C_FAR_SEED || MODE == C_FAR_SEED_P) {
     // Psi = (1/N) DFT_+[phi_{L-1}] -> I, loss term, dL/dI -> phibar_{L-1} = (1/N) DFT_-[2 dL/dI Psi]
     stage_in(a.FA + fo, +1);
     __syncthreads();
@@ -540,7 +541,7 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
         const float I = fmaf(P.x, P.x, P.y * P.y);
         if (a.I_out) a.I_out[px] = I;
         float dI;
-        lacc.add(loss_term(a.loss, I, im[i], a.eps, &dI));
+        lacc.add(loss_term(MODE == C_FAR_SEED_P ? 1 : 0, I, im[i], a.eps, &dI));
         v[i] = cscale(P, sc * dI);
       }
       s3_store(v, c, t, -1);
@@ -722,9 +723,9 @@ static cudaError_t prepare_t2() {
   const int rb = row_smem_bytes<N>(), cb = col_smem_bytes<N>();
 #define ROWA(M_) if (e == cudaSuccess) e = set_attr<N>(k_row<N, M_>, rb);
 #define COLA(M_) if (e == cudaSuccess) e = set_attr<N>(k_col<N, M_>, cb);
-  ROWA(R_FWD) ROWA(R_RC_FIRST) ROWA(R_RC) ROWA(R_ADJ) ROWA(R_NEAR_DET) ROWA(R_NEAR_SEED) ROWA(R_PHAT) ROWA(R_PG_OUT) ROWA(R_NEAR_DSEED)
+  ROWA(R_FWD) ROWA(R_RC_FIRST) ROWA(R_RC) ROWA(R_ADJ) ROWA(R_NEAR_DET) ROWA(R_NEAR_SEED) ROWA(R_PHAT) ROWA(R_PG_OUT) ROWA(R_NEAR_DSEED) ROWA(R_NEAR_DSEED_P)
   COLA(C_PROP) COLA(C_PROP_ADJ) COLA(C_PSI0) COLA(C_FAR) COLA(C_SEED) COLA(C_Q) COLA(C_PHAT) COLA(C_PG)
-  COLA(C_NEAR_PHI) COLA(C_NEAR_Q) COLA(C_FAR_SEED)
+  COLA(C_NEAR_PHI) COLA(C_NEAR_Q) COLA(C_FAR_SEED) COLA(C_FAR_SEED_P)
 #undef ROWA
 #undef COLA
   return e;
@@ -784,13 +785,15 @@ static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEven
         col<N, C_PROP>(a, B, s);
         a.spec_out = nullptr;
       } else if (far) {
-        if (fuse) col<N, C_FAR_SEED>(a, B, s);
+        if (fuse && a.loss == 1) col<N, C_FAR_SEED_P>(a, B, s);
+        else if (fuse) col<N, C_FAR_SEED>(a, B, s);
         else col<N, C_FAR>(a, B, s);
       } else {
         col<N, C_NEAR_PHI>(a, B, s);
         for (int d = 0; d < a.nd; ++d) {
           a.d = d;
-          if (fuse) row<N, R_NEAR_DSEED>(a, B, s);
+          if (fuse && a.loss == 1) row<N, R_NEAR_DSEED_P>(a, B, s);
+          else if (fuse) row<N, R_NEAR_DSEED>(a, B, s);
           else row<N, R_NEAR_DET>(a, B, s);
         }
       }

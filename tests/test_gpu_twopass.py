@@ -25,9 +25,10 @@ def test_twopass_farfield_parity(N, L, M, B, loss, cp):
     _compare(case)
 
 
-@pytest.mark.parametrize("N,L,M,B,nd", [(256, 1, 1, 2, 3), (256, 3, 2, 1, 2), (512, 2, 1, 1, 4)])
-def test_twopass_nearfield_parity(N, L, M, B, nd):
-    case = C.small_case(N=N, L=L, M=M, B=B, loss="lsq", far=False, n_dist=nd, seed=3 + N + L)
+@pytest.mark.parametrize("N,L,M,B,nd,loss", [(256, 1, 1, 2, 3, "lsq"), (256, 3, 2, 1, 2, "lsq"),
+                                             (512, 2, 1, 1, 4, "lsq"), (256, 2, 1, 2, 2, "poisson")])
+def test_twopass_nearfield_parity(N, L, M, B, nd, loss):
+    case = C.small_case(N=N, L=L, M=M, B=B, loss=loss, far=False, n_dist=nd, seed=3 + N + L)
     _compare(case)
 
 
