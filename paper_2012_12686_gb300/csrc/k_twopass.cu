@@ -76,6 +76,44 @@ __device__ __forceinline__ double block_sum2(double v, double* red) {
   return s;
 }
 
+// TwoSum (Knuth): s + e == a + b exactly, in FP32
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// CTA sums of three FP32 values, in FP64 on thread 0 (out[]): a compensated warp tree (each
+// level adds the high parts with TwoSum and carries the error in the low parts), then an FP64
+// sum over the warps in a fixed order.  One pass for three values, no FP64 shuffles.
+__device__ __forceinline__ void block_sum3(float a0, float a1, float a2, double* red, double out[3]) {
+  float hi[3] = {a0, a1, a2}, lo[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float h = __shfl_xor_sync(0xffffffffu, hi[q], o), l = __shfl_xor_sync(0xffffffffu, lo[q], o);
+      float sum, err;
+      two_sum(hi[q], h, sum, err);
+      hi[q] = sum;
+      lo[q] += l + err;
+    }
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0)
+    for (int q = 0; q < 3; ++q) red[3 * w + q] = f32_to_f64(hi[q]) + f32_to_f64(lo[q]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 3; ++q) {
+      double t = 0.0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[3 * i + q];
+      out[q] = t;
+    }
+  }
+  __syncthreads();
+}
+
 // ============================================================================ row kernel
 template <int N, int MODE>
 __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
@@ -512,7 +550,9 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
       }
     }
     if (MODE == C_Q && a.posp) {
-      const double sy = block_sum2(ay, red), sx = block_sum2(ax, red);
+      double sm3[3];
+      block_sum3(ay, ax, 0.f, red, sm3);
+      const double sy = sm3[0], sx = sm3[1];
       if (threadIdx.x == 0) {
         double* pp = a.posp + ((size_t)b * gridDim.x + blockIdx.x) * 3;
         pp[0] = (m == 0) ? sy : pp[0] + sy;
@@ -624,7 +664,9 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
         }
       }
       if (a.posp) {
-        const double s_y = block_sum2(ay, red), s_x = block_sum2(ax, red), s_n = block_sum2(an, red);
+        double sm3[3];
+        block_sum3(ay, ax, an, red, sm3);
+        const double s_y = sm3[0], s_x = sm3[1], s_n = sm3[2];
         if (threadIdx.x == 0) {
           double* pp = a.posp + (((size_t)b * a.nd + d) * gridDim.x + blockIdx.x) * 3;
           pp[0] = (m == 0) ? s_y : pp[0] + s_y;
