@@ -329,7 +329,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(dev)
-    w = synth.workload(args.workload, seed=0)
+    w = synth.workload(args.workload, seed=0, **({"B": args.batch} if args.batch else {}))
     p = w["problem"]
     N, L, B, M = p["N"], p["L"], p["B"], p["M"]
     far = bool(p["farfield"])
@@ -467,6 +467,8 @@ def run_ours(args, rank, world, local_rank):
         line["plain_gpu"] = plain
     if args.workload != WORKLOAD:
         line["config"]["workload"] = args.workload
+    if args.batch:
+        line["config"]["workload"] = f"{args.workload} with batch {args.batch}"
     if not args.no_cpu_baseline and world == 1 and args.workload == WORKLOAD:
         cores = os.cpu_count() or 1
         n_pos = min(8 * cores, len(all_pos))
@@ -632,6 +634,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain torch GPU path")
     ap.add_argument("--workload", default=WORKLOAD, choices=["multislice", "ptycho2d", "tomo", "holo"],
                     help="workload of the timed steps (default: the metric's multislice configuration)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="override the workload's batch (positions / problems per call), e.g. a small case for "
+                         "kernel captures; not a bench line of the metric")
     ap.add_argument("--serve", action="store_true", help="run the serving mix instead of the minibatch benchmark")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
