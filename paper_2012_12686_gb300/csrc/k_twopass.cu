@@ -709,10 +709,12 @@ __global__ void __launch_bounds__(256) k_loss2(const TPArgs a) {
   if (threadIdx.x == 0) a.lossp[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(256) k_final2(const TPArgs a, int nloss, int ncolblk) {
-  __shared__ double red[8];
+// loss: all threads over the partials, fixed split and order; shift / Fresnel-number gradients: one
+// warp per (problem, distance), lanes over the column-CTA partials, fixed shuffle tree
+__global__ void __launch_bounds__(1024) k_final2(const TPArgs a, int nloss, int ncolblk) {
+  __shared__ double red[32];
   if (a.loss_out) {
-    const int chunk = (nloss + 255) / 256;
+    const int chunk = (nloss + blockDim.x - 1) / blockDim.x;
     double acc = 0.0;
     for (int i = threadIdx.x * chunk; i < min(nloss, (int)(threadIdx.x + 1) * chunk); ++i) acc += a.lossp[i];
     const double s = block_sum2(acc, red);
@@ -720,20 +722,30 @@ __global__ void __launch_bounds__(256) k_final2(const TPArgs a, int nloss, int n
   }
   if (a.posp && (a.gpos || a.gnf)) {
     const double pi = 3.14159265358979323846, NN = (double)a.N * a.N, sc = 2.0 * pi / NN;
-    for (int q = threadIdx.x; q < a.B * a.nd; q += 256) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int q = w; q < a.B * a.nd; q += nw) {
       double sy = 0.0, sx = 0.0, sn = 0.0;
-      for (int k = 0; k < ncolblk; ++k) {
-        sy += a.posp[((size_t)q * ncolblk + k) * 3];
-        sx += a.posp[((size_t)q * ncolblk + k) * 3 + 1];
-        sn += a.posp[((size_t)q * ncolblk + k) * 3 + 2];
+      for (int k = l; k < ncolblk; k += 32) {
+        const double* pp = a.posp + ((size_t)q * ncolblk + k) * 3;
+        sy += pp[0];
+        sx += pp[1];
+        sn += pp[2];
       }
-      if (a.gpos) {
-        a.gpos[2 * q] = (float)(sc * sy);
-        a.gpos[2 * q + 1] = (float)(sc * sx);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sn += __shfl_xor_sync(0xffffffffu, sn, o);
       }
-      if (a.gnf) {
-        const double nf = a.nf[q % a.nd];
-        a.gnf[q] = (float)(pi * sn / (nf * nf * NN));
+      if (l == 0) {
+        if (a.gpos) {
+          a.gpos[2 * q] = (float)(sc * sy);
+          a.gpos[2 * q + 1] = (float)(sc * sx);
+        }
+        if (a.gnf) {
+          const double nf = a.nf[q % a.nd];
+          a.gnf[q] = (float)(pi * sn / (nf * nf * NN));
+        }
       }
     }
   }
@@ -896,7 +908,7 @@ static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEven
   }
   if (ev1) cudaEventRecord(ev1, s);
   if (a.adj) {
-    k_final2<<<1, 256, 0, s>>>(a, nloss, ncol);
+    k_final2<<<1, 1024, 0, s>>>(a, nloss, ncol);
     if (want_gap && a.ggap) launch_gap_final(a.gapp, B, L - 1, ncol, a.ggap, s);
     if (a.g_probe) {
       const size_t MNN = (size_t)M * NN;
