@@ -260,6 +260,11 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
     gb = acc + V;
   }
   float2* phat = reinterpret_cast<float2*>(W(pl.off_phat));
+  // the main kernels read the measured intensities: wait for their copy (the pre-kernels above and
+  // the probe transform do not)
+  auto wait_meas = [&]() -> int {
+    return c.meas_ready ? chk(cudaStreamWaitEvent(s, c.meas_ready, 0), "wait for intensities") : ADORYM_OK;
+  };
   if (two_pass(p.N)) {
     TPArgs t{};
     t.N = p.N;
@@ -318,6 +323,7 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
       t.g_probe = pl.want_probe ? c.g_probe : nullptr;
       t.loss_out = c.loss;
     }
+    if ((rc = wait_meas())) return rc;
     if ((rc = chk(launch_twopass(t, s, ev_start, ev_stop), "two-pass"))) return rc;
   } else {
     if (pl.far) {
@@ -373,6 +379,7 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
     a.far = reinterpret_cast<float2*>(W(pl.off_far));
     a.gI = reinterpret_cast<float*>(W(pl.off_gI));
     a.lossp = reinterpret_cast<double*>(W(pl.off_lossp));
+    if ((rc = wait_meas())) return rc;
     if (ev_start) cudaEventRecord(ev_start, s);
     if ((rc = chk(launch_path(a, pl.far ? 1 : 0, s), "path"))) return rc;
     if (ev_stop) cudaEventRecord(ev_stop, s);
@@ -475,6 +482,12 @@ void adorym_destroy(adorym_ctx* ctx) {
   for (auto& kv : ctx->tables) cudaFree(kv.second.dev);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  if (ctx->copy_stream) {
+    cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamDestroy(ctx->copy_stream);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_meas) cudaEventDestroy(ctx->ev_meas);
   delete ctx;
 }
 
@@ -559,7 +572,24 @@ static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const 
   };
   c.probe = reinterpret_cast<const float2*>(stage_in(probe, pl.off_s_probe, pl.bytes_probe));
   c.pos = reinterpret_cast<const float*>(stage_in(pos, pl.off_s_pos, pl.bytes_pos));
-  if (I_meas) c.I_meas = reinterpret_cast<const float*>(stage_in(I_meas, pl.off_s_meas, pl.bytes_meas));
+  if (I_meas && ptr_kind(I_meas) != 1) {
+    // host intensities: copied on a side stream that starts once the stream's earlier work (which
+    // may still read the staging area) is done, overlapping this call's pre-kernels
+    if (!ctx->copy_stream) {
+      if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ctx->ev_meas, cudaEventDisableTiming) != cudaSuccess)
+        return cuda_fail(ctx, cudaGetLastError(), "copy stream");
+    }
+    cudaEventRecord(ctx->ev_fork, s);
+    cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_fork, 0);
+    cudaMemcpyAsync(ws + pl.off_s_meas, I_meas, pl.bytes_meas, cudaMemcpyHostToDevice, ctx->copy_stream);
+    cudaEventRecord(ctx->ev_meas, ctx->copy_stream);
+    c.I_meas = reinterpret_cast<const float*>(ws + pl.off_s_meas);
+    c.meas_ready = ctx->ev_meas;
+  } else if (I_meas) {
+    c.I_meas = I_meas;
+  }
   c.gd = g_delta;
   c.gb = g_beta;
   const bool host_loss = loss_out && ptr_kind(loss_out) == 0;

@@ -58,6 +58,9 @@ struct CallPtrs {
   float* g_nf = nullptr;
   float* I_out = nullptr;
   float* g_gaps = nullptr;
+  // the measured intensities arrive on a side stream: the stream waits for this event before the
+  // main kernels (the pre-kernels overlap the copy); null when there is nothing to wait for
+  cudaEvent_t meas_ready = nullptr;
 };
 
 int validate(const adorym_problem& p, const char** err);
@@ -99,6 +102,8 @@ struct adorym_ctx {
   std::map<std::string, adorym::Tables> tables;
   bool timing = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // fused-kernel timing pair
+  cudaStream_t copy_stream = nullptr;          // host-to-device copy of measured intensities
+  cudaEvent_t ev_fork = nullptr, ev_meas = nullptr;
   bool timed = false;
   adorym::Serve* serve = nullptr;    // owned; created by the first submit or serve_config
 };

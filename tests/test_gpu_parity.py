@@ -120,3 +120,44 @@ def test_multimode_probe():
     """Five incoherent probe modes (the paper's fly-scan / ptychotomography setting)."""
     case = C.small_case(N=64, L=6, M=5, B=6, loss="lsq", seed=31)
     _compare(case)
+
+
+@pytest.mark.parametrize("far", [True, False])
+def test_host_buffers_match_device_buffers(far):
+    """Probe, positions and measured intensities in host memory are staged by the call (the
+    intensities on a side stream that overlaps the first kernels); outputs may be host memory too.
+    Two host-input calls in a row without a synchronisation between them, then one with host
+    outputs, each equal to the same call on device buffers."""
+    import torch
+    from paper_2012_12686_gb300.adorym import Engine
+    case = C.small_case(N=32, L=5, M=1, B=6, loss="poisson", far=far, n_dist=3, seed=11)
+    Im = C.measured(case).astype(np.float32)
+    p = case["problem"]
+    dev = torch.device("cuda:0")
+    eng = Engine(0)
+    d = torch.from_numpy(np.ascontiguousarray(case["delta"])).to(dev)
+    b = torch.from_numpy(np.ascontiguousarray(case["beta"])).to(dev)
+    oid = eng.register_object(d, b)
+    probe_h = torch.from_numpy(np.ascontiguousarray(case["probe"]).astype(np.complex64))
+    pos_h = torch.from_numpy(np.ascontiguousarray(case["pos"]).astype(np.float32))
+    meas_h = [torch.from_numpy(Im).pin_memory(), torch.from_numpy(0.5 * Im).pin_memory()]
+
+    def run(probe, pos, meas, host_out):
+        where = "cpu" if host_out else dev
+        loss = torch.zeros((), dtype=torch.float64, device=where)
+        gd, gb = torch.zeros_like(d), torch.zeros_like(b)
+        gp = torch.zeros(probe.shape, dtype=torch.complex64, device=where)
+        gpos = torch.zeros(pos.shape, dtype=torch.float32, device=where)
+        eng.loss_grad(p, oid, probe, pos, meas, loss, gd, gb, gp, gpos)
+        return loss, gd, gb, gp, gpos
+
+    ref = [run(probe_h.to(dev), pos_h.to(dev), m.to(dev), False) for m in meas_h]
+    torch.cuda.synchronize()
+    got = [run(probe_h, pos_h, m, False) for m in meas_h]      # asynchronous, back to back
+    got.append(run(probe_h, pos_h, meas_h[0], True))           # host outputs: synchronous
+    torch.cuda.synchronize()
+    for g, r in zip(got, [ref[0], ref[1], ref[0]]):
+        for x, y in zip(g, r):
+            x, y = x.cpu().numpy(), y.cpu().numpy()
+            assert C.rel(x, y) <= 1e-6, (far, C.rel(x, y))
+    eng.unregister_object(oid)
