@@ -54,6 +54,9 @@ extern "C" {
 #define ADORYM_ENOENT 5      /* unknown object id or ticket                                    */
 #define ADORYM_ETOOBIG 6     /* adorym_loss_grad_noalloc: the problem needs more scratch than
                                 ADORYM_NOALLOC_SCRATCH_BYTES                                   */
+#define ADORYM_EDATA 7       /* a kernel found invalid input data in device memory (a position
+                                that is not finite or lies beyond +-2^24 px); reported through
+                                the call's device status word, see adorym_check              */
 
 #define ADORYM_LOSS_LSQ 0     /* Eq. lsq_loss: mean (sqrt(I+eps) - sqrt(I_meas+eps))^2        */
 #define ADORYM_LOSS_POISSON 1 /* Eq. poisson_loss: mean (I - I_meas log(I+eps))               */
@@ -95,6 +98,16 @@ void adorym_destroy(adorym_ctx* ctx);
 
 /* Message of the most recent error on this context ("" if none).  Owned by the context. */
 const char* adorym_last_error(adorym_ctx* ctx);
+
+/* Device status word of the most recent adorym_forward / adorym_loss_grad(_ext) call of ctx.
+ * Kernels never trap: input data that only the device sees (positions / hologram shifts) are
+ * checked while the call runs, and an invalid value sets a bit in a per-call status word instead
+ * (the call's results are then meaningless but no memory outside the object and the workspace is
+ * touched: patch corners are clamped).  Calls that return host outputs wait for the GPU and
+ * report ADORYM_EDATA themselves; for asynchronous calls this function waits for the context's
+ * stream and returns ADORYM_OK or ADORYM_EDATA (message in adorym_last_error).  Serving
+ * requests report it through adorym_poll. */
+int adorym_check(adorym_ctx* ctx);
 
 /* Register a resident object volume: delta, beta device pointers to FP32 [Lz][Ly][Lx]
  * (Sec. 2.1 refractive-index representation n = 1 - delta - i beta).  The memory stays owned

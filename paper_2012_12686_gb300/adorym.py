@@ -14,7 +14,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libadorym.so")
 
-OK, EINVAL, ENOMEM, ETIMEDOUT, EDEVICE, ENOENT, ETOOBIG = 0, 1, 2, 3, 4, 5, 6
+OK, EINVAL, ENOMEM, ETIMEDOUT, EDEVICE, ENOENT, ETOOBIG, EDATA = 0, 1, 2, 3, 4, 5, 6, 7
 NOALLOC_SCRATCH_BYTES = 64 << 20
 LOSS = {"lsq": 0, "poisson": 1}
 
@@ -22,7 +22,7 @@ EXPORTS = ["adorym_create", "adorym_destroy", "adorym_last_error", "adorym_regis
            "adorym_unregister_object", "adorym_forward", "adorym_loss_grad", "adorym_submit", "adorym_poll",
            "adorym_serve_config", "adorym_serve_stats", "adorym_workspace_bytes", "adorym_enable_kernel_timing",
            "adorym_kernel_ms", "adorym_loss_grad_noalloc", "adorym_loss_grad_ext", "adorym_regularize",
-           "adorym_l1_weights"]
+           "adorym_l1_weights", "adorym_check"]
 
 
 class Problem(ctypes.Structure):
@@ -107,6 +107,7 @@ def lib() -> ctypes.CDLL:
         L.adorym_l1_weights.argtypes = [vp, i32, ctypes.c_double, vp, vp]
         L.adorym_loss_grad_ext.argtypes = [vp, ctypes.POINTER(Problem), i32, vp, vp, vp, ctypes.POINTER(Grads)]
         L.adorym_loss_grad_noalloc.argtypes = [vp, ctypes.POINTER(Problem), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.adorym_check.argtypes = [vp]
         for name in EXPORTS:
             if name not in ("adorym_destroy", "adorym_last_error"):
                 getattr(L, name).restype = ctypes.c_int
@@ -241,6 +242,11 @@ class Engine:
         if rc not in (OK, ETIMEDOUT):
             raise AdorymError(rc, self.last_error())
         return rc
+
+    def check(self) -> int:
+        """Wait for the context's stream and raise on the last call's device status word (EDATA:
+        invalid positions / shifts found by the kernels)."""
+        return self._check(lib().adorym_check(self._ctx))
 
     def serve_stats(self):
         c, w = ctypes.c_uint64(), ctypes.c_uint64()

@@ -117,6 +117,7 @@ int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan
   }
   q.off_loss = take(sizeof(double));
   q.off_box = take(4 * sizeof(int));
+  q.off_status = take(sizeof(int));
   if (q.want_gaps) {
     const int parts = two_pass(p.N) ? (int)(N / (N == 256 ? 32 : N == 512 ? 16 : 8)) : 1;
     q.off_spck = take(B * M * q.ncp * NN * f2);
@@ -244,7 +245,11 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
   int rc;
   float2* T = reinterpret_cast<float2*>(W(pl.off_T));
   int* box = reinterpret_cast<int*>(W(pl.off_box));
-  if ((rc = chk(launch_bbox(c.pos, p.B, p.N, p.Ly, p.Lx, pl.far ? 1 : 0, pl.tomo ? 1 : 0, box, s), "bbox")))
+  int* status = reinterpret_cast<int*>(W(pl.off_status));
+  if ((rc = chk(cudaMemsetAsync(status, 0, sizeof(int), s), "status"))) return rc;
+  if ((rc = chk(launch_bbox(c.pos, p.B, p.N, p.Ly, p.Lx, pl.far ? 1 : 0, pl.tomo ? 1 : 0, box, 2 * p.B * pl.nd, status,
+                            s),
+                "bbox")))
     return rc;
   if ((rc = chk(launch_transmission(obj.d, obj.b, T, p.Lz, p.Ly, p.Lx, (float)p.kdz, pl.tomo ? 1 : 0, (float)cth,
                                     (float)sth, box, s),
@@ -413,6 +418,11 @@ int prepare_kernels(const adorym_problem& p, const char** err) {
   return ADORYM_OK;
 }
 
+const char* status_message(int status) {
+  return (status & STATUS_BAD_POSITION) ? "a position or hologram shift is not finite or lies beyond +-2^24 px"
+                                        : "invalid input data";
+}
+
 }  // namespace adorym
 
 using namespace adorym;
@@ -487,11 +497,23 @@ void adorym_destroy(adorym_ctx* ctx) {
     cudaStreamDestroy(ctx->copy_stream);
   }
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->status_host) cudaFreeHost(ctx->status_host);
   if (ctx->ev_meas) cudaEventDestroy(ctx->ev_meas);
   delete ctx;
 }
 
 const char* adorym_last_error(adorym_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int adorym_check(adorym_ctx* ctx) {
+  if (!ctx) return ADORYM_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!ctx->status_host) return ADORYM_OK;   // no call yet
+  cudaSetDevice(ctx->device);
+  const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+  if (*ctx->status_host) return fail(ctx, ADORYM_EDATA, status_message(*ctx->status_host));
+  return ADORYM_OK;
+}
 
 int adorym_register_object(adorym_ctx* ctx, const float* delta, const float* beta, int Lz, int Ly, int Lx,
                            int* obj_id) {
@@ -642,11 +664,19 @@ static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const 
     cudaMemcpyAsync(g_gaps, c.g_gaps, (size_t)(p->L - 1) * sizeof(float), cudaMemcpyDeviceToHost, s);
     sync_after = true;
   }
+  // the call's status word goes to a pinned host int (read by adorym_check, or below)
+  if (!ctx->status_host) {
+    void* h = nullptr;
+    if (cudaHostAlloc(&h, sizeof(int), cudaHostAllocDefault) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "status");
+    ctx->status_host = static_cast<int*>(h);
+  }
+  cudaMemcpyAsync(ctx->status_host, ws + pl.off_status, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "enqueue");
   if (sync_after) {
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+    if (*ctx->status_host) return fail(ctx, ADORYM_EDATA, status_message(*ctx->status_host));
   }
   return ADORYM_OK;
 }

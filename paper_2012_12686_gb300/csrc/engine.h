@@ -37,6 +37,7 @@ struct Plan {
   // two-pass path (N >= 256)
   size_t off_FA = 0, off_FR = 0, off_tmp = 0, off_posp = 0;
   size_t off_box = 0;   // int4 bounding box of the batch's patches
+  size_t off_status = 0;   // int device status word of the call (ADORYM_STATUS_* bits)
   size_t off_spck = 0, off_spseg = 0, off_gapp = 0, off_s_ggap = 0;   // slice-gap gradient
   // staging for host-memory arguments
   size_t off_s_probe = 0, off_s_pos = 0, off_s_meas = 0, off_s_gprobe = 0, off_s_gpos = 0, off_s_iout = 0,
@@ -104,6 +105,7 @@ struct adorym_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // fused-kernel timing pair
   cudaStream_t copy_stream = nullptr;          // host-to-device copy of measured intensities
   cudaEvent_t ev_fork = nullptr, ev_meas = nullptr;
+  int* status_host = nullptr;                  // pinned copy of the last call's status word
   bool timed = false;
   adorym::Serve* serve = nullptr;    // owned; created by the first submit or serve_config
 };
@@ -111,5 +113,6 @@ struct adorym_ctx {
 namespace adorym {
 int get_tables(adorym_ctx* ctx, const adorym_problem& p, Tables* out);   // ctx->mu held
 int prepare_kernels(const adorym_problem& p, const char** err);         // attributes, outside capture
+const char* status_message(int status);                                 // text of a device status word
 void serve_shutdown(adorym_ctx* ctx);
 }  // namespace adorym

@@ -98,8 +98,8 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
     // S1: integer corner p0 = floor(pos + 1/2), residual dr = pos - p0 (FP64, exact for float input)
     const double py = a.pos[2 * b], px = a.pos[2 * b + 1];
     const double fy = floor(py + 0.5), fx = floor(px + 0.5);
-    p0y = (int)fy;
-    p0x = (int)fx;
+    p0y = patch_corner(a.pos[2 * b]);
+    p0x = patch_corner(a.pos[2 * b + 1]);
     ramp_table(ry, (float)(py - fy), N, NT);
     ramp_table(rx, (float)(px - fx), N, NT);
   }
@@ -110,7 +110,7 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
   int cur_mode = 0;   // probe mode being processed (partials of mode 0 overwrite, later modes add)
   // transmission T_j at patch pixel (y, x); voxels outside the volume are vacuum (T = 1).  A patch
   // that lies inside the volume (the usual case; CTA-uniform) skips the per-pixel bounds tests.
-  const bool interior = p0y >= 0 && p0x >= 0 && p0y + N <= Ly && p0x + N <= Lx;
+  const bool interior = p0y >= 0 && p0x >= 0 && p0y <= Ly - N && p0x <= Lx - N;
   const size_t slab = (size_t)Ly * Lx;
   auto tload = [&](int j, int y, int x) -> float2 {
     const int gy = p0y + y, gx = p0x + x, gz = FAR ? j : b * L + j;

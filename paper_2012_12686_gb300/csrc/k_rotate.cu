@@ -36,12 +36,20 @@ __device__ __forceinline__ Tap tap(int zt, int xt, int Lz, int Lx, float c, floa
 // or the whole slab (near field), clamped to the volume, as box = {y0, y1, x0, x1}.  With
 // full_x the column range is the whole width (tomography: the rotation transpose mixes x and z).
 __global__ void __launch_bounds__(256) k_bbox(const float* __restrict__ pos, int B, int N, int Ly, int Lx, int far,
-                                              int full_x, int* __restrict__ box) {
+                                              int full_x, int* __restrict__ box, int npos_values,
+                                              int* __restrict__ status) {
   __shared__ int red[4][8];
+  // input check: every position / shift value finite and within +-2^24 px
+  bool bad = false;
+  for (int i = threadIdx.x; i < npos_values; i += 256) {
+    const float v = pos[i];
+    bad |= !(fabsf(v) <= 16777216.f);   // also catches NaN
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, STATUS_BAD_POSITION);
   int y0 = 1 << 30, y1 = -(1 << 30), x0 = 1 << 30, x1 = -(1 << 30);
   if (far) {
     for (int b = threadIdx.x; b < B; b += 256) {
-      const int py = (int)floor((double)pos[2 * b] + 0.5), px = (int)floor((double)pos[2 * b + 1] + 0.5);
+      const int py = patch_corner(pos[2 * b]), px = patch_corner(pos[2 * b + 1]);
       y0 = min(y0, py);
       y1 = max(y1, py + N);
       x0 = min(x0, px);
@@ -202,8 +210,9 @@ __global__ void k_grad_add(const double* __restrict__ ad, const double* __restri
 
 static unsigned vol_grid(size_t n) { return (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16); }
 
-cudaError_t launch_bbox(const float* pos, int B, int N, int Ly, int Lx, int far, int full_x, int* box, cudaStream_t s) {
-  k_bbox<<<1, 256, 0, s>>>(pos, B, N, Ly, Lx, far, full_x, box);
+cudaError_t launch_bbox(const float* pos, int B, int N, int Ly, int Lx, int far, int full_x, int* box,
+                        int npos_values, int* status, cudaStream_t s) {
+  k_bbox<<<1, 256, 0, s>>>(pos, B, N, Ly, Lx, far, full_x, box, npos_values, status);
   return cudaGetLastError();
 }
 

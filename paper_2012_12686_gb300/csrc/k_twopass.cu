@@ -205,8 +205,8 @@ __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
     if (MODE == R_FWD || MODE == R_RC_FIRST || MODE == R_RC) {
       int p0y = 0, p0x = 0, gz = FAR ? j : b * a.L + j;
       if (FAR) {
-        p0y = (int)floor((double)a.pos[2 * b] + 0.5);
-        p0x = (int)floor((double)a.pos[2 * b + 1] + 0.5);
+        p0y = patch_corner(a.pos[2 * b]);
+        p0x = patch_corner(a.pos[2 * b + 1]);
       }
       const int gy = p0y + y;
       const bool row_in = gy >= 0 && gy < a.Ly;
@@ -246,8 +246,8 @@ __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
     if (MODE == R_ADJ) {
       int p0y = 0, p0x = 0, gz = FAR ? j : b * a.L + j;
       if (FAR) {
-        p0y = (int)floor((double)a.pos[2 * b] + 0.5);
-        p0x = (int)floor((double)a.pos[2 * b + 1] + 0.5);
+        p0y = patch_corner(a.pos[2 * b]);
+        p0x = patch_corner(a.pos[2 * b + 1]);
       }
       const int gy = p0y + y;
       const bool row_in = gy >= 0 && gy < a.Ly;

@@ -114,7 +114,11 @@ cudaError_t launch_probe_grad(int N, int M, int B, int farfield, const float2* q
                               cudaStream_t s);
 // box = {y0, y1, x0, x1}: rows / columns of the volume the batch's patches touch (whole width if
 // full_x), computed on the device from the positions
-cudaError_t launch_bbox(const float* pos, int B, int N, int Ly, int Lx, int far, int full_x, int* box, cudaStream_t s);
+// status word bits set by the kernels (the host maps any bit to ADORYM_EDATA)
+constexpr int STATUS_BAD_POSITION = 1;   // a position / shift is not finite or beyond +-2^24 px
+// npos_values: 2 B (far field) or 2 B n_dist (near-field shifts) floats checked into *status
+cudaError_t launch_bbox(const float* pos, int B, int N, int Ly, int Lx, int far, int full_x, int* box,
+                        int npos_values, int* status, cudaStream_t s);
 // T = exp(-kdz beta) exp(i kdz delta) over the box (Eq. ri_modulation), optionally after the
 // bilinear rotation of Eq. rotation_transform (rotate = 1)
 cudaError_t launch_transmission(const float* vd, const float* vb, float2* T, int Lz, int Ly, int Lx, float kdz,

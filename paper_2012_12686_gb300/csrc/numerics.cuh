@@ -44,6 +44,14 @@ __device__ __forceinline__ float f64_to_f32(const double* p) {   // load and nar
   return f64bits_to_f32(w.y, w.x);
 }
 
+// Integer patch corner floor(pos + 1/2) of the position split (Sec. 2.3.1), clamped to +-2^24 so
+// that corner + patch offsets and corner + N never overflow an int; a non-finite position gives
+// corner 0 (the input check reports it).
+__device__ __forceinline__ int patch_corner(float pos) {
+  const double f = floor((double)pos + 0.5);
+  return f != f ? 0 : (int)fmin(fmax(f, -16777216.0), 16777216.0);
+}
+
 // Compensated FP32 running sum (Kahan summation): the low-order part lost by each addition is
 // carried in c and fed back into the next one, so the sum of n terms is accurate to a few ulps
 // of sum |x_i| independent of n.  Read out once, in FP64.

@@ -81,6 +81,7 @@ struct Ticket {
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
+  int* status = nullptr;  // pinned: the running ticket's device status word, copied by its graph
   uint64_t ticket = 0;    // 0 = free
   std::map<std::string, cudaGraphExec_t> graphs;
 };
@@ -139,6 +140,9 @@ static int launch_ticket(adorym_ctx* ctx, Serve& S, uint64_t id) {
     return ADORYM_EDEVICE;
   }
   rc = enqueue(t.plan, it->second, tab, c, S.arena.base + t.ws_off, sl.stream, &err);
+  if (!rc)
+    cudaMemcpyAsync(sl.status, S.arena.base + t.ws_off + t.plan.off_status, sizeof(int), cudaMemcpyDeviceToHost,
+                    sl.stream);
   e = cudaStreamEndCapture(sl.stream, &g);
   if (rc || e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -201,8 +205,10 @@ static void worker_main(adorym_ctx* ctx) {
       cudaError_t q = cudaEventQuery(sl.done);
       if (q == cudaErrorNotReady) continue;
       const uint64_t id = sl.ticket;
-      finish(S, id, q == cudaSuccess ? ADORYM_OK : ADORYM_EDEVICE);
+      const bool bad_data = q == cudaSuccess && *sl.status != 0;
+      finish(S, id, q != cudaSuccess ? ADORYM_EDEVICE : bad_data ? ADORYM_EDATA : ADORYM_OK);
       if (q != cudaSuccess) ctx->err = std::string("request failed: ") + cudaGetErrorString(q);
+      if (bad_data) ctx->err = std::string("request failed: ") + status_message(*sl.status);
       progress = true;
     }
     // admit in arrival order while a slot and memory are free
@@ -258,6 +264,11 @@ static int serve_start(adorym_ctx* ctx) {
   for (auto& sl : S->slots) {
     cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    void* h = nullptr;
+    if (cudaHostAlloc(&h, sizeof(int), cudaHostAllocDefault) == cudaSuccess) {
+      sl.status = static_cast<int*>(h);
+      *sl.status = 0;
+    }
   }
   ctx->serve = S.release();
   ctx->serve->worker = std::thread(worker_main, ctx);
@@ -278,6 +289,7 @@ void serve_shutdown(adorym_ctx* ctx) {
     for (auto& kv : sl.graphs) cudaGraphExecDestroy(kv.second);
     cudaStreamDestroy(sl.stream);
     cudaEventDestroy(sl.done);
+    if (sl.status) cudaFreeHost(sl.status);
   }
   if (S.arena.base) cudaFree(S.arena.base);
   delete ctx->serve;
@@ -323,6 +335,11 @@ int adorym_serve_config(adorym_ctx* ctx, int slots, uint64_t budget_bytes) {
   for (auto& sl : S->slots) {
     cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    void* h = nullptr;
+    if (cudaHostAlloc(&h, sizeof(int), cudaHostAllocDefault) == cudaSuccess) {
+      sl.status = static_cast<int*>(h);
+      *sl.status = 0;
+    }
   }
   ctx->serve = S.release();
   ctx->serve->worker = std::thread(worker_main, ctx);
