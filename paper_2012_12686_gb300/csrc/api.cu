@@ -245,8 +245,8 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
   int rc;
   float2* T = reinterpret_cast<float2*>(W(pl.off_T));
   int* box = reinterpret_cast<int*>(W(pl.off_box));
-  int* status = reinterpret_cast<int*>(W(pl.off_status));
-  if ((rc = chk(cudaMemsetAsync(status, 0, sizeof(int), s), "status"))) return rc;
+  int* status = c.status ? c.status : reinterpret_cast<int*>(W(pl.off_status));
+  if (!c.status && (rc = chk(cudaMemsetAsync(status, 0, sizeof(int), s), "status"))) return rc;
   if ((rc = chk(launch_bbox(c.pos, p.B, p.N, p.Ly, p.Lx, pl.far ? 1 : 0, pl.tomo ? 1 : 0, box, 2 * p.B * pl.nd, status,
                             s),
                 "bbox")))
@@ -304,6 +304,7 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
     t.far = reinterpret_cast<float2*>(W(pl.off_far));
     t.gI = reinterpret_cast<float*>(W(pl.off_gI));
     t.lossp = reinterpret_cast<double*>(W(pl.off_lossp));
+    t.status = status;
     t.tmp = reinterpret_cast<float2*>(W(pl.off_tmp));
     if (pl.adj) {
       t.FR = reinterpret_cast<float2*>(W(pl.off_FR));
@@ -419,8 +420,9 @@ int prepare_kernels(const adorym_problem& p, const char** err) {
 }
 
 const char* status_message(int status) {
-  return (status & STATUS_BAD_POSITION) ? "a position or hologram shift is not finite or lies beyond +-2^24 px"
-                                        : "invalid input data";
+  return (status & STATUS_BAD_POSITION)   ? "a position or hologram shift is not finite or lies beyond +-2^24 px"
+         : (status & STATUS_WAIT_TIMEOUT) ? "a device-side wait for a tile copy timed out"
+                                          : "invalid input data";
 }
 
 }  // namespace adorym

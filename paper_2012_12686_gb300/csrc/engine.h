@@ -62,6 +62,9 @@ struct CallPtrs {
   // the measured intensities arrive on a side stream: the stream waits for this event before the
   // main kernels (the pre-kernels overlap the copy); null when there is nothing to wait for
   cudaEvent_t meas_ready = nullptr;
+  // device-visible status word to use instead of the plan's (not cleared by the call: the owner
+  // zeroes it before the work runs); null: the workspace word, cleared on the stream
+  int* status = nullptr;
 };
 
 int validate(const adorym_problem& p, const char** err);

@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(256) k_bbox(const float* __restrict__ pos, int
     const float v = pos[i];
     bad |= !(fabsf(v) <= 16777216.f);   // also catches NaN
   }
-  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, STATUS_BAD_POSITION);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(status, STATUS_BAD_POSITION);
   int y0 = 1 << 30, y1 = -(1 << 30), x0 = 1 << 30, x1 = -(1 << 30);
   if (far) {
     for (int b = threadIdx.x; b < B; b += 256) {

@@ -16,6 +16,11 @@
 // keeps both the strided and the contiguous stage accesses free of bank conflicts with the
 // lane index on the x digit, so every global access is coalesced.  Loss and position-gradient
 // reductions write per-CTA FP64 partials that a final kernel adds in a fixed order.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdint>
+
 #include "numerics.cuh"
 #include "fft_block.cuh"
 #include "kernels.cuh"
@@ -35,9 +40,10 @@ template <int N>
 constexpr int row_smem_bytes() {
   return Geo2<N>::RB * (N + Geo2<N>::N1) * (int)sizeof(float2) + N * (int)sizeof(float2) + 64 * 8;
 }
+// column tile + tw, ry, hy tables + 64 doubles of reduction scratch + one mbarrier (TMA staging)
 template <int N>
 constexpr int col_smem_bytes() {
-  return N * Geo2<N>::CW * (int)sizeof(float2) + 3 * N * (int)sizeof(float2) + 64 * 8;
+  return N * Geo2<N>::CW * (int)sizeof(float2) + 3 * N * (int)sizeof(float2) + 64 * 8 + 16;
 }
 
 // R_NEAR_DSEED / C_FAR_SEED (one probe mode with measured data; the _P forms for the Poisson loss,
@@ -112,6 +118,49 @@ __device__ __forceinline__ void block_sum3(float a0, float a1, float a2, double*
     }
   }
   __syncthreads();
+}
+
+// ============================================================================ TMA staging
+// The column kernels' N x CW tiles are brought into shared memory by the tensor-memory
+// accelerator: one thread issues min(N, 256)-row boxes of a 2-D tensor map over the field buffer
+// (cp.async.bulk.tensor), completion is counted in bytes on an mbarrier, and every thread waits on
+// the barrier's phase, for at most about a second (then the call's status word records the
+// timeout and the CTA leaves after a second bounded wait for its copies).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// wait for phase `phase` of the barrier for at most ~2^31 clock cycles
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, phase))
+    if (clock64() - t0 > (1LL << 31)) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
 }
 
 // ============================================================================ row kernel
@@ -357,15 +406,20 @@ __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
 
 // ============================================================================ column kernel
 template <int N, int MODE>
-__global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
+__global__ void __launch_bounds__(NT2, 2) k_col(const __grid_constant__ TPArgs a) {
   constexpr int N1 = Geo2<N>::N1, N2 = Geo2<N>::N2, CW = Geo2<N>::CW;
   constexpr size_t NN = (size_t)N * N;
-  extern __shared__ float2 sm[];
+  constexpr int BOXR = N < 256 ? N : 256;   // rows per TMA box
+  extern __shared__ __align__(128) float2 sm[];
   float2* C = sm;
   float2* tw = C + N * CW;
   float2* ry = tw + N;
   float2* hy = ry + N;                // hy (far: propagator / near: detector factor of distance d)
   double* red = reinterpret_cast<double*>(hy + N);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(red + 64);
+  const bool tma = a.tma != 0 && (smem_u32(C) & 127u) == 0;
+  uint32_t phase = 0;
+  if (tma && threadIdx.x == 0) mbar_init(bar);
   const int p0 = blockIdx.x * CW;
   const int f = blockIdx.y;
   const bool FAR = a.farfield != 0;
@@ -388,8 +442,54 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
   }
   __syncthreads();
 
-  // S1 from global column tile -> smem
-  auto stage_in = [&](const float2* src, int sgn) {
+  // tensor map and first row of the field at src (a whole number of rows into FA, FR, far or tmp)
+  auto tma_source = [&](const float2* src, int* which, int* row0) -> bool {
+    const float2* bases[4] = {a.FA, a.FR, a.far, a.tmp};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (!bases[k] || src < bases[k]) continue;
+      const size_t off = (size_t)(src - bases[k]);
+      if (off >= (size_t)a.tm_rows[k] * N) continue;
+      if (off % N) return false;
+      *which = k;
+      *row0 = (int)(off / N);
+      return true;
+    }
+    return false;
+  };
+  // S1 of the column tile at src -> smem.  Returns false (for every thread of the CTA) when the
+  // tile copy did not complete in time; the caller then leaves the kernel.
+  auto stage_in = [&](const float2* src, int sgn) -> bool {
+    int which = 0, row0 = 0;
+    if (tma && tma_source(src, &which, &row0)) {
+      // every earlier access of C is ordered before the asynchronous writes
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        mbar_expect_tx(bar, (uint32_t)(N * CW * sizeof(float2)));
+#pragma unroll
+        for (int yb = 0; yb < N / BOXR; ++yb) tma_load_2d(C + yb * BOXR * CW, &a.tm[which], p0, row0 + yb * BOXR, bar);
+      }
+      const bool ok = __syncthreads_and(mbar_wait_bounded(bar, phase));
+      phase ^= 1u;
+      if (!ok) {
+        if (threadIdx.x == 0) set_status(a.status, STATUS_WAIT_TIMEOUT);
+        mbar_wait_bounded(bar, phase ^ 1u);   // the copies still in flight land in this CTA's smem
+        return false;
+      }
+      // in place: task (c, t) reads and writes the slots of rows N2 i + t of column c
+      for (int tau = threadIdx.x; tau < CW * N2; tau += NT2) {
+        const int c = tau % CW, t = tau / CW;
+        float2 v[N1];
+#pragma unroll
+        for (int i = 0; i < N1; ++i) v[i] = C[(N2 * i + t) * CW + c];
+        if (sgn < 0) { dft<N1, -1>(v); twiddle<-1>(v, tw, t); }
+        else { dft<N1, +1>(v); twiddle<+1>(v, tw, t); }
+#pragma unroll
+        for (int k = 0; k < N1; ++k) C[(N2 * k + t) * CW + c] = v[k];
+      }
+      return true;
+    }
     for (int tau = threadIdx.x; tau < CW * N2; tau += NT2) {
       const int c = tau % CW, t = tau / CW;
       float2 v[N1];
@@ -400,6 +500,7 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
 #pragma unroll
       for (int k = 0; k < N1; ++k) C[(N2 * k + t) * CW + c] = v[k];
     }
+    return true;
   };
   // S4 from smem -> global column tile (natural y)
   auto stage_out = [&](float2* dst, int sgn) {
@@ -436,7 +537,7 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
                      ? a.spec_out + (((size_t)b * a.M + m) * a.spo_n + a.spo_slot) * NN : nullptr;
     const float2* si = (MODE == C_PROP_ADJ && a.spec_in)
                            ? a.spec_in + (((size_t)b * a.M + m) * a.spi_n + a.spi_slot) * NN : nullptr;
-    stage_in(F, -1);
+    if (!stage_in(F, -1)) return;
     __syncthreads();
     float gs = 0.f;
     for (int tau = threadIdx.x; tau < CW * N1; tau += NT2) {
@@ -508,7 +609,7 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
   } else if (MODE == C_FAR || MODE == C_Q || MODE == C_PHAT) {
     const int sg = (MODE == C_FAR) ? +1 : -1;
     const float2* F = (MODE == C_PHAT) ? a.tmp + (size_t)f * NN : a.FA + fo;
-    stage_in(F, sg);
+    if (!stage_in(F, sg)) return;
     __syncthreads();
     float ay = 0.f, ax = 0.f;
     for (int tau = threadIdx.x; tau < CW * N1; tau += NT2) {
@@ -562,7 +663,7 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
     }
   } else if (MODE == C_FAR_SEED || MODE == C_FAR_SEED_P) {
     // Psi = (1/N) DFT_+[phi_{L-1}] -> I, loss term, dL/dI -> phibar_{L-1} = (1/N) DFT_-[2 dL/dI Psi]
-    stage_in(a.FA + fo, +1);
+    if (!stage_in(a.FA + fo, +1)) return;
     __syncthreads();
     const float invN = 1.0f / (float)N, sc = 2.0f * invN * (float)a.inv_npix;
     const size_t pb = (size_t)b * NN;
@@ -594,7 +695,7 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
     // Phi = DFT_-[phi] (stored for the shift gradients); then for each distance
     // Psi_d = IDFT_-{Phi G_d}: y-inverse here, x-inverse in the row kernel.  Each thread reads
     // back the Phi values it stored itself (no barrier needed; they are L2-resident)
-    stage_in(a.FA + fo, -1);
+    if (!stage_in(a.FA + fo, -1)) return;
     __syncthreads();
     float2* Phi = a.far + (((size_t)b * (a.nd + 1) + a.nd) * a.M + m) * NN;
     for (int tau = threadIdx.x; tau < CW * N1; tau += NT2) {
@@ -629,7 +730,7 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const TPArgs a) {
     for (int d = 0; d < a.nd; ++d) {
       const float sy = a.pos[((size_t)b * a.nd + d) * 2], sx = a.pos[((size_t)b * a.nd + d) * 2 + 1];
       __syncthreads();
-      stage_in(a.far + (((size_t)b * (a.nd + 1) + d) * a.M + m) * NN, -1);
+      if (!stage_in(a.far + (((size_t)b * (a.nd + 1) + d) * a.M + m) * NN, -1)) return;
       for (int i = threadIdx.x; i < N; i += NT2) ry[i] = cmul(shift_ramp(sy, i, N), a.hd[(size_t)d * N + i]);
       __syncthreads();
       float ay = 0.f, ax = 0.f, an = 0.f;
@@ -797,11 +898,64 @@ cudaError_t prepare_twopass(int N) {
   return e;
 }
 
+// ADORYM_TMA_STAGING=0 builds the register-staged column loads only (for comparisons)
+#ifndef ADORYM_TMA_STAGING
+#define ADORYM_TMA_STAGING 1
+#endif
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against the driver)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D map over `rows` rows of N complex64 (8-byte elements) at base, box CW x min(N, 256).  The
+// TMA rules are checked here: base 16-byte aligned, row stride and box width multiples of 16
+// bytes (every x coordinate the kernels use is a multiple of CW, i.e. of 16 bytes).
+template <int N>
+static bool encode_tile_map(CUtensorMap* m, const void* base, unsigned long long rows) {
+  constexpr int CW = Geo2<N>::CW;
+  static_assert((CW * sizeof(float2)) % 16 == 0 && (N * sizeof(float2)) % 16 == 0, "TMA alignment");
+  auto fn = tensor_map_encoder();
+  if (!fn || !base || rows == 0 || (reinterpret_cast<uintptr_t>(base) & 15u)) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)N * sizeof(float2)};
+  const cuuint32_t box[2] = {(cuuint32_t)CW, (cuuint32_t)std::min(N, 256)};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int N>
 static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
   const bool far = a.farfield != 0;
   const int B = a.B, M = a.M, L = a.L;
   const size_t NN = (size_t)N * N;
+  {
+    // tile maps of the column kernels' sources: FA, FR (adjoint only), far, tmp
+    const void* bases[4] = {a.FA, a.FR, a.far, a.tmp};
+    const unsigned long long rows[4] = {(unsigned long long)B * M * N, a.FR ? (unsigned long long)B * M * N : 0ull,
+                                        (unsigned long long)B * (far ? 1 : a.nd + 1) * M * N,
+                                        (unsigned long long)M * N};
+    bool ok = a.status != nullptr;
+    for (int k = 0; k < 4 && ok; ++k) {
+      a.tm_rows[k] = bases[k] ? rows[k] : 0ull;
+      if (bases[k]) ok = encode_tile_map<N>(&a.tm[k], bases[k], rows[k]);
+    }
+    a.tma = (ok && ADORYM_TMA_STAGING) ? 1 : 0;
+  }
   // slice-gap gradient: spectra of checkpoint slices [B][M][ncp] and of segment slices [B][M][cp]
   float2* spck = a.spec_out;
   float2* spsg = const_cast<float2*>(a.spec_in);

@@ -1,5 +1,6 @@
 // Device-side argument blocks and host launchers shared by the kernel files and the C ABI.
 #pragma once
+#include <cuda.h>   // CUtensorMap (type only; encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -95,6 +96,12 @@ struct TPArgs {
   float* ggap;             // [L-1] output
   float2* g_probe;
   double* loss_out;
+  int* status;             // the call's device status word (STATUS_* bits)
+  // TMA staging of the column kernels' tiles: 2-D maps over the field buffers FA, FR, far, tmp
+  // (rows of N complex64, box CW x min(N, 256)); tma = 0 falls back to register-staged loads
+  int tma;
+  unsigned long long tm_rows[4];
+  CUtensorMap tm[4];
   int m, j, s, j0, j1, d, buf;
 };
 
@@ -116,6 +123,7 @@ cudaError_t launch_probe_grad(int N, int M, int B, int farfield, const float2* q
 // full_x), computed on the device from the positions
 // status word bits set by the kernels (the host maps any bit to ADORYM_EDATA)
 constexpr int STATUS_BAD_POSITION = 1;   // a position / shift is not finite or beyond +-2^24 px
+constexpr int STATUS_WAIT_TIMEOUT = 2;   // a bounded device-side wait (TMA completion) gave up
 // npos_values: 2 B (far field) or 2 B n_dist (near-field shifts) floats checked into *status
 cudaError_t launch_bbox(const float* pos, int B, int N, int Ly, int Lx, int far, int full_x, int* box,
                         int npos_values, int* status, cudaStream_t s);

@@ -44,6 +44,13 @@ __device__ __forceinline__ float f64_to_f32(const double* p) {   // load and nar
   return f64bits_to_f32(w.y, w.x);
 }
 
+// Set a bit of a call's status word.  Plain read-modify-write rather than an atomic: the word may
+// live in mapped host memory, and every writer within one kernel sets the same bit.
+__device__ __forceinline__ void set_status(int* status, int bit) {
+  volatile int* s = status;
+  *s = *s | bit;
+}
+
 // Integer patch corner floor(pos + 1/2) of the position split (Sec. 2.3.1), clamped to +-2^24 so
 // that corner + patch offsets and corner + N never overflow an int; a non-finite position gives
 // corner 0 (the input check reports it).

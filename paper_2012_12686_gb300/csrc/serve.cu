@@ -81,7 +81,9 @@ struct Ticket {
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  int* status = nullptr;  // pinned: the running ticket's device status word, copied by its graph
+  int* status = nullptr;  // mapped pinned host word: the running ticket's status (kernels write it
+                          // only on bad input; zeroed by the host before each launch)
+  int* status_dev = nullptr;
   uint64_t ticket = 0;    // 0 = free
   std::map<std::string, cudaGraphExec_t> graphs;
 };
@@ -139,10 +141,8 @@ static int launch_ticket(adorym_ctx* ctx, Serve& S, uint64_t id) {
     ctx->err = std::string("begin capture: ") + cudaGetErrorString(e);
     return ADORYM_EDEVICE;
   }
+  c.status = sl.status_dev;
   rc = enqueue(t.plan, it->second, tab, c, S.arena.base + t.ws_off, sl.stream, &err);
-  if (!rc)
-    cudaMemcpyAsync(sl.status, S.arena.base + t.ws_off + t.plan.off_status, sizeof(int), cudaMemcpyDeviceToHost,
-                    sl.stream);
   e = cudaStreamEndCapture(sl.stream, &g);
   if (rc || e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -173,6 +173,7 @@ static int launch_ticket(adorym_ctx* ctx, Serve& S, uint64_t id) {
     sl.graphs[key] = ex;
   }
   cudaGraphDestroy(g);
+  if (sl.status) *sl.status = 0;   // the slot's previous ticket has finished
   e = cudaGraphLaunch(sl.graphs[key], sl.stream);
   if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
   if (e != cudaSuccess) {
@@ -205,7 +206,7 @@ static void worker_main(adorym_ctx* ctx) {
       cudaError_t q = cudaEventQuery(sl.done);
       if (q == cudaErrorNotReady) continue;
       const uint64_t id = sl.ticket;
-      const bool bad_data = q == cudaSuccess && *sl.status != 0;
+      const bool bad_data = q == cudaSuccess && sl.status && *sl.status != 0;
       finish(S, id, q != cudaSuccess ? ADORYM_EDEVICE : bad_data ? ADORYM_EDATA : ADORYM_OK);
       if (q != cudaSuccess) ctx->err = std::string("request failed: ") + cudaGetErrorString(q);
       if (bad_data) ctx->err = std::string("request failed: ") + status_message(*sl.status);
@@ -265,9 +266,14 @@ static int serve_start(adorym_ctx* ctx) {
     cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
     void* h = nullptr;
-    if (cudaHostAlloc(&h, sizeof(int), cudaHostAllocDefault) == cudaSuccess) {
+    void* hd = nullptr;
+    if (cudaHostAlloc(&h, sizeof(int), cudaHostAllocMapped) == cudaSuccess &&
+        cudaHostGetDevicePointer(&hd, h, 0) == cudaSuccess) {
       sl.status = static_cast<int*>(h);
+      sl.status_dev = static_cast<int*>(hd);
       *sl.status = 0;
+    } else {
+      cudaGetLastError();
     }
   }
   ctx->serve = S.release();
@@ -336,9 +342,14 @@ int adorym_serve_config(adorym_ctx* ctx, int slots, uint64_t budget_bytes) {
     cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
     void* h = nullptr;
-    if (cudaHostAlloc(&h, sizeof(int), cudaHostAllocDefault) == cudaSuccess) {
+    void* hd = nullptr;
+    if (cudaHostAlloc(&h, sizeof(int), cudaHostAllocMapped) == cudaSuccess &&
+        cudaHostGetDevicePointer(&hd, h, 0) == cudaSuccess) {
       sl.status = static_cast<int*>(h);
+      sl.status_dev = static_cast<int*>(hd);
       *sl.status = 0;
+    } else {
+      cudaGetLastError();
     }
   }
   ctx->serve = S.release();
