@@ -251,19 +251,19 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
                             s),
                 "bbox")))
     return rc;
-  if ((rc = chk(launch_transmission(obj.d, obj.b, T, p.Lz, p.Ly, p.Lx, (float)p.kdz, pl.tomo ? 1 : 0, (float)cth,
-                                    (float)sth, box, s),
-                "transmission")))
-    return rc;
   // near field with one probe mode: one term per voxel and call, added in place by the kernels
   const bool direct = pl.want_obj && !pl.far && p.M == 1;
   if (pl.want_obj && !direct) {
-    // the scatter-add over overlapping positions is a reduction: accumulate it in FP64
+    // the scatter-add over overlapping positions is a reduction: accumulate it in FP64 (the
+    // accumulators are zeroed over the box by the transmission pass)
     double* acc = reinterpret_cast<double*>(W(pl.off_grot));
-    if ((rc = chk(launch_zero_box(acc, acc + V, p.Lz, p.Ly, p.Lx, box, s), "zero"))) return rc;
     gd = acc;
     gb = acc + V;
   }
+  if ((rc = chk(launch_transmission(obj.d, obj.b, T, p.Lz, p.Ly, p.Lx, (float)p.kdz, pl.tomo ? 1 : 0, (float)cth,
+                                    (float)sth, box, gd, gb, s),
+                "transmission")))
+    return rc;
   float2* phat = reinterpret_cast<float2*>(W(pl.off_phat));
   // the main kernels read the measured intensities: wait for their copy (the pre-kernels above and
   // the probe transform do not)

@@ -37,22 +37,24 @@ __global__ void __launch_bounds__(Geo<N>::NT) k_probe_hat(const float2* __restri
 // ---------------------------------------------------------------------------- probe gradient
 // qsum[m][p] = sum_b qacc[b][m][p] in FP64, fixed order
 // Block of 256 threads = 32 consecutive elements x 8 batch chunks; each thread sums its chunk
-// in FP64, then the 8 partials of an element are added in chunk order (deterministic).
+// Kahan-compensated in FP32 (loads issued four at a time), then the 8 partials of an element are
+// added in FP64 in chunk order (deterministic).
 __global__ void __launch_bounds__(256) k_qsum(const float2* __restrict__ qacc, float2* __restrict__ qsum, int B,
                                               size_t MNN) {
   __shared__ double2 part[8][32];
   const int e = threadIdx.x & 31, c = threadIdx.x >> 5;
   const size_t i = (size_t)blockIdx.x * 32 + e;
   const int b0 = (B * c) / 8, b1 = (B * (c + 1)) / 8;
-  double sr = 0.0, si = 0.0;
+  Kahan sr, si;
   if (i < MNN) {
+#pragma unroll 4
     for (int b = b0; b < b1; ++b) {
-      const float2 v = qacc[(size_t)b * MNN + i];
-      sr += v.x;
-      si += v.y;
+      const float2 v = __ldg(qacc + (size_t)b * MNN + i);
+      sr.add(v.x);
+      si.add(v.y);
     }
   }
-  part[c][e] = make_double2(sr, si);
+  part[c][e] = make_double2(sr.value(), si.value());
   __syncthreads();
   if (c == 0 && i < MNN) {
     double r = 0.0, im = 0.0;

@@ -111,7 +111,8 @@ __device__ __forceinline__ Region region(const int* __restrict__ box, int Lz) {
 // instead of evaluating sincos/exp for every (position, slice, pixel) they touch.
 template <bool ROT>
 __global__ void k_transmission(const float* __restrict__ vd, const float* __restrict__ vb, float2* __restrict__ T,
-                               int Lz, int Ly, int Lx, float kdz, float c, float s, const int* __restrict__ box) {
+                               int Lz, int Ly, int Lx, float kdz, float c, float s, const int* __restrict__ box,
+                               double* __restrict__ zero_a, double* __restrict__ zero_b) {
   const Region R = region(box, Lz);
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n; i += (size_t)gridDim.x * blockDim.x) {
     const int xt = R.x0 + (int)(i % R.w);
@@ -143,6 +144,10 @@ __global__ void k_transmission(const float* __restrict__ vd, const float* __rest
     sincosf(kdz * sd, &sn, &cs);
     const float e = expf(-kdz * sb);
     T[io] = make_float2(e * cs, e * sn);
+    if (zero_a) {
+      zero_a[io] = 0.0;
+      zero_b[io] = 0.0;
+    }
   }
 }
 
@@ -187,17 +192,8 @@ __global__ void k_rotate_adj(const double* __restrict__ gdr, const double* __res
   }
 }
 
-// FP64 object-gradient accumulators: zero the box, then add the box into the caller's gradient
-__global__ void k_zero_box(double* __restrict__ a, double* __restrict__ b, int Lz, int Ly, int Lx,
-                           const int* __restrict__ box) {
-  const Region R = region(box, Lz);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t io = ((size_t)(i / ((size_t)R.w * R.h)) * Ly + R.y0 + (i / R.w) % R.h) * Lx + R.x0 + i % R.w;
-    a[io] = 0.0;
-    b[io] = 0.0;
-  }
-}
-
+// FP64 object-gradient accumulators (zeroed over the box by the transmission pass): add the box
+// into the caller's gradient
 __global__ void k_grad_add(const double* __restrict__ ad, const double* __restrict__ ab, float* __restrict__ gd,
                            float* __restrict__ gb, int Lz, int Ly, int Lx, const int* __restrict__ box) {
   const Region R = region(box, Lz);
@@ -217,21 +213,17 @@ cudaError_t launch_bbox(const float* pos, int B, int N, int Ly, int Lx, int far,
 }
 
 cudaError_t launch_transmission(const float* vd, const float* vb, float2* T, int Lz, int Ly, int Lx, float kdz,
-                                int rotate, float c, float sn, const int* box, cudaStream_t s) {
+                                int rotate, float c, float sn, const int* box, double* zero_a, double* zero_b,
+                                cudaStream_t s) {
   const unsigned grid = vol_grid((size_t)Lz * Ly * Lx);
-  if (rotate) k_transmission<true><<<grid, 256, 0, s>>>(vd, vb, T, Lz, Ly, Lx, kdz, c, sn, box);
-  else k_transmission<false><<<grid, 256, 0, s>>>(vd, vb, T, Lz, Ly, Lx, kdz, c, sn, box);
+  if (rotate) k_transmission<true><<<grid, 256, 0, s>>>(vd, vb, T, Lz, Ly, Lx, kdz, c, sn, box, zero_a, zero_b);
+  else k_transmission<false><<<grid, 256, 0, s>>>(vd, vb, T, Lz, Ly, Lx, kdz, c, sn, box, zero_a, zero_b);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rotate_adj(const double* gdr, const double* gbr, float* gd, float* gb, int Lz, int Ly, int Lx,
                               float c, float sn, const int* box, cudaStream_t s) {
   k_rotate_adj<<<vol_grid((size_t)Lz * Ly * Lx), 256, 0, s>>>(gdr, gbr, gd, gb, Lz, Ly, Lx, c, sn, box);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_zero_box(double* a, double* b, int Lz, int Ly, int Lx, const int* box, cudaStream_t s) {
-  k_zero_box<<<vol_grid((size_t)Lz * Ly * Lx), 256, 0, s>>>(a, b, Lz, Ly, Lx, box);
   return cudaGetLastError();
 }
 

@@ -128,14 +128,15 @@ constexpr int STATUS_WAIT_TIMEOUT = 2;   // a bounded device-side wait (TMA comp
 cudaError_t launch_bbox(const float* pos, int B, int N, int Ly, int Lx, int far, int full_x, int* box,
                         int npos_values, int* status, cudaStream_t s);
 // T = exp(-kdz beta) exp(i kdz delta) over the box (Eq. ri_modulation), optionally after the
-// bilinear rotation of Eq. rotation_transform (rotate = 1)
+// bilinear rotation of Eq. rotation_transform (rotate = 1); zero_a / zero_b (FP64 object-gradient
+// accumulators over the same box) are zeroed in the same pass when non-null
 cudaError_t launch_transmission(const float* vd, const float* vb, float2* T, int Lz, int Ly, int Lx, float kdz,
-                                int rotate, float c, float sn, const int* box, cudaStream_t s);
+                                int rotate, float c, float sn, const int* box, double* zero_a, double* zero_b,
+                                cudaStream_t s);
 // transpose of the rotation applied to the FP64 rotated-frame accumulators, added into gd/gb (rows of the box)
 cudaError_t launch_rotate_adj(const double* gd_rot, const double* gb_rot, float* gd, float* gb, int Lz, int Ly,
                               int Lx, float c, float sn, const int* box, cudaStream_t s);
-// FP64 accumulators: zero the box; add the box into the caller's FP32 gradient
-cudaError_t launch_zero_box(double* a, double* b, int Lz, int Ly, int Lx, const int* box, cudaStream_t s);
+// FP64 accumulators: add the box into the caller's FP32 gradient
 cudaError_t launch_grad_add(const double* acc_d, const double* acc_b, float* gd, float* gb, int Lz, int Ly, int Lx,
                             const int* box, cudaStream_t s);
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s);
