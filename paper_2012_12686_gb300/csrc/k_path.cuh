@@ -49,8 +49,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;   // valid on thread 0
 }
 
-__device__ __forceinline__ double freqd(int k, int N) { return (double)(k <= (N - 1) / 2 ? k : k - N) * (1.0 / (double)N); }
-// the same frequency in FP32 (exact: N is a power of two)
+// frequency f_k of bin k in cycles per pixel (Nyquist bin negative), exact in FP32 (N a power of two)
 __device__ __forceinline__ float freqf1(int k, int N) { return (float)(k <= (N - 1) / 2 ? k : k - N) * (1.0f / (float)N); }
 
 // exp(-2 pi i d f_k) for k < N into out (d exact in FP32: a float shift, or a float position
