@@ -109,6 +109,11 @@ const char* adorym_last_error(adorym_ctx* ctx);
  * requests report it through adorym_poll. */
 int adorym_check(adorym_ctx* ctx);
 
+/* Number of kernels this library has launched in the process so far (kernels recorded into a
+ * serving graph count once, at capture).  Accounting only (no counterpart in the paper):
+ * differences around a region give the kernels that region launched. */
+uint64_t adorym_kernel_launches(void);
+
 /* Register a resident object volume: delta, beta device pointers to FP32 [Lz][Ly][Lx]
  * (Sec. 2.1 refractive-index representation n = 1 - delta - i beta).  The memory stays owned
  * by the caller and must outlive the registration; its contents may change between calls

@@ -22,7 +22,7 @@ EXPORTS = ["adorym_create", "adorym_destroy", "adorym_last_error", "adorym_regis
            "adorym_unregister_object", "adorym_forward", "adorym_loss_grad", "adorym_submit", "adorym_poll",
            "adorym_serve_config", "adorym_serve_stats", "adorym_workspace_bytes", "adorym_enable_kernel_timing",
            "adorym_kernel_ms", "adorym_loss_grad_noalloc", "adorym_loss_grad_ext", "adorym_regularize",
-           "adorym_l1_weights", "adorym_check"]
+           "adorym_l1_weights", "adorym_check", "adorym_kernel_launches"]
 
 
 class Problem(ctypes.Structure):
@@ -108,11 +108,18 @@ def lib() -> ctypes.CDLL:
         L.adorym_loss_grad_ext.argtypes = [vp, ctypes.POINTER(Problem), i32, vp, vp, vp, ctypes.POINTER(Grads)]
         L.adorym_loss_grad_noalloc.argtypes = [vp, ctypes.POINTER(Problem), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.adorym_check.argtypes = [vp]
+        L.adorym_kernel_launches.argtypes = []
         for name in EXPORTS:
-            if name not in ("adorym_destroy", "adorym_last_error"):
+            if name not in ("adorym_destroy", "adorym_last_error", "adorym_kernel_launches"):
                 getattr(L, name).restype = ctypes.c_int
+        L.adorym_kernel_launches.restype = ctypes.c_uint64
         _lib = L
     return _lib
+
+
+def kernel_launches() -> int:
+    """Kernels this library has launched in the process so far (differences give a region's count)."""
+    return int(lib().adorym_kernel_launches())
 
 
 def _ptr(x):

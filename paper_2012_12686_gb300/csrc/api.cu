@@ -45,6 +45,8 @@ int validate(const adorym_problem& p, const char** err) {
   return ADORYM_OK;
 }
 
+std::atomic<unsigned long long> g_kernel_launches{0};
+
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // SMs of the current device (0 when there is none)
@@ -505,6 +507,8 @@ void adorym_destroy(adorym_ctx* ctx) {
 }
 
 const char* adorym_last_error(adorym_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+uint64_t adorym_kernel_launches(void) { return g_kernel_launches.load(std::memory_order_relaxed); }
 
 int adorym_check(adorym_ctx* ctx) {
   if (!ctx) return ADORYM_EINVAL;

@@ -77,12 +77,12 @@ __global__ void k_gap_final(const double* __restrict__ gapp, int B, int ngap, in
 }
 
 cudaError_t launch_gap_final(const double* gapp, int B, int ngap, int parts, float* g_gap, cudaStream_t s) {
-  k_gap_final<<<1, 256, 0, s>>>(gapp, B, ngap, parts, g_gap);
+  (k_gap_final<<<1, 256, 0, s>>>(gapp, B, ngap, parts, g_gap), note_launch());
   return cudaGetLastError();
 }
 
 cudaError_t launch_qsum(const float2* qacc, float2* qsum, int B, size_t MNN, cudaStream_t s) {
-  k_qsum<<<(unsigned)((MNN + 31) / 32), 256, 0, s>>>(qacc, qsum, B, MNN);
+  (k_qsum<<<(unsigned)((MNN + 31) / 32), 256, 0, s>>>(qacc, qsum, B, MNN), note_launch());
   return cudaGetLastError();
 }
 
@@ -165,7 +165,7 @@ cudaError_t launch_path(const PathArgs& a, int farfield, cudaStream_t s) {
 template <int N>
 static cudaError_t launch_probe_hat_t(int M, const float2* probe, float2* phat, const float2* tw, cudaStream_t s) {
   const int smem = (N * (N + 1) + N) * (int)sizeof(float2);
-  k_probe_hat<N><<<M, Geo<N>::NT, smem, s>>>(probe, phat, tw);
+  (k_probe_hat<N><<<M, Geo<N>::NT, smem, s>>>(probe, phat, tw), note_launch());
   return cudaGetLastError();
 }
 
@@ -185,10 +185,10 @@ static cudaError_t launch_probe_grad_t(int M, int B, const float2* qacc, float2*
                                        const double* lossp, double inv_npix, double* loss_out, cudaStream_t s) {
   const size_t MNN = (size_t)M * N * N;
   if (g) {
-    k_qsum<<<(unsigned)((MNN + 31) / 32), 256, 0, s>>>(qacc, qsum, B, MNN);
+    (k_qsum<<<(unsigned)((MNN + 31) / 32), 256, 0, s>>>(qacc, qsum, B, MNN), note_launch());
   }
   const int smem = (N * (N + 1) + N) * (int)sizeof(float2);
-  k_probe_grad<N, FAR><<<M, Geo<N>::NT, smem, s>>>(qsum, g, tw, lossp, B, inv_npix, loss_out);
+  (k_probe_grad<N, FAR><<<M, Geo<N>::NT, smem, s>>>(qsum, g, tw, lossp, B, inv_npix, loss_out), note_launch());
   return cudaGetLastError();
 }
 

@@ -649,13 +649,13 @@ constexpr int path_smem_bytes_t() {
 
 template <int N, int FAR, bool GAP>
 cudaError_t launch_path_t(const PathArgs& a, cudaStream_t s) {
-  k_path<N, FAR, GAP><<<a.B, Geo<N>::NT, path_smem_bytes_t<N>(), s>>>(a);
+  (k_path<N, FAR, GAP><<<a.B, Geo<N>::NT, path_smem_bytes_t<N>(), s>>>(a), note_launch());
   return cudaGetLastError();
 }
 
 template <int N, int FAR>
 cudaError_t launch_path_pipe_t(const PathArgs& a, cudaStream_t s) {
-  k_path_pipe<N, FAR><<<2 * a.B, Geo<N>::NT, path_smem_bytes_t<N>(), s>>>(a);
+  (k_path_pipe<N, FAR><<<2 * a.B, Geo<N>::NT, path_smem_bytes_t<N>(), s>>>(a), note_launch());
   return cudaGetLastError();
 }
 

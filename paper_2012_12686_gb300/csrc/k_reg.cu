@@ -114,19 +114,19 @@ cudaError_t launch_regularize(const float* d, const float* b, const float* wd, c
   const unsigned grid = reg_grid(n);
   const float invNo = (float)(1.0 / (double)n);
   if (gam != 0.0)
-    k_regularize<true><<<grid, 256, 0, s>>>(d, b, wd, wb, Lz, Ly, Lx, (float)ad, (float)ab, (float)gam, invNo, gd,
-                                             gb, part);
+    (k_regularize<true><<<grid, 256, 0, s>>>(d, b, wd, wb, Lz, Ly, Lx, (float)ad, (float)ab, (float)gam, invNo, gd,
+                                             gb, part), note_launch());
   else
-    k_regularize<false><<<grid, 256, 0, s>>>(d, b, wd, wb, Lz, Ly, Lx, (float)ad, (float)ab, 0.f, invNo, gd, gb,
-                                              part);
-  if (loss) k_reg_final<<<1, 32, 0, s>>>(part, (int)grid, 1.0 / (double)n, loss);
+    (k_regularize<false><<<grid, 256, 0, s>>>(d, b, wd, wb, Lz, Ly, Lx, (float)ad, (float)ab, 0.f, invNo, gd, gb,
+                                              part), note_launch());
+  if (loss) (k_reg_final<<<1, 32, 0, s>>>(part, (int)grid, 1.0 / (double)n, loss), note_launch());
   return cudaGetLastError();
 }
 
 cudaError_t launch_l1_weights(const float* c, size_t n, float eps, float* part, float* w, cudaStream_t s) {
   const unsigned grid = reg_grid(n);
-  k_absmax<<<grid, 256, 0, s>>>(c, n, part);
-  k_l1_weights<<<grid, 256, 0, s>>>(c, n, part, (int)grid, eps, w);
+  (k_absmax<<<grid, 256, 0, s>>>(c, n, part), note_launch());
+  (k_l1_weights<<<grid, 256, 0, s>>>(c, n, part, (int)grid, eps, w), note_launch());
   return cudaGetLastError();
 }
 

@@ -208,7 +208,7 @@ static unsigned vol_grid(size_t n) { return (unsigned)std::min<size_t>((n + 255)
 
 cudaError_t launch_bbox(const float* pos, int B, int N, int Ly, int Lx, int far, int full_x, int* box,
                         int npos_values, int* status, cudaStream_t s) {
-  k_bbox<<<1, 256, 0, s>>>(pos, B, N, Ly, Lx, far, full_x, box, npos_values, status);
+  (k_bbox<<<1, 256, 0, s>>>(pos, B, N, Ly, Lx, far, full_x, box, npos_values, status), note_launch());
   return cudaGetLastError();
 }
 
@@ -216,20 +216,20 @@ cudaError_t launch_transmission(const float* vd, const float* vb, float2* T, int
                                 int rotate, float c, float sn, const int* box, double* zero_a, double* zero_b,
                                 cudaStream_t s) {
   const unsigned grid = vol_grid((size_t)Lz * Ly * Lx);
-  if (rotate) k_transmission<true><<<grid, 256, 0, s>>>(vd, vb, T, Lz, Ly, Lx, kdz, c, sn, box, zero_a, zero_b);
-  else k_transmission<false><<<grid, 256, 0, s>>>(vd, vb, T, Lz, Ly, Lx, kdz, c, sn, box, zero_a, zero_b);
+  if (rotate) (k_transmission<true><<<grid, 256, 0, s>>>(vd, vb, T, Lz, Ly, Lx, kdz, c, sn, box, zero_a, zero_b), note_launch());
+  else (k_transmission<false><<<grid, 256, 0, s>>>(vd, vb, T, Lz, Ly, Lx, kdz, c, sn, box, zero_a, zero_b), note_launch());
   return cudaGetLastError();
 }
 
 cudaError_t launch_rotate_adj(const double* gdr, const double* gbr, float* gd, float* gb, int Lz, int Ly, int Lx,
                               float c, float sn, const int* box, cudaStream_t s) {
-  k_rotate_adj<<<vol_grid((size_t)Lz * Ly * Lx), 256, 0, s>>>(gdr, gbr, gd, gb, Lz, Ly, Lx, c, sn, box);
+  (k_rotate_adj<<<vol_grid((size_t)Lz * Ly * Lx), 256, 0, s>>>(gdr, gbr, gd, gb, Lz, Ly, Lx, c, sn, box), note_launch());
   return cudaGetLastError();
 }
 
 cudaError_t launch_grad_add(const double* ad, const double* ab, float* gd, float* gb, int Lz, int Ly, int Lx,
                             const int* box, cudaStream_t s) {
-  k_grad_add<<<vol_grid((size_t)Lz * Ly * Lx), 256, 0, s>>>(ad, ab, gd, gb, Lz, Ly, Lx, box);
+  (k_grad_add<<<vol_grid((size_t)Lz * Ly * Lx), 256, 0, s>>>(ad, ab, gd, gb, Lz, Ly, Lx, box), note_launch());
   return cudaGetLastError();
 }
 

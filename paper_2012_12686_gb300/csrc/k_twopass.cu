@@ -860,11 +860,11 @@ __global__ void k_add2(float2* __restrict__ g, const float2* __restrict__ q, siz
 // ============================================================================ launch sequence
 template <int N, int MODE>
 static void row(const TPArgs& a, int gy, cudaStream_t s) {
-  k_row<N, MODE><<<dim3(N / Geo2<N>::RB, gy), NT2, row_smem_bytes<N>(), s>>>(a);
+  (k_row<N, MODE><<<dim3(N / Geo2<N>::RB, gy), NT2, row_smem_bytes<N>(), s>>>(a), note_launch());
 }
 template <int N, int MODE>
 static void col(const TPArgs& a, int gy, cudaStream_t s) {
-  k_col<N, MODE><<<dim3(N / Geo2<N>::CW, gy), NT2, col_smem_bytes<N>(), s>>>(a);
+  (k_col<N, MODE><<<dim3(N / Geo2<N>::CW, gy), NT2, col_smem_bytes<N>(), s>>>(a), note_launch());
 }
 
 template <int N, class F>
@@ -1007,7 +1007,7 @@ static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEven
       }
     }
   }
-  if (!fuse) k_loss2<<<dim3((unsigned)(NN / LOSS_PX), B * a.nd), 256, 0, s>>>(a);
+  if (!fuse) (k_loss2<<<dim3((unsigned)(NN / LOSS_PX), B * a.nd), 256, 0, s>>>(a), note_launch());
   if (a.adj) {
     // ---------------- adjoint
     for (int m = 0; m < M; ++m) {
@@ -1062,7 +1062,7 @@ static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEven
   }
   if (ev1) cudaEventRecord(ev1, s);
   if (a.adj) {
-    k_final2<<<1, 1024, 0, s>>>(a, nloss, ncol);
+    (k_final2<<<1, 1024, 0, s>>>(a, nloss, ncol), note_launch());
     if (want_gap && a.ggap) launch_gap_final(a.gapp, B, L - 1, ncol, a.ggap, s);
     if (a.g_probe) {
       const size_t MNN = (size_t)M * NN;
@@ -1072,7 +1072,7 @@ static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEven
         col<N, C_PG>(a, M, s);
         row<N, R_PG_OUT>(a, M, s);
       } else {
-        k_add2<<<1024, 256, 0, s>>>(a.g_probe, a.qsum, MNN);
+        (k_add2<<<1024, 256, 0, s>>>(a.g_probe, a.qsum, MNN), note_launch());
       }
     }
   }

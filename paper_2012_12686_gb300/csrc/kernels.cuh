@@ -2,10 +2,16 @@
 #pragma once
 #include <cuda.h>   // CUtensorMap (type only; encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 
 namespace adorym {
+
+// Kernels launched (or recorded into a captured graph) by this library in this process; every
+// launch site adds one (adorym_kernel_launches reports it)
+extern std::atomic<unsigned long long> g_kernel_launches;
+inline void note_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // One far-field (or near-field) loss/gradient launch over a batch, as seen by the fused kernel.
 struct PathArgs {
