@@ -324,7 +324,7 @@ def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
     from paper_2012_12686_gb300 import synth
-    from paper_2012_12686_gb300.adorym import Engine, Problem, kernel_launches
+    from paper_2012_12686_gb300.adorym import Engine, Problem, fp32_peak, kernel_launches
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
@@ -433,12 +433,17 @@ def run_ours(args, rank, world, local_rank):
     peaks = measured_peaks()
     props = torch.cuda.get_device_properties(dev)
     sm_max = (peaks.get("sm_max_mhz") or 2070.0)
-    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    fp32_peak_derived = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     k_ms = statistics.mean(path_ms)
     if far and N <= 128:
         achieved = units * flops_per_unit(N) / (k_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "kernel": f"k_path<{N},far>"}
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_derived, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak_derived, "kernel": f"k_path<{N},far>"}
+        try:   # the same fraction against an FFMA throughput kernel measured now, on this GPU
+            measured = fp32_peak(local_rank)
+            roof.update(peak_measured_ffma=measured, frac_of_measured_ffma=achieved / measured)
+        except Exception as exc:
+            roof.update(peak_measured_ffma=None, peak_measured_note=str(exc))
     else:
         # two-pass / near field: HBM-bound; algorithmic bytes of the minimal pass structure
         bpu = twopass_bytes_per_unit(N, L, cp, nd, far)

@@ -114,6 +114,13 @@ int adorym_check(adorym_ctx* ctx);
  * differences around a region give the kernels that region launched. */
 uint64_t adorym_kernel_launches(void);
 
+/* Measured FP32 fused-multiply-add throughput of `device` in TFLOP/s (2 flops per FMA): a
+ * throughput kernel of independent FMA chains on several CTAs per SM, best of four timed runs
+ * after one warm-up.  Measurement only (no counterpart in the paper): the denominator against
+ * which the FP32-bound kernels' roofline fraction can be read.  Allocates a small buffer, runs
+ * about 20 ms, synchronizes; returns ADORYM_OK or an error code. */
+int adorym_fp32_peak(int device, double* tflops);
+
 /* Register a resident object volume: delta, beta device pointers to FP32 [Lz][Ly][Lx]
  * (Sec. 2.1 refractive-index representation n = 1 - delta - i beta).  The memory stays owned
  * by the caller and must outlive the registration; its contents may change between calls

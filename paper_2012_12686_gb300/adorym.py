@@ -22,7 +22,8 @@ EXPORTS = ["adorym_create", "adorym_destroy", "adorym_last_error", "adorym_regis
            "adorym_unregister_object", "adorym_forward", "adorym_loss_grad", "adorym_submit", "adorym_poll",
            "adorym_serve_config", "adorym_serve_stats", "adorym_workspace_bytes", "adorym_enable_kernel_timing",
            "adorym_kernel_ms", "adorym_loss_grad_noalloc", "adorym_loss_grad_ext", "adorym_regularize",
-           "adorym_l1_weights", "adorym_check", "adorym_kernel_launches"]
+           "adorym_l1_weights", "adorym_check", "adorym_kernel_launches",
+           "adorym_fp32_peak"]
 
 
 class Problem(ctypes.Structure):
@@ -109,12 +110,22 @@ def lib() -> ctypes.CDLL:
         L.adorym_loss_grad_noalloc.argtypes = [vp, ctypes.POINTER(Problem), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.adorym_check.argtypes = [vp]
         L.adorym_kernel_launches.argtypes = []
+        L.adorym_fp32_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         for name in EXPORTS:
             if name not in ("adorym_destroy", "adorym_last_error", "adorym_kernel_launches"):
                 getattr(L, name).restype = ctypes.c_int
         L.adorym_kernel_launches.restype = ctypes.c_uint64
         _lib = L
     return _lib
+
+
+def fp32_peak(device: int = 0) -> float:
+    """Measured FP32 FMA throughput of the device, TFLOP/s."""
+    v = ctypes.c_double()
+    rc = lib().adorym_fp32_peak(device, ctypes.byref(v))
+    if rc:
+        raise AdorymError(rc, "fp32 peak measurement failed")
+    return v.value
 
 
 def kernel_launches() -> int:

@@ -1,0 +1,83 @@
+// FP32 FMA throughput of the device, measured: the denominator the fused kernel's FP32 roofline
+// fraction is read against (measurement only; the paper has no counterpart).
+//
+// Every thread runs kChains independent dependent chains of fused multiply-adds (enough
+// independent work per warp to cover the FMA latency), on a grid of several CTAs per SM; the
+// result is stored so that nothing is optimised away.  The values stay normal and bounded
+// (x <- x * a + b with |a| < 1).
+#include <algorithm>
+
+#include "adorym.h"
+#include "kernels.cuh"
+
+namespace adorym {
+
+constexpr int kChains = 8;
+
+__global__ void __launch_bounds__(256) k_ffma_peak(int iters, float a, float b, float* __restrict__ out) {
+  float x[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) x[c] = (float)(threadIdx.x + c) * 1e-3f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+#pragma unroll
+      for (int c = 0; c < kChains; ++c) x[c] = fmaf(x[c], a, b);
+    }
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += x[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace adorym
+
+using namespace adorym;
+
+extern "C" int adorym_fp32_peak(int device, double* tflops) {
+  if (!tflops) return ADORYM_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return ADORYM_EDEVICE;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    return ADORYM_EDEVICE;
+  }
+  const int blocks = sms * 8, threads = 256, iters = 4096;
+  float* out = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = 0;
+  if (cudaMalloc(&out, (size_t)blocks * threads * sizeof(float)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    rc = ADORYM_ENOMEM;
+  } else {
+    float best = 1e30f;
+    for (int rep = 0; rep < 5; ++rep) {   // first run warms up clocks and caches
+      cudaEventRecord(e0, s);
+      (k_ffma_peak<<<blocks, threads, 0, s>>>(iters, 0.9999f, 1e-4f, out), note_launch());
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = ADORYM_EDEVICE;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) best = std::min(best, ms);
+    }
+    if (!rc) {
+      const double flops = 2.0 * kChains * 16.0 * iters * (double)blocks * threads;
+      *tflops = flops / (best * 1e-3) / 1e12;
+    }
+  }
+  cudaGetLastError();
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  if (out) cudaFree(out);
+  return rc;
+}
