@@ -35,7 +35,12 @@
  *   Every entry point returns ADORYM_OK or an error code and never aborts; the message of the
  *   last error of a context is returned by adorym_last_error().  Kernels index the object only
  *   after bounds checks (pixels outside the volume read as vacuum and their gradients are
- *   dropped), so no input can make them access memory out of range.
+ *   dropped) and clamp patch corners to +-2^24 px, so no input can make them access memory out
+ *   of range.  Data that only the device sees (positions, hologram shifts) are checked while the
+ *   call runs: a non-finite or huge value sets the call's device status word, reported as
+ *   ADORYM_EDATA by calls with host outputs, by adorym_check and by adorym_poll.  No kernel
+ *   traps; the one device-side wait (a column tile's TMA copy) is bounded and reports a timeout
+ *   through the same status word.
  */
 #ifndef ADORYM_H
 #define ADORYM_H
