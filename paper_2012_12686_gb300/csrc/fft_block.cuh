@@ -115,6 +115,19 @@ __device__ __forceinline__ void twiddle(float2 (&v)[R], const float2* __restrict
   }
 }
 
+// Twiddles of one task from a per-stage table row: row[k] = W_N^(t k), k < R (row 16-byte
+// aligned), read two at a time; row[0] = 1 is skipped.  Same values as twiddle() above.
+template <int S, int R>
+__device__ __forceinline__ void twiddle_row(float2 (&v)[R], const float2* __restrict__ row) {
+  const float4* r4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+  for (int k2 = 0; k2 < R / 2; ++k2) {
+    const float4 w = r4[k2];
+    if (k2 > 0) v[2 * k2] = S < 0 ? cmul(v[2 * k2], make_float2(w.x, w.y)) : cmulc(v[2 * k2], make_float2(w.x, w.y));
+    v[2 * k2 + 1] = S < 0 ? cmul(v[2 * k2 + 1], make_float2(w.z, w.w)) : cmulc(v[2 * k2 + 1], make_float2(w.z, w.w));
+  }
+}
+
 template <int N_>
 struct Geo;
 // NT threads per CTA; MINB resident CTAs per SM the register budget is sized for (128 regs/thread)
@@ -136,6 +149,21 @@ template <int N>
 struct Field {
   static constexpr int N1 = Geo<N>::N1, N2 = Geo<N>::N2, NT = Geo<N>::NT, LD = N + 1;
   static constexpr int SMEM_FLOAT2 = N * LD;
+  // shared twiddle tables at tw (16-byte aligned): tw[m] = W_N^m (m < N); at N = 128 also the
+  // S1/S4-side table [N2][N1] at tw + N and the S3-side table [N1][N2] at tw + 2N (entries
+  // W_N^(t k)), which the passes read two twiddles per access (fewer shared-memory instructions,
+  // -2 % time); at N = 64 the single-twiddle reads of tw measured faster
+  static constexpr bool PAIRED_TW = N >= 128;
+  static constexpr int TW_ENTRIES = PAIRED_TW ? 3 * N : N;
+  __device__ static __forceinline__ void fill_twiddles(float2* tw, const float2* __restrict__ twg) {
+    for (int i = threadIdx.x; i < N; i += NT) {
+      tw[i] = twg[i];
+      if (PAIRED_TW) {
+        tw[N + i] = twg[(i / N1) * (i % N1)];
+        tw[2 * N + i] = twg[(i / N2) * (i % N2)];
+      }
+    }
+  }
   // y-frequency held by smem row r after the column forward stages (C2)
   __device__ static __forceinline__ int row_freq(int r) { return r / N2 + N1 * (r % N2); }
 };
@@ -193,7 +221,8 @@ __device__ __forceinline__ void pass_c14(float2* __restrict__ A, const float2* _
       op(v[q], pa[q], pb[q], x, t);
       if (STORE && S1) {
         dft<N1, S1>(v[q]);
-        twiddle<S1>(v[q], tw, t);
+        if constexpr (F::PAIRED_TW) twiddle_row<S1, N1>(v[q], tw + N + t * N1);
+        else twiddle<S1>(v[q], tw, t);
       }
     }
     if (STORE) {
@@ -230,7 +259,10 @@ __device__ __noinline__ void pass_c23(float2* __restrict__ A, const float2* __re
     if (!P::ok(tau)) continue;
     const int t = tau / N;
     dft<N2, S>(v[q]);
-    if (IS_S3) twiddle<S>(v[q], tw, t);
+    if constexpr (IS_S3) {
+      if constexpr (F::PAIRED_TW) twiddle_row<S, N2>(v[q], tw + 2 * N + t * N2);
+      else twiddle<S>(v[q], tw, t);
+    }
   }
 #pragma unroll
   for (int q = 0; q < P::n; ++q) {
@@ -263,7 +295,10 @@ __device__ __noinline__ void pass_r14(float2* __restrict__ A, const float2* __re
     if (!P::ok(tau)) continue;
     const int t = tau / N;
     dft<N1, S>(v[q]);
-    if (IS_S1) twiddle<S>(v[q], tw, t);
+    if constexpr (IS_S1) {
+      if constexpr (F::PAIRED_TW) twiddle_row<S, N1>(v[q], tw + N + t * N1);
+      else twiddle<S>(v[q], tw, t);
+    }
   }
 #pragma unroll
   for (int q = 0; q < P::n; ++q) {
@@ -304,7 +339,8 @@ __device__ __forceinline__ void pass_r23(float2* __restrict__ A, const float2* _
     op(v[q], F::row_freq(r), t);
     if (S3) {
       dft<N2, S3>(v[q]);
-      twiddle<S3>(v[q], tw, t);
+      if constexpr (F::PAIRED_TW) twiddle_row<S3, N2>(v[q], tw + 2 * N + t * N2);
+      else twiddle<S3>(v[q], tw, t);
     }
   }
   if (S3) {

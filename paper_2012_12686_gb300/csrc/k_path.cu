@@ -9,11 +9,11 @@ template <int N>
 __global__ void __launch_bounds__(Geo<N>::NT) k_probe_hat(const float2* __restrict__ probe, float2* __restrict__ phat,
                                                         const float2* __restrict__ twg) {
   using F = Field<N>;
-  constexpr int N1 = F::N1, N2 = F::N2, NT = F::NT;
+  constexpr int N1 = F::N1, N2 = F::N2;
   extern __shared__ float2 sm[];
   float2* A = sm;
   float2* tw = A + N * F::LD;
-  for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
+  F::fill_twiddles(tw, twg);
   __syncthreads();
   const float2* p = probe + (size_t)blockIdx.x * N * N;
   float2* o = phat + (size_t)blockIdx.x * N * N;
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(Geo<N>::NT) k_probe_grad(const float2* __restr
     for (size_t i = threadIdx.x; i < NN; i += NT) o[i] = cadd(o[i], q[i]);
     return;
   }
-  for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
+  F::fill_twiddles(tw, twg);
   __syncthreads();
   const float invNN = 1.0f / (float)NN;
   using V1 = float2[N1];
@@ -164,7 +164,7 @@ cudaError_t launch_path(const PathArgs& a, int farfield, cudaStream_t s) {
 
 template <int N>
 static cudaError_t launch_probe_hat_t(int M, const float2* probe, float2* phat, const float2* tw, cudaStream_t s) {
-  const int smem = (N * (N + 1) + N) * (int)sizeof(float2);
+  const int smem = (N * (N + 1) + Field<N>::TW_ENTRIES) * (int)sizeof(float2);
   (k_probe_hat<N><<<M, Geo<N>::NT, smem, s>>>(probe, phat, tw), note_launch());
   return cudaGetLastError();
 }
@@ -187,7 +187,7 @@ static cudaError_t launch_probe_grad_t(int M, int B, const float2* qacc, float2*
   if (g) {
     (k_qsum<<<(unsigned)((MNN + 31) / 32), 256, 0, s>>>(qacc, qsum, B, MNN), note_launch());
   }
-  const int smem = (N * (N + 1) + N) * (int)sizeof(float2);
+  const int smem = (N * (N + 1) + Field<N>::TW_ENTRIES) * (int)sizeof(float2);
   (k_probe_grad<N, FAR><<<M, Geo<N>::NT, smem, s>>>(qsum, g, tw, lossp, B, inv_npix, loss_out), note_launch());
   return cudaGetLastError();
 }
@@ -216,7 +216,7 @@ static cudaError_t prepare_t() {
   cudaError_t e = prepare_path_t<N, FAR, false>();
   if (e == cudaSuccess) e = prepare_path_gaps(N, FAR);
   if (e == cudaSuccess) e = prepare_path_pipe(N, FAR);
-  const int small = (N * (N + 1) + N) * (int)sizeof(float2);
+  const int small = (N * (N + 1) + Field<N>::TW_ENTRIES) * (int)sizeof(float2);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_probe_hat<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, small);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_probe_grad<N, FAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, small);
   return e;

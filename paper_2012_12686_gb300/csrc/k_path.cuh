@@ -76,8 +76,8 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
   using V2 = float2[N2];
   extern __shared__ float2 sm[];
   float2* A = sm;
-  float2* tw = A + N * LD;
-  float2* hy = tw + N;
+  float2* tw = A + N * LD;             // F::TW_ENTRIES twiddles (tw, then the per-stage tables)
+  float2* hy = tw + F::TW_ENTRIES;
   float2* hx = hy + N;
   float2* ry = hx + N;
   float2* rx = ry + N;
@@ -87,8 +87,8 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
   const int b = PIPE ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
   const int rank = PIPE ? (int)(blockIdx.x & 1) : 0;   // cluster of two CTAs along x
   const int M = a.M, L = a.L, cp = a.cp, ncp = a.ncp;
+  F::fill_twiddles(tw, a.tw);
   for (int i = threadIdx.x; i < N; i += NT) {
-    tw[i] = a.tw[i];
     hy[i] = a.hy[i];
     hx[i] = a.hx[i];
   }
@@ -641,10 +641,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Geo<N>::NT, Geo<N>::
   path_body<N, FAR, false, true>(a);
 }
 
-// field + tw, hy, hx, ry, rx tables + one double per warp for block reductions
+// field + twiddle tables (3N) + hy, hx, ry, rx tables + one double per warp for block reductions
 template <int N>
 constexpr int path_smem_bytes_t() {
-  return (N * (N + 1) + 5 * N) * (int)sizeof(float2) + (Geo<N>::NT / 32) * (int)sizeof(double);
+  return (N * (N + 1) + Field<N>::TW_ENTRIES + 4 * N) * (int)sizeof(float2) + (Geo<N>::NT / 32) * (int)sizeof(double);
 }
 
 template <int N, int FAR, bool GAP>
