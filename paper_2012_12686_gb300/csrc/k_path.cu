@@ -224,10 +224,11 @@ static cudaError_t prepare_t() {
 
 cudaError_t prepare_path(int N, int farfield) {
   // idempotent; called by every entry point before it enqueues (never inside a stream capture)
-  static bool done[11][2] = {};
+  static std::atomic<bool> done[kMaxDevices][11][2] = {};
+  const int dev = current_device();
   int l = 0;
   while ((1 << l) < N) ++l;
-  if (l < 11 && done[l][farfield ? 1 : 0]) return cudaSuccess;
+  if (dev >= 0 && l < 11 && done[dev][l][farfield ? 1 : 0].load(std::memory_order_acquire)) return cudaSuccess;
   cudaError_t e = cudaErrorInvalidValue;
   switch (N) {
 #define ADORYM_CASE(n) \
@@ -243,7 +244,7 @@ cudaError_t prepare_path(int N, int farfield) {
     default:
       return cudaErrorInvalidValue;
   }
-  if (e == cudaSuccess && l < 11) done[l][farfield ? 1 : 0] = true;
+  if (e == cudaSuccess && dev >= 0 && l < 11) done[dev][l][farfield ? 1 : 0].store(true, std::memory_order_release);
   return e;
 }
 

@@ -886,15 +886,16 @@ static cudaError_t prepare_t2() {
   return e;
 }
 
-static bool g_prepared2[3] = {false, false, false};
 
 cudaError_t prepare_twopass(int N) {
   // idempotent; called by every entry point before it enqueues (never inside a stream capture)
   const int i = N == 256 ? 0 : N == 512 ? 1 : N == 1024 ? 2 : -1;
   if (i < 0) return cudaErrorInvalidValue;
-  if (g_prepared2[i]) return cudaSuccess;
+  static std::atomic<bool> prepared[kMaxDevices][3] = {};
+  const int dev = current_device();
+  if (dev >= 0 && prepared[dev][i].load(std::memory_order_acquire)) return cudaSuccess;
   cudaError_t e = N == 256 ? prepare_t2<256>() : N == 512 ? prepare_t2<512>() : prepare_t2<1024>();
-  if (e == cudaSuccess) g_prepared2[i] = true;
+  if (e == cudaSuccess && dev >= 0) prepared[dev][i].store(true, std::memory_order_release);
   return e;
 }
 
@@ -905,18 +906,16 @@ cudaError_t prepare_twopass(int N) {
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link against the driver)
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // looked up once per process (thread-safe initialisation of a function-local static)
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    else
-      cudaGetLastError();
-  }
+      return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+    return nullptr;
+  }();
   return fn;
 }
 

@@ -13,6 +13,18 @@ namespace adorym {
 extern std::atomic<unsigned long long> g_kernel_launches;
 inline void note_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
 
+// kernel attributes are per device: the "already prepared" caches are indexed by the current
+// device (up to this many) and atomic, as several contexts may prepare from different threads
+constexpr int kMaxDevices = 64;
+inline int current_device() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return (d >= 0 && d < kMaxDevices) ? d : -1;
+}
+
 // One far-field (or near-field) loss/gradient launch over a batch, as seen by the fused kernel.
 struct PathArgs {
   int N, L, M, B, Ly, Lx;
