@@ -37,6 +37,11 @@ using namespace adorym;
 
 extern "C" int adorym_fp32_peak(int device, double* tflops) {
   if (!tflops) return ADORYM_EINVAL;
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess) {
+    cudaGetLastError();
+    return ADORYM_EDEVICE;
+  }
   if (cudaSetDevice(device) != cudaSuccess) {
     cudaGetLastError();
     return ADORYM_EDEVICE;
@@ -44,6 +49,7 @@ extern "C" int adorym_fp32_peak(int device, double* tflops) {
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) {
     cudaGetLastError();
+    cudaSetDevice(prev);
     return ADORYM_EDEVICE;
   }
   const int blocks = sms * 8, threads = 256, iters = 4096;
@@ -79,5 +85,6 @@ extern "C" int adorym_fp32_peak(int device, double* tflops) {
   if (e1) cudaEventDestroy(e1);
   if (s) cudaStreamDestroy(s);
   if (out) cudaFree(out);
+  cudaSetDevice(prev);   // the caller's current device is left as it was
   return rc;
 }
