@@ -25,8 +25,9 @@
 // After C2, smem row r holds y-frequency  r / N2 + N1 * (r % N2).
 //
 // Twiddles W_N^m = exp(-2 pi i m / N) come from a table built in FP64 on the
-// host and rounded once to FP32; the in-register DFT_R (R <= 16) uses
-// compile-time constants of exp(+-2 pi i k / 16).
+// host and rounded once to FP32 (at N = 128 rearranged per stage so that a task
+// reads two of them per 128-bit shared load); the in-register DFT_R (R <= 16)
+// uses compile-time constants of exp(+-2 pi i k / 16).
 #pragma once
 #include <cuda_runtime.h>
 #include <utility>

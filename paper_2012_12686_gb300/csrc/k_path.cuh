@@ -9,7 +9,7 @@
 //   near: Psi_d = IDFT_-{ DFT_-[phi_L-1] H_d exp(-2 pi i s_d.nu) }   Eq. fresnel_prop to the detector
 //   I = sum_modes |Psi|^2                                            Eq. multimode
 // Loss: mean over the batch's detector pixels of Eq. lsq_loss (amplitudes, I + eps) or
-// Eq. poisson_loss (log(I + eps)), summed in FP64.
+// Eq. poisson_loss (log(I + eps)), summed Kahan-compensated per thread and in FP64 across threads.
 // Adjoint (chain rule; the paper obtains it by reverse-mode AD, Sec. 2.3.1):
 //   Psibar = 2 dL/dI Psi;  phibar_L-1 = (1/N) DFT_-[Psibar] (far) or IDFT_-{sum_d conj(G_d) DFT_-[Psibar_d]} (near)
 //   psibar_j = conj(T_j) phibar_j;  dL/ddelta_j += k dz Im(psibar_j conj psi_j);

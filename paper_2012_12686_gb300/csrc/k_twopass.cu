@@ -14,8 +14,12 @@
 // x-transform) + column kernel (forward y-transform, propagator, inverse y-transform).  The
 // row tile uses a skewed shared-memory layout (one pad element after every N2 elements), which
 // keeps both the strided and the contiguous stage accesses free of bank conflicts with the
-// lane index on the x digit, so every global access is coalesced.  Loss and position-gradient
-// reductions write per-CTA FP64 partials that a final kernel adds in a fixed order.
+// lane index on the x digit, so every global access is coalesced.  The column tile is brought in
+// by TMA (a 2-D tensor map over the field buffer, completion on an mbarrier) and lands in the
+// [row][column] layout the first in-place stage reads.  With one probe mode and measured data the
+// detector pass also forms the loss term and the adjoint seed.  Loss and position-gradient
+// reductions write per-CTA FP64 partials (compensated FP32 within a CTA) that a final kernel adds
+// in a fixed order.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
