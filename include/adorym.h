@@ -62,6 +62,7 @@ extern "C" {
 #define ADORYM_EDATA 7       /* a kernel found invalid input data in device memory (a position
                                 that is not finite or lies beyond +-2^24 px); reported through
                                 the call's device status word, see adorym_check              */
+#define ADORYM_ECANCELED 8   /* adorym_poll: the request was cancelled before it was admitted   */
 
 #define ADORYM_LOSS_LSQ 0     /* Eq. lsq_loss: mean (sqrt(I+eps) - sqrt(I_meas+eps))^2        */
 #define ADORYM_LOSS_POISSON 1 /* Eq. poisson_loss: mean (I - I_meas log(I+eps))               */
@@ -230,6 +231,17 @@ int adorym_poll(adorym_ctx* ctx, uint64_t ticket, int64_t timeout_us);
  * footprint budget in bytes for admitted requests' workspaces (0 = no limit).  Only allowed
  * while no request is in flight. */
 int adorym_serve_config(adorym_ctx* ctx, int slots, uint64_t budget_bytes);
+
+/* Cancel a serving request that is still waiting for admission: it is removed from the queue and
+ * its adorym_poll returns ADORYM_ECANCELED.  Returns ADORYM_OK, ADORYM_ENOENT for an unknown
+ * ticket, or ADORYM_EINVAL when the request has already been admitted (its GPU work is not
+ * interrupted) or has finished.  No counterpart in the paper (serving). */
+int adorym_cancel(adorym_ctx* ctx, uint64_t ticket);
+
+/* Failure injection for tests of error handling, host side only: the next `count` workspace
+ * allocations of ctx fail with ADORYM_ENOMEM without touching the device (the context's existing
+ * workspace is kept, later calls allocate normally).  No counterpart in the paper. */
+int adorym_inject_alloc_failures(adorym_ctx* ctx, int count);
 
 /* Serving statistics since the context was created: completed requests and the number of
  * times a request had to wait for admission. */

@@ -14,7 +14,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libadorym.so")
 
-OK, EINVAL, ENOMEM, ETIMEDOUT, EDEVICE, ENOENT, ETOOBIG, EDATA = 0, 1, 2, 3, 4, 5, 6, 7
+OK, EINVAL, ENOMEM, ETIMEDOUT, EDEVICE, ENOENT, ETOOBIG, EDATA, ECANCELED = 0, 1, 2, 3, 4, 5, 6, 7, 8
 NOALLOC_SCRATCH_BYTES = 64 << 20
 LOSS = {"lsq": 0, "poisson": 1}
 
@@ -23,7 +23,7 @@ EXPORTS = ["adorym_create", "adorym_destroy", "adorym_last_error", "adorym_regis
            "adorym_serve_config", "adorym_serve_stats", "adorym_workspace_bytes", "adorym_enable_kernel_timing",
            "adorym_kernel_ms", "adorym_loss_grad_noalloc", "adorym_loss_grad_ext", "adorym_regularize",
            "adorym_l1_weights", "adorym_check", "adorym_kernel_launches",
-           "adorym_fp32_peak"]
+           "adorym_fp32_peak", "adorym_cancel", "adorym_inject_alloc_failures"]
 
 
 class Problem(ctypes.Structure):
@@ -111,6 +111,8 @@ def lib() -> ctypes.CDLL:
         L.adorym_check.argtypes = [vp]
         L.adorym_kernel_launches.argtypes = []
         L.adorym_fp32_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
+        L.adorym_cancel.argtypes = [vp, u64]
+        L.adorym_inject_alloc_failures.argtypes = [vp, i32]
         for name in EXPORTS:
             if name not in ("adorym_destroy", "adorym_last_error", "adorym_kernel_launches"):
                 getattr(L, name).restype = ctypes.c_int
@@ -265,6 +267,14 @@ class Engine:
         """Wait for the context's stream and raise on the last call's device status word (EDATA:
         invalid positions / shifts found by the kernels)."""
         return self._check(lib().adorym_check(self._ctx))
+
+    def cancel(self, ticket: int) -> int:
+        """Cancel a request still waiting for admission (its poll then reports ECANCELED)."""
+        return self._check(lib().adorym_cancel(self._ctx, ticket))
+
+    def inject_alloc_failures(self, count: int) -> int:
+        """Make the next `count` workspace allocations fail with ENOMEM (host side; for tests)."""
+        return self._check(lib().adorym_inject_alloc_failures(self._ctx, count))
 
     def serve_stats(self):
         c, w = ctypes.c_uint64(), ctypes.c_uint64()

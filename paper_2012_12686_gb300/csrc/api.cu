@@ -455,6 +455,10 @@ static int ptr_kind(const void* p) {
 
 static int ensure_ws(adorym_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->ws_cap) return ADORYM_OK;
+  if (ctx->inject_alloc_failures > 0) {   // injected: fail before the current workspace is touched
+    --ctx->inject_alloc_failures;
+    return fail(ctx, ADORYM_ENOMEM, "injected workspace allocation failure");
+  }
   cudaStreamSynchronize(ctx->stream);
   if (ctx->ws) cudaFree(ctx->ws);
   ctx->ws = nullptr;
@@ -507,6 +511,13 @@ void adorym_destroy(adorym_ctx* ctx) {
 }
 
 const char* adorym_last_error(adorym_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int adorym_inject_alloc_failures(adorym_ctx* ctx, int count) {
+  if (!ctx || count < 0) return ADORYM_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->inject_alloc_failures = count;
+  return ADORYM_OK;
+}
 
 uint64_t adorym_kernel_launches(void) { return g_kernel_launches.load(std::memory_order_relaxed); }
 

@@ -109,6 +109,7 @@ struct adorym_ctx {
   cudaStream_t copy_stream = nullptr;          // host-to-device copy of measured intensities
   cudaEvent_t ev_fork = nullptr, ev_meas = nullptr;
   int* status_host = nullptr;                  // pinned copy of the last call's status word
+  int inject_alloc_failures = 0;               // adorym_inject_alloc_failures: pending count
   bool timed = false;
   adorym::Serve* serve = nullptr;    // owned; created by the first submit or serve_config
 };

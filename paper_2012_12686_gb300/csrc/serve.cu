@@ -438,6 +438,29 @@ int adorym_poll(adorym_ctx* ctx, uint64_t ticket, int64_t timeout_us) {
   return rc;
 }
 
+int adorym_cancel(adorym_ctx* ctx, uint64_t ticket) {
+  if (!ctx) return ADORYM_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!ctx->serve) return ADORYM_ENOENT;
+  Serve& S = *ctx->serve;
+  auto it = S.tickets.find(ticket);
+  if (it == S.tickets.end()) return ADORYM_ENOENT;
+  if (it->second.state != 0) {
+    ctx->err = "request already admitted or finished";
+    return ADORYM_EINVAL;
+  }
+  for (auto q = S.queue.begin(); q != S.queue.end(); ++q)
+    if (*q == ticket) {
+      S.queue.erase(q);
+      break;
+    }
+  it->second.state = 2;
+  it->second.rc = ADORYM_ECANCELED;
+  S.cv_done.notify_all();
+  S.cv_work.notify_all();   // the request behind it may now fit
+  return ADORYM_OK;
+}
+
 int adorym_serve_stats(adorym_ctx* ctx, uint64_t* completed, uint64_t* admission_waits) {
   if (!ctx) return ADORYM_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
