@@ -254,8 +254,11 @@ int adorym_serve_stats(adorym_ctx* ctx, uint64_t* completed, uint64_t* admission
 int adorym_enable_kernel_timing(adorym_ctx* ctx, int enable);
 int adorym_kernel_ms(adorym_ctx* ctx, float* path_ms);
 
-/* Device workspace (bytes) that adorym_loss_grad needs for this problem, for admission
- * planning by callers.  grads: bitmask 1 = object, 2 = probe, 4 = positions. */
+/* Device workspace (bytes) that a served request (adorym_submit) needs for this problem, for
+ * admission planning by callers.  grads: bitmask 1 = object, 2 = probe, 4 = positions.  A direct
+ * adorym_loss_grad call with N <= 128 and a batch below the device's SM count takes more: the
+ * SMs the batch leaves idle recompute checkpoint segments into a store of
+ * B * M * (ncp - 1) * cp * N^2 * 8 bytes (ncp checkpoints every cp slices). */
 int adorym_workspace_bytes(const adorym_problem* p, int grads, uint64_t* bytes);
 
 /* Size of the fixed device scratch array used by adorym_loss_grad_noalloc. */

@@ -148,6 +148,32 @@ int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan
   return ADORYM_OK;
 }
 
+#ifndef ADORYM_HELPERS
+#define ADORYM_HELPERS 1
+#endif
+
+size_t helper_ctl_ints(const Plan& q) {
+  return q.helpers ? 1 + (size_t)q.p.B * q.p.M * (1 + q.ncp) : 0;
+}
+
+void plan_helpers(Plan* pl) {
+  Plan& q = *pl;
+  const long long B = q.p.B, M = q.p.M, sms = device_sms();
+  if (!ADORYM_HELPERS || two_pass(q.p.N) || !q.adj || q.pipe || q.gaps || q.ncp < 2 || q.cp < 2 || B >= sms) return;
+  // segments 0..ncp-2 with more than one slice are the tasks; one helper per idle SM, at most one per task
+  long long tasks = 0;
+  for (int s = 0; s + 1 < q.ncp; ++s) tasks += (std::min((s + 1) * q.cp, q.p.L) - 1 > s * q.cp) ? B * M : 0;
+  q.helpers = (int)std::min(sms - B, tasks);
+  if (q.helpers <= 0) {
+    q.helpers = 0;
+    return;
+  }
+  q.off_hseg = q.total;
+  q.total += al((size_t)B * M * (q.ncp - 1) * q.cp * q.NN * sizeof(float2));
+  q.off_hctl = q.total;
+  q.total += al(helper_ctl_ints(q) * sizeof(int));
+}
+
 static std::string table_key(const adorym_problem& p) {
   char buf[256];
   int n = snprintf(buf, sizeof buf, "%d|%.17g|%d", p.N, p.lambda_dz_over_px2, p.farfield ? 0 : p.n_dist);
@@ -249,8 +275,9 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
   int* box = reinterpret_cast<int*>(W(pl.off_box));
   int* status = c.status ? c.status : reinterpret_cast<int*>(W(pl.off_status));
   if (!c.status && (rc = chk(cudaMemsetAsync(status, 0, sizeof(int), s), "status"))) return rc;
+  int* hctl = pl.helpers ? reinterpret_cast<int*>(W(pl.off_hctl)) : nullptr;
   if ((rc = chk(launch_bbox(c.pos, p.B, p.N, p.Ly, p.Lx, pl.far ? 1 : 0, pl.tomo ? 1 : 0, box, 2 * p.B * pl.nd, status,
-                            s),
+                            s, hctl, (int)helper_ctl_ints(pl)),
                 "bbox")))
     return rc;
   // near field with one probe mode: one term per voxel and call, added in place by the kernels
@@ -383,6 +410,13 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
         a.spseg = reinterpret_cast<float2*>(W(pl.off_spseg));
         a.gapp = reinterpret_cast<double*>(W(pl.off_gapp));
       }
+    }
+    if (pl.helpers) {
+      a.helpers = pl.helpers;
+      a.hseg = reinterpret_cast<float2*>(W(pl.off_hseg));
+      a.hnext = hctl;
+      a.hprog = hctl + 1;
+      a.hflag = hctl + 1 + (size_t)p.B * p.M;
     }
     a.far = reinterpret_cast<float2*>(W(pl.off_far));
     a.gI = reinterpret_cast<float*>(W(pl.off_gI));
@@ -596,6 +630,7 @@ static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const 
   if (rc) return fail(ctx, rc, msg);
   std::string err;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "set device");
+  plan_helpers(&pl);
   Tables tab;
   if ((rc = get_tables(ctx, *p, &tab))) return rc;
   if ((rc = prepare_kernels(*p, &msg))) return fail(ctx, rc, msg);

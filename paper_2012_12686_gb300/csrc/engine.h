@@ -31,12 +31,14 @@ struct Plan {
   bool want_obj = false, want_probe = false, want_pos = false, want_loss = false, want_nf = false;
   bool gaps = false, want_gaps = false;   // variable slice spacing / its gradient
   bool pipe = false;   // shared-memory path: two-CTA clusters (adjoint + segment recompute)
+  int helpers = 0;     // shared-memory path: recompute-helper CTAs on SMs the batch leaves idle
   size_t NN = 0;
   size_t off_phat = 0, off_ckpt = 0, off_seg = 0, off_park = 0, off_far = 0, off_gI = 0, off_fbar = 0,
          off_lossp = 0, off_qacc = 0, off_qsum = 0, off_T = 0, off_grot = 0, off_loss = 0;
   // two-pass path (N >= 256)
   size_t off_FA = 0, off_FR = 0, off_tmp = 0, off_posp = 0;
   size_t off_box = 0;   // int4 bounding box of the batch's patches
+  size_t off_hseg = 0, off_hctl = 0;   // helper segment store; helper control words (hnext, hprog, hflag)
   size_t off_status = 0;   // int device status word of the call (ADORYM_STATUS_* bits)
   size_t off_spck = 0, off_spseg = 0, off_gapp = 0, off_s_ggap = 0;   // slice-gap gradient
   // staging for host-memory arguments
@@ -70,6 +72,10 @@ struct CallPtrs {
 int validate(const adorym_problem& p, const char** err);
 bool two_pass(int N);   // N >= 256: fields in HBM, row/column kernels per slice step
 int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan* plan, const char** err);
+// direct calls on an otherwise idle device: give the fused kernel recompute helpers on the SMs a
+// batch below the SM count leaves idle (extends the workspace; serving does not use them)
+void plan_helpers(Plan* plan);
+size_t helper_ctl_ints(const Plan& plan);
 // FP64-built tables (twiddles, propagator factors) of a problem: table_count(p) float2 values
 size_t table_count(const adorym_problem& p);
 void fill_tables(const adorym_problem& p, float2* out);

@@ -26,6 +26,15 @@
 // s-1 from its checkpoint while rank 0 reverses segment s, into the other half of a
 // double-buffered segment store, so the recompute leaves the critical path.  The two meet at one
 // hardware cluster barrier per segment (no spin-waits).
+//
+// Recompute helpers (one CTA per position, batch below the SM count): the SMs the batch leaves
+// idle run helper CTAs that recompute segments 0, 1, ... of every position (in that order: the
+// adjoint sweep needs them last, and their checkpoints are written first) into a separate store.
+// A position takes each segment with an atomic compare-and-swap when its sweep reaches it: a
+// segment no helper has started is recomputed by the position itself, a finished one is read from
+// the store, and only a segment a helper is working on is waited for.  A helper waits for a
+// checkpoint only before claiming its segment.  Both waits are bounded (a helper skips the
+// segment, a position recomputes it itself), so no CTA depends on another being resident.
 #pragma once
 #include "numerics.cuh"
 #include "fft_block.cuh"
@@ -63,6 +72,45 @@ __device__ __forceinline__ void ramp_table(float2* out, float d, int N, int NT) 
 __device__ __forceinline__ void cluster_barrier() {
   __threadfence();
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// gpu-scope acquire load / release store of a flag word (helper protocol)
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// thread 0 of a position's CTA at segment s: take the segment (0 -> 3) or find it recomputed by a
+// helper.  Waits, bounded by about 2^28 cycles, only while a helper holds it (1).  True: the
+// helper's slices are complete and visible; false: the position recomputes the segment itself.
+__device__ __forceinline__ bool take_segment(int* flag) {
+  int st = atomicCAS(flag, 0, 3);
+  if (st == 1) {
+    const long long t0 = clock64();
+    do {
+      __nanosleep(256);
+      st = ld_acquire_gpu(flag);
+    } while (st == 1 && clock64() - t0 < (1ll << 28));
+  }
+  __threadfence();
+  return st == 2;
+}
+
+// thread 0 of a helper: wait until the position's forward has written `need` checkpoints (1);
+// 0 when the position took the segment meanwhile; -1 after about 2^24 cycles (the position is
+// not progressing, e.g. not resident: the helper stops so that it does not hold the SM)
+__device__ __forceinline__ int wait_checkpoints(const int* prog, int need, const int* flag) {
+  const long long t0 = clock64();
+  for (;;) {
+    if (ld_acquire_gpu(prog) >= need) return 1;
+    if (*reinterpret_cast<const volatile int*>(flag) != 0) return 0;
+    if (clock64() - t0 > (1ll << 24)) return -1;
+    __nanosleep(512);
+  }
 }
 
 // GAP: per-gap propagators (variable slice spacing) and the slice-gap gradient; the uniform-spacing
@@ -275,6 +323,13 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
         pass_c14<N, +1, -1, true, true>(A, tw, pre_T(j), fwd_op(j, false));
       }
       __syncthreads();
+      if constexpr (!PIPE && !GAP) {
+        // checkpoint j / cp is written: helpers may recompute segment j / cp from now on
+        if (a.helpers && adj && j % cp == 0 && threadIdx.x == 0) {
+          __threadfence();
+          st_release_gpu(a.hprog + (size_t)b * M + m, j / cp + 1);
+        }
+      }
       if (!last) {
         propagate_tail(false, j, spec_slot_fwd(j + 1), nullptr);
         continue;
@@ -524,20 +579,35 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
     for (int s = ncp - 1; s >= 0; --s) {
       const int j0 = s * cp, j1 = min(j0 + cp, L) - 1;
       float2* sg = seg_slot(m, s);
+      bool from_helper = false;   // psi_{j0+1..j1} in a helper's store instead of the own slot
       if (!PIPE && s != ncp - 1 && j1 > j0) {
-        // park the adjoint field, recompute the segment in shared memory, restore
-        float2* pk = a.park + (size_t)b * N * LD;
-        for (int i = threadIdx.x; i < N * LD; i += NT) pk[i] = A[i];
-        __syncthreads();
-        recompute(s, sg);
-        for (int i = threadIdx.x; i < N * LD; i += NT) A[i] = pk[i];
-        __syncthreads();
+        bool own = true;
+        if constexpr (!GAP) {
+          if (a.helpers) {
+            bool done = false;
+            if (threadIdx.x == 0) done = take_segment(a.hflag + ((size_t)b * M + m) * ncp + s);
+            // the vote is CTA-uniform; the lane-0 broadcast lets the compiler treat the branch
+            // below as warp-uniform (a plain vote result cost ~6 % through extra spills)
+            from_helper = __shfl_sync(0xffffffffu, __syncthreads_or(done), 0) != 0;
+            own = !from_helper;
+          }
+        }
+        if (own) {
+          // park the adjoint field, recompute the segment in shared memory, restore
+          float2* pk = a.park + (size_t)b * N * LD;
+          for (int i = threadIdx.x; i < N * LD; i += NT) pk[i] = A[i];
+          __syncthreads();
+          recompute(s, sg);
+          for (int i = threadIdx.x; i < N * LD; i += NT) A[i] = pk[i];
+          __syncthreads();
+        }
       }
       for (int j = j1; j >= j0; --j) {
         const bool first = (j == 0);
         // prefetch T_j and psi_j (checkpoint or recomputed segment)
         auto pre = [&, j](V1& pa, V1& pb, int x, int t) {
-          const float2* src = (j == j0) ? ck + (size_t)s * NN : sg + (size_t)(j - j0) * NN;
+          const float2* seg_j = from_helper ? a.hseg + (((size_t)b * M + m) * (ncp - 1) + s) * cp * NN : sg;
+          const float2* src = (j == j0) ? ck + (size_t)s * NN : seg_j + (size_t)(j - j0) * NN;
           tloads(pa, j, x, t);
 #pragma unroll
           for (int k = 0; k < N1; ++k) pb[k] = __ldcg(src + (N2 * k + t) * N + x);   // L2: written by the partner CTA
@@ -629,9 +699,130 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
   }
 }
 
+// A recompute helper (CTA blockIdx.x >= B of k_path without slice gaps): claims segments
+// 0..ncp-2 of the positions in segment-major order and recomputes psi_{j0+1..j1} of each from its
+// checkpoint into the helper store, with the same passes and operation order as a position's own
+// recompute (so the result does not depend on which CTA recomputed a segment).  Kept apart from
+// path_body so that the position code keeps its register allocation.
+template <int N, int FAR>
+__device__ __forceinline__ void helper_body(const PathArgs& a) {
+  using F = Field<N>;
+  constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD, NT = F::NT;
+  constexpr size_t NN = (size_t)N * N;
+  using V1 = float2[N1];
+  using V2 = float2[N2];
+  extern __shared__ float2 sm[];
+  float2* A = sm;
+  float2* tw = A + N * LD;
+  float2* hy = tw + F::TW_ENTRIES;
+  float2* hx = hy + N;
+  __shared__ int h_task;
+  F::fill_twiddles(tw, a.tw);
+  for (int i = threadIdx.x; i < N; i += NT) {
+    hy[i] = a.hy[i];
+    hx[i] = a.hx[i];
+  }
+  const int M = a.M, L = a.L, cp = a.cp, ncp = a.ncp, B = a.B, Ly = a.Ly, Lx = a.Lx;
+  const int MB = M * B, ntask = (ncp - 1) * MB;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      int got = -1;
+      for (int tk = atomicAdd(a.hnext, 1); tk < ntask; tk = atomicAdd(a.hnext, 1)) {
+        const int s = tk / MB, m = (tk - s * MB) / B, bb = tk - s * MB - m * B;
+        if (min(s * cp + cp, L) - 1 <= s * cp) continue;   // one-slice segment: nothing to recompute
+        int* fl = a.hflag + ((size_t)bb * M + m) * ncp + s;
+        const int w = wait_checkpoints(a.hprog + (size_t)bb * M + m, s + 1, fl);
+        if (w < 0) break;
+        if (w > 0 && atomicCAS(fl, 0, 1) == 0) {
+          got = tk;
+          break;
+        }
+      }
+      h_task = got;
+    }
+    __syncthreads();   // also orders the table fill and the last task's stores
+    const int tk = h_task;
+    __syncthreads();
+    if (tk < 0) return;
+    const int s = tk / MB, m = (tk - s * MB) / B, b = tk - s * MB - m * B;
+    const int p0y = FAR ? patch_corner(a.pos[2 * b]) : 0, p0x = FAR ? patch_corner(a.pos[2 * b + 1]) : 0;
+    const bool interior = p0y >= 0 && p0x >= 0 && p0y <= Ly - N && p0x <= Lx - N;
+    auto tloads = [&](V1& pa, int j, int x, int t) {
+      const size_t gz = FAR ? j : (size_t)b * L + j;
+      if (interior) {
+        const float2* p = a.T + (gz * Ly + (p0y + t)) * Lx + (p0x + x);
+#pragma unroll
+        for (int k = 0; k < N1; ++k) pa[k] = __ldg(p + (size_t)(N2 * k) * Lx);
+      } else {
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+          const int gy = p0y + N2 * k + t, gx = p0x + x;
+          pa[k] = (gy >= 0 && gy < Ly && gx >= 0 && gx < Lx) ? __ldg(a.T + (gz * Ly + gy) * Lx + gx)
+                                                             : make_float2(1.f, 0.f);
+        }
+      }
+    };
+    const size_t bm = (size_t)b * M + m;
+    const float2* ck = a.ckpt + (bm * ncp + s) * NN;
+    float2* sg = a.hseg + (bm * (ncp - 1) + s) * cp * NN;
+    const int j0 = s * cp, j1 = min(j0 + cp, L) - 1;
+    for (int j = j0; j < j1; ++j) {
+      if (j == j0) {
+        pass_c14<N, 0, -1, false, true>(A, tw, [&](V1& pa, V1& pb, int x, int t) {
+          tloads(pa, j, x, t);
+#pragma unroll
+          for (int k = 0; k < N1; ++k) pb[k] = __ldcg(ck + (N2 * k + t) * N + x);
+        }, [&](V1& v, V1& pa, V1& pb, int, int) {
+#pragma unroll
+          for (int k = 0; k < N1; ++k) v[k] = cmul(pb[k], pa[k]);
+        });
+      } else {
+        pass_c14<N, +1, -1, true, true>(A, tw, [&](V1& pa, V1&, int x, int t) { tloads(pa, j, x, t); },
+                                        [&](V1& v, V1& pa, V1&, int x, int t) {
+#pragma unroll
+          for (int k = 0; k < N1; ++k) {
+            sg[(size_t)(j - j0) * NN + (N2 * k + t) * N + x] = v[k];
+            v[k] = cmul(v[k], pa[k]);
+          }
+        });
+      }
+      __syncthreads();
+      // propagation tail: C2, R1, R23 (H), R4, C3
+      pass_c23<N, false, -1>(A, tw);
+      __syncthreads();
+      pass_r14<N, true, -1>(A, tw);
+      __syncthreads();
+      pass_r23<N, -1, +1>(A, tw, [&](V2& v, int ky, int t) {
+        const float2 h = hy[ky];
+#pragma unroll
+        for (int i = 0; i < N2; ++i) v[i] = cmul(cmul(v[i], h), hx[t + N1 * i]);
+      });
+      __syncthreads();
+      pass_r14<N, false, +1>(A, tw);
+      __syncthreads();
+      pass_c23<N, true, +1>(A, tw);
+      __syncthreads();
+    }
+    pass_c14<N, +1, 0, true, false>(A, tw, NoPre(), [&](V1& v, V1&, V1&, int x, int t) {
+#pragma unroll
+      for (int k = 0; k < N1; ++k) sg[(size_t)(j1 - j0) * NN + (N2 * k + t) * N + x] = v[k];
+    });
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release_gpu(a.hflag + bm * ncp + s, 2);
+    }
+  }
+}
 
 template <int N, int FAR, bool GAP>
 __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArgs a) {
+  if constexpr (!GAP) {
+    if ((int)blockIdx.x >= a.B) {
+      helper_body<N, FAR>(a);
+      return;
+    }
+  }
   path_body<N, FAR, GAP, false>(a);
 }
 
@@ -649,7 +840,8 @@ constexpr int path_smem_bytes_t() {
 
 template <int N, int FAR, bool GAP>
 cudaError_t launch_path_t(const PathArgs& a, cudaStream_t s) {
-  (k_path<N, FAR, GAP><<<a.B, Geo<N>::NT, path_smem_bytes_t<N>(), s>>>(a), note_launch());
+  // positions, then the recompute helpers (none with slice gaps)
+  (k_path<N, FAR, GAP><<<a.B + (GAP ? 0 : a.helpers), Geo<N>::NT, path_smem_bytes_t<N>(), s>>>(a), note_launch());
   return cudaGetLastError();
 }
 

@@ -37,8 +37,9 @@ __device__ __forceinline__ Tap tap(int zt, int xt, int Lz, int Lx, float c, floa
 // full_x the column range is the whole width (tomography: the rotation transpose mixes x and z).
 __global__ void __launch_bounds__(256) k_bbox(const float* __restrict__ pos, int B, int N, int Ly, int Lx, int far,
                                               int full_x, int* __restrict__ box, int npos_values,
-                                              int* __restrict__ status) {
+                                              int* __restrict__ status, int* __restrict__ zero, int nzero) {
   __shared__ int red[4][8];
+  for (int i = threadIdx.x; i < nzero; i += 256) zero[i] = 0;
   // input check: every position / shift value finite and within +-2^24 px
   bool bad = false;
   for (int i = threadIdx.x; i < npos_values; i += 256) {
@@ -207,8 +208,8 @@ __global__ void k_grad_add(const double* __restrict__ ad, const double* __restri
 static unsigned vol_grid(size_t n) { return (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16); }
 
 cudaError_t launch_bbox(const float* pos, int B, int N, int Ly, int Lx, int far, int full_x, int* box,
-                        int npos_values, int* status, cudaStream_t s) {
-  (k_bbox<<<1, 256, 0, s>>>(pos, B, N, Ly, Lx, far, full_x, box, npos_values, status), note_launch());
+                        int npos_values, int* status, cudaStream_t s, int* zero, int nzero) {
+  (k_bbox<<<1, 256, 0, s>>>(pos, B, N, Ly, Lx, far, full_x, box, npos_values, status, zero, nzero), note_launch());
   return cudaGetLastError();
 }
 

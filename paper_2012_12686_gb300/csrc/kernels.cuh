@@ -65,6 +65,14 @@ struct PathArgs {
   // sparse / variable multislice: per-gap propagator factors [L-1][N] (null: uniform hy, hx)
   const float2* hyj;
   const float2* hxj;
+  // recompute helpers (uniform spacing, one CTA per position, batch below the SM count): CTAs
+  // blockIdx.x >= B recompute segments 0..ncp-2 into hseg while the positions run; the control
+  // words are zeroed by the bounding-box kernel before each launch
+  int helpers;            // helper CTAs (grid B + helpers); 0: none
+  float2* hseg;           // [B][M][ncp-1][cp][N*N] helper-recomputed psi_j (slice 0 of a segment unused)
+  int* hnext;             // next helper task (segment-major: s, then m, then b)
+  int* hprog;             // [B][M] checkpoints the forward has written so far (release / acquire)
+  int* hflag;             // [B][M][ncp] 0 free, 1 helper recomputing, 2 helper done, 3 taken by the position
   float2* spck;           // gap gradient: spectra F[psi_j] / N^2 of checkpoint slices [B][M][ncp][N*N]
   float2* spseg;          //               and of segment slices [B][M][cp][N*N]
   double* gapp;           // [B][L-1] per-position slice-gap gradient partials, or null
@@ -143,8 +151,9 @@ cudaError_t launch_probe_grad(int N, int M, int B, int farfield, const float2* q
 constexpr int STATUS_BAD_POSITION = 1;   // a position / shift is not finite or beyond +-2^24 px
 constexpr int STATUS_WAIT_TIMEOUT = 2;   // a bounded device-side wait (TMA completion) gave up
 // npos_values: 2 B (far field) or 2 B n_dist (near-field shifts) floats checked into *status
+// also zeroes nzero ints at zero (the fused kernel's helper control words), when given
 cudaError_t launch_bbox(const float* pos, int B, int N, int Ly, int Lx, int far, int full_x, int* box,
-                        int npos_values, int* status, cudaStream_t s);
+                        int npos_values, int* status, cudaStream_t s, int* zero = nullptr, int nzero = 0);
 // T = exp(-kdz beta) exp(i kdz delta) over the box (Eq. ri_modulation), optionally after the
 // bilinear rotation of Eq. rotation_transform (rotate = 1); zero_a / zero_b (FP64 object-gradient
 // accumulators over the same box) are zeroed in the same pass when non-null
