@@ -148,6 +148,10 @@ int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan
   return ADORYM_OK;
 }
 
+#ifndef ADORYM_SIDE_STREAM
+#define ADORYM_SIDE_STREAM 1
+#endif
+
 #ifndef ADORYM_HELPERS
 #define ADORYM_HELPERS 1
 #endif
@@ -274,7 +278,17 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
   float2* T = reinterpret_cast<float2*>(W(pl.off_T));
   int* box = reinterpret_cast<int*>(W(pl.off_box));
   int* status = c.status ? c.status : reinterpret_cast<int*>(W(pl.off_status));
+  bool join_side = false;   // the call's stream waits for the side stream's last kernels
   if (!c.status && (rc = chk(cudaMemsetAsync(status, 0, sizeof(int), s), "status"))) return rc;
+  float2* phat = reinterpret_cast<float2*>(W(pl.off_phat));
+  // the probe transform needs only the probe: on the side stream it overlaps the passes below
+  const bool side = c.side && !two_pass(p.N);
+  if (side && pl.far) {
+    if ((rc = chk(cudaEventRecord(c.ev_side[0], s), "fork"))) return rc;
+    if ((rc = chk(cudaStreamWaitEvent(c.side, c.ev_side[0], 0), "fork"))) return rc;
+    if ((rc = chk(launch_probe_hat(p.N, p.M, c.probe, phat, tab.tw(), c.side), "probe_hat"))) return rc;
+    if ((rc = chk(cudaEventRecord(c.ev_side[1], c.side), "join"))) return rc;
+  }
   int* hctl = pl.helpers ? reinterpret_cast<int*>(W(pl.off_hctl)) : nullptr;
   if ((rc = chk(launch_bbox(c.pos, p.B, p.N, p.Ly, p.Lx, pl.far ? 1 : 0, pl.tomo ? 1 : 0, box, 2 * p.B * pl.nd, status,
                             s, hctl, (int)helper_ctl_ints(pl)),
@@ -293,7 +307,6 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
                                     (float)sth, box, gd, gb, s),
                 "transmission")))
     return rc;
-  float2* phat = reinterpret_cast<float2*>(W(pl.off_phat));
   // the main kernels read the measured intensities: wait for their copy (the pre-kernels above and
   // the probe transform do not)
   auto wait_meas = [&]() -> int {
@@ -362,7 +375,9 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
     if ((rc = chk(launch_twopass(t, s, ev_start, ev_stop), "two-pass"))) return rc;
   } else {
     if (pl.far) {
-      if ((rc = chk(launch_probe_hat(p.N, p.M, c.probe, phat, tab.tw(), s), "probe_hat"))) return rc;
+      rc = side ? chk(cudaStreamWaitEvent(s, c.ev_side[1], 0), "join")
+                : chk(launch_probe_hat(p.N, p.M, c.probe, phat, tab.tw(), s), "probe_hat");
+      if (rc) return rc;
     }
     PathArgs a{};
     a.N = p.N;
@@ -429,10 +444,20 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
       if ((rc = chk(launch_gap_final(a.gapp, p.B, p.L - 1, 1, c.g_gaps, s), "gap_final"))) return rc;
     }
     if (pl.adj && (pl.want_probe || c.loss)) {
+      // the probe-gradient kernels (one CTA per mode) run beside the object-gradient pass
+      cudaStream_t sp = side ? c.side : s;
+      if (side) {
+        if ((rc = chk(cudaEventRecord(c.ev_side[2], s), "fork"))) return rc;
+        if ((rc = chk(cudaStreamWaitEvent(c.side, c.ev_side[2], 0), "fork"))) return rc;
+      }
       if ((rc = chk(launch_probe_grad(p.N, p.M, p.B, pl.far ? 1 : 0, a.qacc, reinterpret_cast<float2*>(W(pl.off_qsum)),
-                                      pl.want_probe ? c.g_probe : nullptr, tab.tw(), a.lossp, a.inv_npix, c.loss, s),
+                                      pl.want_probe ? c.g_probe : nullptr, tab.tw(), a.lossp, a.inv_npix, c.loss, sp),
                     "probe_grad")))
         return rc;
+      if (side) {
+        if ((rc = chk(cudaEventRecord(c.ev_side[3], c.side), "join"))) return rc;
+        join_side = true;
+      }
     }
   }
   if (pl.want_obj && !direct) {
@@ -442,6 +467,7 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
       rc = chk(launch_grad_add(gd, gb, c.gd, c.gb, p.Lz, p.Ly, p.Lx, box, s), "grad_add");
     if (rc) return rc;
   }
+  if (join_side && (rc = chk(cudaStreamWaitEvent(s, c.ev_side[3], 0), "join"))) return rc;
   return ADORYM_OK;
 }
 
@@ -541,6 +567,12 @@ void adorym_destroy(adorym_ctx* ctx) {
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->status_host) cudaFreeHost(ctx->status_host);
   if (ctx->ev_meas) cudaEventDestroy(ctx->ev_meas);
+  if (ctx->side_stream) {
+    cudaStreamSynchronize(ctx->side_stream);
+    cudaStreamDestroy(ctx->side_stream);
+  }
+  for (cudaEvent_t e : ctx->ev_side)
+    if (e) cudaEventDestroy(e);
   delete ctx;
 }
 
@@ -688,6 +720,15 @@ static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const 
   if (ctx->timing && !ctx->ev0) {
     cudaEventCreate(&ctx->ev0);
     cudaEventCreate(&ctx->ev1);
+  }
+  if (ADORYM_SIDE_STREAM && !two_pass(p->N)) {
+    if (!ctx->side_stream) {
+      bool ok = cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking) == cudaSuccess;
+      for (cudaEvent_t& e : ctx->ev_side) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+      if (!ok) return cuda_fail(ctx, cudaGetLastError(), "side stream");
+    }
+    c.side = ctx->side_stream;
+    for (int i = 0; i < 4; ++i) c.ev_side[i] = ctx->ev_side[i];
   }
   if ((rc = enqueue(pl, obj, tab, c, ws, s, &err, ctx->timing ? ctx->ev0 : nullptr, ctx->timing ? ctx->ev1 : nullptr)))
     return fail(ctx, rc, err);

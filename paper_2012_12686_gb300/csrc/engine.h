@@ -64,6 +64,12 @@ struct CallPtrs {
   // the measured intensities arrive on a side stream: the stream waits for this event before the
   // main kernels (the pre-kernels overlap the copy); null when there is nothing to wait for
   cudaEvent_t meas_ready = nullptr;
+  // shared-memory path: a second stream for the single-CTA probe kernels, forked from the call's
+  // stream and joined back with ev_side = {fork 1, join 1, fork 2, join 2}: the probe transform
+  // runs beside the bounding-box and transmission passes, the probe-gradient reduction and
+  // transform beside the object-gradient pass.  Null: everything on the call's stream.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_side[4] = {nullptr, nullptr, nullptr, nullptr};
   // device-visible status word to use instead of the plan's (not cleared by the call: the owner
   // zeroes it before the work runs); null: the workspace word, cleared on the stream
   int* status = nullptr;
@@ -115,6 +121,8 @@ struct adorym_ctx {
   cudaStream_t copy_stream = nullptr;          // host-to-device copy of measured intensities
   cudaEvent_t ev_fork = nullptr, ev_meas = nullptr;
   int* status_host = nullptr;                  // pinned copy of the last call's status word
+  cudaStream_t side_stream = nullptr;          // single-CTA probe kernels (CallPtrs::side)
+  cudaEvent_t ev_side[4] = {nullptr, nullptr, nullptr, nullptr};
   int inject_alloc_failures = 0;               // adorym_inject_alloc_failures: pending count
   bool timed = false;
   adorym::Serve* serve = nullptr;    // owned; created by the first submit or serve_config
