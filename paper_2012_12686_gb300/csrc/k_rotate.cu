@@ -166,8 +166,13 @@ __global__ void k_rotate_adj(const double* __restrict__ gdr, const double* __res
     // rotated-frame point that maps exactly onto this node (inverse rotation)
     const float u = (float)x - cx, w = (float)z - cz;
     const float xs = c * u + s * w + cx, zs = -s * u + c * w + cz;
-    const int xa = max(0, (int)floorf(xs - 1.5f)), xb = min(Lx - 1, (int)ceilf(xs + 1.5f));
-    const int za = max(0, (int)floorf(zs - 1.5f)), zb = min(Lz - 1, (int)ceilf(zs + 1.5f));
+    // a contributing voxel samples within one pixel of the node in x and z, so (inverse rotation)
+    // it lies within |c| + |s| <= sqrt(2) of (xs, zs) along each axis: at most 3 x 3 candidates
+    // (the margin covers FP32 rounding of xs, zs and of the forward taps); the membership test
+    // below is the forward pass's own
+    const float r = fabsf(c) + fabsf(s) + 0.01f;
+    const int xa = max(0, (int)ceilf(xs - r)), xb = min(Lx - 1, (int)floorf(xs + r));
+    const int za = max(0, (int)ceilf(zs - r)), zb = min(Lz - 1, (int)floorf(zs + r));
     // the taps are FP64 sums over positions; each is narrowed once (integer arithmetic, round to
     // nearest) and the <= 4 weighted taps are added in FP32, like the caller's FP32 gradient
     float ad = 0.f, ab = 0.f;

@@ -49,8 +49,11 @@ def test_farfield_parity(N, L, M, B, loss, cp):
     _compare(case)
 
 
-def test_tomography_parity():
-    case = C.small_case(N=16, L=17, M=1, B=4, loss="lsq", tomo=True, theta=0.7, Ly=20, Lx=17, seed=5)
+# tilt angles: generic, exactly 45 degrees (the widest candidate window of the rotation's
+# transpose, |cos| + |sin| = sqrt 2), no rotation, near 90 degrees, obtuse
+@pytest.mark.parametrize("theta", [0.7, 0.7853981633974483, 0.0, 1.52, 2.5])
+def test_tomography_parity(theta):
+    case = C.small_case(N=16, L=17, M=1, B=4, loss="lsq", tomo=True, theta=theta, Ly=20, Lx=17, seed=5)
     _compare(case)
 
 
