@@ -437,8 +437,14 @@ def run_ours(args, rank, world, local_rank):
     k_ms = statistics.mean(path_ms)
     if far and N <= 128:
         achieved = units * flops_per_unit(N) / (k_ms * 1e-3) / 1e12
+        # the library's launch form for this batch: two-CTA clusters up to half the SM count,
+        # recompute helpers on the idle SMs below the SM count (checkpointed sweeps), else plain
+        sms = props.multi_processor_count
+        ncp_ = -(-L // cp)
+        form = ("k_path_pipe" if 2 * B <= sms and ncp_ > 1 and cp > 1 else
+                "k_path_help" if B < sms and ncp_ > 1 and cp > 1 else "k_path")
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_derived, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak_derived, "kernel": f"k_path<{N},far>"}
+                "frac": achieved / fp32_peak_derived, "kernel": f"{form}<{N},far>"}
         try:   # the same fraction against an FFMA throughput kernel measured now, on this GPU
             measured = fp32_peak(local_rank)
             roof.update(peak_measured_ffma=measured, frac_of_measured_ffma=achieved / measured)

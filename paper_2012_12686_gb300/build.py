@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libadorym.so")
-SOURCES = ["k_path.cu", "k_path_gaps.cu", "k_path_pipe.cu", "k_twopass.cu", "k_rotate.cu", "k_reg.cu", "api.cu", "serve.cu", "noalloc.cu", "k_peak.cu"]
+SOURCES = ["k_path.cu", "k_path_gaps.cu", "k_path_pipe.cu", "k_path_help.cu", "k_twopass.cu", "k_rotate.cu", "k_reg.cu", "api.cu", "serve.cu", "noalloc.cu", "k_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-I", os.path.join(ROOT, "include")]

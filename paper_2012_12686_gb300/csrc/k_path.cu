@@ -147,6 +147,7 @@ int path_smem_bytes(int N) {
 cudaError_t launch_path(const PathArgs& a, int farfield, cudaStream_t s) {
   if (a.hyj) return launch_path_gaps(a, farfield, s);   // variable slice spacing
   if (a.pipe) return launch_path_pipe(a, farfield, s);
+  if (a.helpers) return launch_path_help(a, farfield, s);
   switch (a.N) {
 #define ADORYM_CASE(n)                                                                      \
   case n:                                                                                   \
@@ -216,6 +217,7 @@ static cudaError_t prepare_t() {
   cudaError_t e = prepare_path_t<N, FAR, false>();
   if (e == cudaSuccess) e = prepare_path_gaps(N, FAR);
   if (e == cudaSuccess) e = prepare_path_pipe(N, FAR);
+  if (e == cudaSuccess) e = prepare_path_help(N, FAR);
   const int small = (N * (N + 1) + Field<N>::TW_ENTRIES) * (int)sizeof(float2);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_probe_hat<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, small);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_probe_grad<N, FAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, small);

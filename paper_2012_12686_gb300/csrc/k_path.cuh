@@ -115,8 +115,11 @@ __device__ __forceinline__ int wait_checkpoints(const int* prog, int need, const
 
 // GAP: per-gap propagators (variable slice spacing) and the slice-gap gradient; the uniform-spacing
 // instantiation carries none of that code.  PIPE: the two-CTA cluster form described above.
-template <int N, int FAR, bool GAP, bool PIPE>
+// HELP: the position side of the recompute-helper protocol (a separate instantiation, so that
+// calls without helpers run code with the register allocation of the plain form).
+template <int N, int FAR, bool GAP, bool PIPE, bool HELP = false>
 __device__ __forceinline__ void path_body(const PathArgs& a) {
+  static_assert(!(HELP && (GAP || PIPE)), "recompute helpers serve the plain one-CTA form only");
   using F = Field<N>;
   constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD, NT = F::NT;
   constexpr size_t NN = (size_t)N * N;
@@ -323,7 +326,7 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
         pass_c14<N, +1, -1, true, true>(A, tw, pre_T(j), fwd_op(j, false));
       }
       __syncthreads();
-      if constexpr (!PIPE && !GAP) {
+      if constexpr (HELP) {
         // checkpoint j / cp is written: helpers may recompute segment j / cp from now on
         if (a.helpers && adj && j % cp == 0 && threadIdx.x == 0) {
           __threadfence();
@@ -582,7 +585,7 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
       bool from_helper = false;   // psi_{j0+1..j1} in a helper's store instead of the own slot
       if (!PIPE && s != ncp - 1 && j1 > j0) {
         bool own = true;
-        if constexpr (!GAP) {
+        if constexpr (HELP) {
           if (a.helpers) {
             bool done = false;
             if (threadIdx.x == 0) done = take_segment(a.hflag + ((size_t)b * M + m) * ncp + s);
@@ -699,7 +702,7 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
   }
 }
 
-// A recompute helper (CTA blockIdx.x >= B of k_path without slice gaps): claims segments
+// A recompute helper (CTA blockIdx.x >= B of k_path_help): claims segments
 // 0..ncp-2 of the positions in segment-major order and recomputes psi_{j0+1..j1} of each from its
 // checkpoint into the helper store, with the same passes and operation order as a position's own
 // recompute (so the result does not depend on which CTA recomputed a segment).  Kept apart from
@@ -817,13 +820,17 @@ __device__ __forceinline__ void helper_body(const PathArgs& a) {
 
 template <int N, int FAR, bool GAP>
 __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path(const PathArgs a) {
-  if constexpr (!GAP) {
-    if ((int)blockIdx.x >= a.B) {
-      helper_body<N, FAR>(a);
-      return;
-    }
-  }
   path_body<N, FAR, GAP, false>(a);
+}
+
+// with recompute helpers: grid B + helpers, CTAs beyond the batch are helpers
+template <int N, int FAR>
+__global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_path_help(const PathArgs a) {
+  if ((int)blockIdx.x >= a.B) {
+    helper_body<N, FAR>(a);
+    return;
+  }
+  path_body<N, FAR, false, false, true>(a);
 }
 
 // the pipelined form: grid 2 B, clusters of two CTAs (rank 0 adjoint, rank 1 recompute)
@@ -840,8 +847,14 @@ constexpr int path_smem_bytes_t() {
 
 template <int N, int FAR, bool GAP>
 cudaError_t launch_path_t(const PathArgs& a, cudaStream_t s) {
-  // positions, then the recompute helpers (none with slice gaps)
-  (k_path<N, FAR, GAP><<<a.B + (GAP ? 0 : a.helpers), Geo<N>::NT, path_smem_bytes_t<N>(), s>>>(a), note_launch());
+  (k_path<N, FAR, GAP><<<a.B, Geo<N>::NT, path_smem_bytes_t<N>(), s>>>(a), note_launch());
+  return cudaGetLastError();
+}
+
+template <int N, int FAR>
+cudaError_t launch_path_help_t(const PathArgs& a, cudaStream_t s) {
+  // positions, then the recompute helpers
+  (k_path_help<N, FAR><<<a.B + a.helpers, Geo<N>::NT, path_smem_bytes_t<N>(), s>>>(a), note_launch());
   return cudaGetLastError();
 }
 
@@ -854,6 +867,11 @@ cudaError_t launch_path_pipe_t(const PathArgs& a, cudaStream_t s) {
 template <int N, int FAR, bool GAP>
 cudaError_t prepare_path_t() {
   return cudaFuncSetAttribute(k_path<N, FAR, GAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, path_smem_bytes_t<N>());
+}
+
+template <int N, int FAR>
+cudaError_t prepare_path_help_t() {
+  return cudaFuncSetAttribute(k_path_help<N, FAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, path_smem_bytes_t<N>());
 }
 
 template <int N, int FAR>

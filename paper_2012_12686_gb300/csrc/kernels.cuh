@@ -140,6 +140,9 @@ cudaError_t prepare_path_gaps(int N, int farfield);
 // the pipelined two-CTA-cluster instantiation (a.pipe != 0), in its own translation unit
 cudaError_t launch_path_pipe(const PathArgs& a, int farfield, cudaStream_t s);
 cudaError_t prepare_path_pipe(int N, int farfield);
+// the instantiation with recompute helpers (a.helpers > 0), in its own translation unit
+cudaError_t launch_path_help(const PathArgs& a, int farfield, cudaStream_t s);
+cudaError_t prepare_path_help(int N, int farfield);
 // g_gap[j] = sum_b gapp[b][j][k] over b and k < parts (fixed order)
 cudaError_t launch_gap_final(const double* gapp, int B, int ngap, int parts, float* g_gap, cudaStream_t s);
 cudaError_t launch_probe_grad(int N, int M, int B, int farfield, const float2* qacc, float2* qsum, float2* g_probe,
