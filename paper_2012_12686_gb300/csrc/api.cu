@@ -307,8 +307,9 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
                                     (float)sth, box, gd, gb, s),
                 "transmission")))
     return rc;
-  // the main kernels read the measured intensities: wait for their copy (the pre-kernels above and
-  // the probe transform do not)
+  // the fused kernel reads the measured intensities: wait for their copy before it (the pre-kernels
+  // above and the probe transform do not read them); the two-pass sequence waits inside, before
+  // its detector passes
   auto wait_meas = [&]() -> int {
     return c.meas_ready ? chk(cudaStreamWaitEvent(s, c.meas_ready, 0), "wait for intensities") : ADORYM_OK;
   };
@@ -371,8 +372,7 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
       t.g_probe = pl.want_probe ? c.g_probe : nullptr;
       t.loss_out = c.loss;
     }
-    if ((rc = wait_meas())) return rc;
-    if ((rc = chk(launch_twopass(t, s, ev_start, ev_stop), "two-pass"))) return rc;
+    if ((rc = chk(launch_twopass(t, s, ev_start, ev_stop, c.meas_ready), "two-pass"))) return rc;
   } else {
     if (pl.far) {
       rc = side ? chk(cudaStreamWaitEvent(s, c.ev_side[1], 0), "join")

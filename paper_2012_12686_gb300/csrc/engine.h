@@ -62,7 +62,8 @@ struct CallPtrs {
   float* I_out = nullptr;
   float* g_gaps = nullptr;
   // the measured intensities arrive on a side stream: the stream waits for this event before the
-  // main kernels (the pre-kernels overlap the copy); null when there is nothing to wait for
+  // first kernel that reads them (the kernels before it overlap the copy); null when there is
+  // nothing to wait for
   cudaEvent_t meas_ready = nullptr;
   // shared-memory path: a second stream for the single-CTA probe kernels, forked from the call's
   // stream and joined back with ev_side = {fork 1, join 1, fork 2, join 2}: the probe transform

@@ -942,7 +942,7 @@ static bool encode_tile_map(CUtensorMap* m, const void* base, unsigned long long
 }
 
 template <int N>
-static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, cudaEvent_t meas_ready) {
   const bool far = a.farfield != 0;
   const int B = a.B, M = a.M, L = a.L;
   const size_t NN = (size_t)N * N;
@@ -975,6 +975,15 @@ static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEven
   // one probe mode with measured data: loss and adjoint seed fused into the detector pass
   const bool fuse = a.adj && M == 1 && a.I_meas != nullptr;
   const int nloss = !fuse ? (int)(B * a.nd * (NN / LOSS_PX)) : far ? B * ncol : B * a.nd * (N / Geo2<N>::RB);
+  // the detector passes (and the separate loss pass) are the first readers of the measured
+  // intensities: wait for their copy there, not before the forward passes
+  cudaError_t werr = cudaSuccess;
+  auto wait_meas = [&]() {
+    if (!meas_ready) return;
+    const cudaError_t e = cudaStreamWaitEvent(s, meas_ready, 0);
+    if (e != cudaSuccess && werr == cudaSuccess) werr = e;
+    meas_ready = nullptr;
+  };
   if (ev0) cudaEventRecord(ev0, s);
   if (far) {
     row<N, R_PHAT>(a, M, s);
@@ -996,11 +1005,13 @@ static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEven
         col<N, C_PROP>(a, B, s);
         a.spec_out = nullptr;
       } else if (far) {
+        wait_meas();
         if (fuse && a.loss == 1) col<N, C_FAR_SEED_P>(a, B, s);
         else if (fuse) col<N, C_FAR_SEED>(a, B, s);
         else col<N, C_FAR>(a, B, s);
       } else {
         col<N, C_NEAR_PHI>(a, B, s);
+        wait_meas();
         for (int d = 0; d < a.nd; ++d) {
           a.d = d;
           if (fuse && a.loss == 1) row<N, R_NEAR_DSEED_P>(a, B, s);
@@ -1010,6 +1021,7 @@ static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEven
       }
     }
   }
+  wait_meas();   // (no-op when a detector pass already waited)
   if (!fuse) (k_loss2<<<dim3((unsigned)(NN / LOSS_PX), B * a.nd), 256, 0, s>>>(a), note_launch());
   if (a.adj) {
     // ---------------- adjoint
@@ -1079,14 +1091,15 @@ static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEven
       }
     }
   }
-  return cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
+  return e != cudaSuccess ? e : werr;
 }
 
-cudaError_t launch_twopass(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+cudaError_t launch_twopass(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, cudaEvent_t meas_ready) {
   switch (a.N) {
-    case 256: return twopass_t<256>(a, s, ev0, ev1);
-    case 512: return twopass_t<512>(a, s, ev0, ev1);
-    case 1024: return twopass_t<1024>(a, s, ev0, ev1);
+    case 256: return twopass_t<256>(a, s, ev0, ev1, meas_ready);
+    case 512: return twopass_t<512>(a, s, ev0, ev1, meas_ready);
+    case 1024: return twopass_t<1024>(a, s, ev0, ev1, meas_ready);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -181,7 +181,10 @@ cudaError_t launch_l1_weights(const float* c, size_t n, float eps, float* part, 
 cudaError_t launch_qsum(const float2* qacc, float2* qsum, int B, size_t MNN, cudaStream_t s);
 int path_smem_bytes(int N);
 // whole two-pass loss/gradient (adj = 1) or forward (adj = 0) sequence for N in {256, 512, 1024}
-cudaError_t launch_twopass(TPArgs a, cudaStream_t s, cudaEvent_t ev_start, cudaEvent_t ev_stop);
+// meas_ready (or null): event of the measured intensities' copy; the stream waits for it just
+// before the first kernel that reads them, so the copy overlaps the forward passes
+cudaError_t launch_twopass(TPArgs a, cudaStream_t s, cudaEvent_t ev_start, cudaEvent_t ev_stop,
+                           cudaEvent_t meas_ready = nullptr);
 cudaError_t prepare_twopass(int N);
 // set the dynamic shared-memory attributes of every kernel used for tile size N (call outside capture)
 cudaError_t prepare_path(int N, int farfield);
