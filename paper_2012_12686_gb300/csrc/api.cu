@@ -372,7 +372,8 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
       t.g_probe = pl.want_probe ? c.g_probe : nullptr;
       t.loss_out = c.loss;
     }
-    if ((rc = chk(launch_twopass(t, s, ev_start, ev_stop, c.meas_ready), "two-pass"))) return rc;
+    if ((rc = chk(launch_twopass(t, s, ev_start, ev_stop, c.meas_ready, c.meas_part, c.n_meas_part), "two-pass")))
+      return rc;
   } else {
     if (pl.far) {
       rc = side ? chk(cudaStreamWaitEvent(s, c.ev_side[1], 0), "join")
@@ -567,6 +568,8 @@ void adorym_destroy(adorym_ctx* ctx) {
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->status_host) cudaFreeHost(ctx->status_host);
   if (ctx->ev_meas) cudaEventDestroy(ctx->ev_meas);
+  for (cudaEvent_t e : ctx->ev_meas_d)
+    if (e) cudaEventDestroy(e);
   if (ctx->side_stream) {
     cudaStreamSynchronize(ctx->side_stream);
     cudaStreamDestroy(ctx->side_stream);
@@ -689,10 +692,29 @@ static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const 
     }
     cudaEventRecord(ctx->ev_fork, s);
     cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_fork, 0);
-    cudaMemcpyAsync(ws + pl.off_s_meas, I_meas, pl.bytes_meas, cudaMemcpyHostToDevice, ctx->copy_stream);
-    cudaEventRecord(ctx->ev_meas, ctx->copy_stream);
     c.I_meas = reinterpret_cast<const float*>(ws + pl.off_s_meas);
     c.meas_ready = ctx->ev_meas;
+    if (two_pass(p->N) && !pl.far && pl.nd > 1) {
+      // one strided copy per distance ([B] rows of N^2 values at a pitch of n_dist N^2), each
+      // with its own event: the detector pass of distance d starts once its rows have arrived
+      if (!ctx->ev_meas_d[0]) {
+        bool ok = true;
+        for (cudaEvent_t& e : ctx->ev_meas_d) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) return cuda_fail(ctx, cudaGetLastError(), "copy events");
+      }
+      const size_t row = pl.NN * sizeof(float), pitch = (size_t)pl.nd * row;
+      for (int d = 0; d < pl.nd; ++d) {
+        cudaMemcpy2DAsync(ws + pl.off_s_meas + d * row, pitch, reinterpret_cast<const char*>(I_meas) + d * row, pitch, row,
+                          (size_t)p->B, cudaMemcpyHostToDevice, ctx->copy_stream);
+        cudaEventRecord(ctx->ev_meas_d[d], ctx->copy_stream);
+      }
+      c.meas_ready = ctx->ev_meas_d[pl.nd - 1];   // the copy stream is in order: the last part
+      c.meas_part = ctx->ev_meas_d;
+      c.n_meas_part = pl.nd;
+    } else {
+      cudaMemcpyAsync(ws + pl.off_s_meas, I_meas, pl.bytes_meas, cudaMemcpyHostToDevice, ctx->copy_stream);
+      cudaEventRecord(ctx->ev_meas, ctx->copy_stream);
+    }
   } else if (I_meas) {
     c.I_meas = I_meas;
   }

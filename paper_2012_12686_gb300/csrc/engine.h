@@ -65,6 +65,11 @@ struct CallPtrs {
   // first kernel that reads them (the kernels before it overlap the copy); null when there is
   // nothing to wait for
   cudaEvent_t meas_ready = nullptr;
+  // near field, two-pass path: the intensities of distance d arrive separately (meas_part[d],
+  // n_meas_part = n_dist; meas_ready is then the last part), so each detector pass waits only
+  // for its own distance
+  const cudaEvent_t* meas_part = nullptr;
+  int n_meas_part = 0;
   // shared-memory path: a second stream for the single-CTA probe kernels, forked from the call's
   // stream and joined back with ev_side = {fork 1, join 1, fork 2, join 2}: the probe transform
   // runs beside the bounding-box and transmission passes, the probe-gradient reduction and
@@ -121,6 +126,7 @@ struct adorym_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // fused-kernel timing pair
   cudaStream_t copy_stream = nullptr;          // host-to-device copy of measured intensities
   cudaEvent_t ev_fork = nullptr, ev_meas = nullptr;
+  cudaEvent_t ev_meas_d[4] = {nullptr, nullptr, nullptr, nullptr};   // per-distance intensity copies
   int* status_host = nullptr;                  // pinned copy of the last call's status word
   cudaStream_t side_stream = nullptr;          // single-CTA probe kernels (CallPtrs::side)
   cudaEvent_t ev_side[4] = {nullptr, nullptr, nullptr, nullptr};

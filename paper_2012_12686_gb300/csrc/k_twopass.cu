@@ -942,7 +942,8 @@ static bool encode_tile_map(CUtensorMap* m, const void* base, unsigned long long
 }
 
 template <int N>
-static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, cudaEvent_t meas_ready) {
+static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, cudaEvent_t meas_ready,
+                             const cudaEvent_t* meas_part, int n_meas_part) {
   const bool far = a.farfield != 0;
   const int B = a.B, M = a.M, L = a.L;
   const size_t NN = (size_t)N * N;
@@ -1011,9 +1012,14 @@ static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEven
         else col<N, C_FAR>(a, B, s);
       } else {
         col<N, C_NEAR_PHI>(a, B, s);
-        wait_meas();
+        const bool parts = meas_ready && meas_part && n_meas_part == a.nd;
+        if (!parts) wait_meas();
         for (int d = 0; d < a.nd; ++d) {
           a.d = d;
+          if (parts) {   // this distance's intensities only; the later ones are still arriving
+            const cudaError_t e = cudaStreamWaitEvent(s, meas_part[d], 0);
+            if (e != cudaSuccess && werr == cudaSuccess) werr = e;
+          }
           if (fuse && a.loss == 1) row<N, R_NEAR_DSEED_P>(a, B, s);
           else if (fuse) row<N, R_NEAR_DSEED>(a, B, s);
           else row<N, R_NEAR_DET>(a, B, s);
@@ -1095,11 +1101,12 @@ static cudaError_t twopass_t(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEven
   return e != cudaSuccess ? e : werr;
 }
 
-cudaError_t launch_twopass(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, cudaEvent_t meas_ready) {
+cudaError_t launch_twopass(TPArgs a, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, cudaEvent_t meas_ready,
+                           const cudaEvent_t* meas_part, int n_meas_part) {
   switch (a.N) {
-    case 256: return twopass_t<256>(a, s, ev0, ev1, meas_ready);
-    case 512: return twopass_t<512>(a, s, ev0, ev1, meas_ready);
-    case 1024: return twopass_t<1024>(a, s, ev0, ev1, meas_ready);
+    case 256: return twopass_t<256>(a, s, ev0, ev1, meas_ready, meas_part, n_meas_part);
+    case 512: return twopass_t<512>(a, s, ev0, ev1, meas_ready, meas_part, n_meas_part);
+    case 1024: return twopass_t<1024>(a, s, ev0, ev1, meas_ready, meas_part, n_meas_part);
     default: return cudaErrorInvalidValue;
   }
 }

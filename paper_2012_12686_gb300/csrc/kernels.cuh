@@ -182,9 +182,12 @@ cudaError_t launch_qsum(const float2* qacc, float2* qsum, int B, size_t MNN, cud
 int path_smem_bytes(int N);
 // whole two-pass loss/gradient (adj = 1) or forward (adj = 0) sequence for N in {256, 512, 1024}
 // meas_ready (or null): event of the measured intensities' copy; the stream waits for it just
-// before the first kernel that reads them, so the copy overlaps the forward passes
+// before the first kernel that reads them, so the copy overlaps the forward passes.  Near field
+// with n_meas_part = n_dist: meas_part[d] marks distance d's intensities, and each detector pass
+// waits only for its own distance
 cudaError_t launch_twopass(TPArgs a, cudaStream_t s, cudaEvent_t ev_start, cudaEvent_t ev_stop,
-                           cudaEvent_t meas_ready = nullptr);
+                           cudaEvent_t meas_ready = nullptr, const cudaEvent_t* meas_part = nullptr,
+                           int n_meas_part = 0);
 cudaError_t prepare_twopass(int N);
 // set the dynamic shared-memory attributes of every kernel used for tile size N (call outside capture)
 cudaError_t prepare_path(int N, int farfield);
