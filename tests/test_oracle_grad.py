@@ -34,7 +34,7 @@ def test_dot_products_of_linear_stages():
         gv = np.zeros_like(vol); model.put_chunk_T(gv, p0, ch)
         assert abs(np.sum(ch * model.take_chunk(vol, p0, N)) - np.sum(gv * vol)) < 1e-10
     v3, w3 = g.standard_normal((10, 3, 11)), g.standard_normal((10, 3, 11))
-    for th in (0.3, 1.2, 2.9):
+    for th in (0.3, 1.2, 2.9, np.pi / 4, 3 * np.pi / 4, -0.5):   # incl. the diagonal tilts
         assert abs(np.sum(w3 * model.rotate(v3, th)) - np.sum(model.rotate_T(w3, th) * v3)) < 1e-10
 
 
