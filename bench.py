@@ -50,6 +50,19 @@ def bytes_per_unit(N: int, L: int, cp: int) -> float:
     return 8 * N * N + 16 * N * N + 16 * N * N / cp
 
 
+def launch_form(B: int, L: int, cp: int, sms: int) -> str:
+    """Fused-kernel form the library launches for a direct loss_grad call with uniform slice
+    spacing (N <= 128): two-CTA clusters for batches of at most half the SM count, recompute
+    helpers on the idle SMs for batches below the SM count, else one CTA per position; the two
+    recompute forms only when the sweep has more than one checkpoint segment of several slices."""
+    ncp = -(-L // cp)
+    if ncp > 1 and cp > 1 and 2 * B <= sms:
+        return "k_path_pipe"
+    if ncp > 1 and cp > 1 and B < sms:
+        return "k_path_help"
+    return "k_path"
+
+
 def twopass_bytes_per_unit(N: int, L: int, cp: int, nd: int, far: bool) -> float:
     """Algorithmic HBM bytes per unit of the two-pass structure: every 2-D transform of an N x N
     complex64 field in HBM needs two read+write passes (32 N^2 bytes).  Far field per (position,
@@ -437,12 +450,7 @@ def run_ours(args, rank, world, local_rank):
     k_ms = statistics.mean(path_ms)
     if far and N <= 128:
         achieved = units * flops_per_unit(N) / (k_ms * 1e-3) / 1e12
-        # the library's launch form for this batch: two-CTA clusters up to half the SM count,
-        # recompute helpers on the idle SMs below the SM count (checkpointed sweeps), else plain
-        sms = props.multi_processor_count
-        ncp_ = -(-L // cp)
-        form = ("k_path_pipe" if 2 * B <= sms and ncp_ > 1 and cp > 1 else
-                "k_path_help" if B < sms and ncp_ > 1 and cp > 1 else "k_path")
+        form = launch_form(B, L, cp, props.multi_processor_count)
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_derived, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak_derived, "kernel": f"{form}<{N},far>"}
         try:   # the same fraction against an FFMA throughput kernel measured now, on this GPU
@@ -456,7 +464,8 @@ def run_ours(args, rank, world, local_rank):
         achieved = units * bpu / (k_ms * 1e-3) / 1e9
         hpk = peaks.get("hbm_gbs", 6795.5)
         roof = {"bound": "hbm", "achieved": achieved, "peak": hpk, "unit": "GB/s", "frac": achieved / hpk,
-                "kernel": "k_row/k_col two-pass sequence" if N >= 256 else f"k_path<{N},near>",
+                "kernel": ("k_row/k_col two-pass sequence" if N >= 256
+                           else f"{launch_form(B, L, cp, props.multi_processor_count)}<{N},near>"),
                 "bytes_per_unit": bpu}
     hbm_ach = units * bytes_per_unit(N, L, cp) / (k_ms * 1e-3) / 1e9
     src = kernel_source_bytes()
