@@ -62,4 +62,8 @@ def test_workspace_planning_and_validation(lib):
 def test_null_context_is_rejected(lib):
     assert lib.adorym_forward(None, None, 0, None, None, None) != 0
     assert lib.adorym_poll(None, 1, 0) != 0
+    from paper_2012_12686_gb300.adorym import EINVAL
+    assert lib.adorym_cancel(None, 1) == EINVAL
+    assert lib.adorym_inject_alloc_failures(None, 1) == EINVAL
+    assert lib.adorym_check(None) == EINVAL
     assert lib.adorym_last_error(None) == b"null context"
