@@ -214,3 +214,36 @@ def test_nearfield_integer_shift_rolls_hologram():
     pb2 = model.Problem.of(dict(pb.__dict__, nf=[1e9]))
     I2 = model.forward(pb2, delta, beta, probe, np.zeros((1, 1, 2)))
     np.testing.assert_allclose(I2[0, 0], np.exp(-2 * 10.0 * beta[0]), rtol=1e-8)
+
+
+def _golden_kv(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if "=" in line:
+                k, v = (t.strip() for t in line.split("=", 1))
+                out[k] = v
+    return out
+
+
+def test_delta_phase_sign_by_far_field_peak():
+    """A delta ramp with k dz delta = 2 pi a x / N deflects the whole beam into far-field bin
+    (0, -a mod N) (tests/golden/phase_ramp_farfield.txt, worked by hand from Eq. ri_modulation and
+    Eq. fraunhofer).  Exercises transmission() through the full forward model; flipping the sign of
+    its delta phase moves the peak to (0, a)."""
+    g = _golden_kv("phase_ramp_farfield.txt")
+    N, a = int(g["N"]), int(g["a"])
+    kdz = 253.354
+    x = np.arange(N, dtype=np.float64)
+    delta = np.broadcast_to(2 * math.pi * a * x / (N * kdz), (1, N, N)).copy()
+    beta = np.zeros((1, N, N))
+    p = dict(N=N, L=1, M=1, B=1, Lz=1, Ly=N, Lx=N, kdz=kdz, lambda_dz_over_px2=0.3, farfield=1, nf=[],
+             loss="lsq", eps=1e-6)
+    I = model.forward(p, delta, beta, np.ones((1, N, N), np.complex128), np.zeros((1, 2)))[0]
+    ky, kx = np.unravel_index(np.argmax(I), I.shape)
+    assert (ky, kx) == (int(g["peak_ky"]), int(g["peak_kx"]))
+    assert abs(I[ky, kx] - float(g["peak_I"])) < 1e-9
+    rest = I.copy()
+    rest[ky, kx] = 0.0
+    assert np.max(rest) < 1e-18
