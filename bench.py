@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -87,14 +88,14 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="adorym_clocks_", suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={SMI_FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -111,6 +112,10 @@ class ClockSampler:
 
     def summary(self):
         if self.proc is None:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         rows = []
         try:
@@ -142,6 +147,56 @@ def _oracle_one(args):
     return time.perf_counter() - t
 
 
+def _oracle_one_kept(args):
+    """The oracle's outputs for one task: (0, (intensities, (loss, gd, gb, gp, gpos)))."""
+    import oracle
+    problem, d, b, probe, pos, Im = args
+    r = oracle.loss_grad(problem, d, b, probe, pos, Im)
+    return 0.0, (oracle.forward(problem, d, b, probe, pos), r)
+
+
+def _oracle_fwd(args):
+    import oracle
+    problem, d, b, probe, pos = args
+    return oracle.forward(problem, d, b, probe, pos)
+
+
+def oracle_measured(w, n_pos: int, workers: int, seed: int = 99, pool=None):
+    """Measured intensities of the first n_pos positions made by the oracle alone: its forward
+    model of the workload's second object (delta_meas, beta_meas) plus Poisson noise, one
+    position per task on its patch.  [n_pos, N, N] float32."""
+    import numpy as np
+    from paper_2012_12686_gb300 import synth
+    N = w["problem"]["N"]
+    p = dict(w["problem"], B=1, Ly=N, Lx=N)
+    jobs = []
+    for i in range(n_pos):
+        pos = np.asarray(w["pos"][i:i + 1], np.float64)
+        c = np.floor(pos[0] + 0.5).astype(int)
+        jobs.append((p, _crop(w["delta_meas"], c, N), _crop(w["beta_meas"], c, N), w["probe"], pos - c))
+    own = pool is None
+    if own:
+        pool = oracle_pool(workers)
+    try:
+        I = np.concatenate(pool.map(_oracle_fwd, jobs), 0)
+    finally:
+        if own:
+            pool.close()
+            pool.join()
+    return synth.poisson(I, seed, w.get("photons", 1.0)).astype(np.float32)
+
+
+def _crop(vol, c, N):
+    """vol[:, c0:c0+N, c1:c1+N] with zeros outside the volume (the patch the oracle reads)."""
+    import numpy as np
+    out = np.zeros((vol.shape[0], N, N), vol.dtype)
+    ya, yb = max(c[0], 0), min(c[0] + N, vol.shape[1])
+    xa, xb = max(c[1], 0), min(c[1] + N, vol.shape[2])
+    if ya < yb and xa < xb:
+        out[:, ya - c[0]:yb - c[0], xa - c[1]:xb - c[1]] = vol[:, ya:yb, xa:xb]
+    return out
+
+
 def oracle_pool(workers: int):
     """Spawn pool of single-threaded oracle workers (one BLAS thread each)."""
     import multiprocessing as mp
@@ -150,13 +205,15 @@ def oracle_pool(workers: int):
     return mp.get_context("spawn").Pool(workers)
 
 
-def oracle_sample(w, I_meas_np, n_pos: int, workers: int, pool=None):
+def oracle_sample(w, I_meas_np, n_pos: int, workers: int, pool=None, keep=False):
     """Time the FP64 oracle (as it stands) on n_pos positions of the minibatch, one position per
-    task, over a spawn pool of `workers` single-threaded processes.  Returns (wall s, positions)."""
+    task, over a spawn pool of `workers` single-threaded processes.  Returns (wall s, positions),
+    and with keep=True also the per-position outputs [(corner, I, (loss, gd, gb, gp, gpos))]: each
+    task is the one-position problem on its patch (patch frame, loss normalised by N^2)."""
     import numpy as np
     N = w["problem"]["N"]
     p = dict(w["problem"], B=1, Ly=N, Lx=N)
-    jobs = []
+    jobs, corners = [], []
     for i in range(n_pos):
         # each task gets only its patch of the volume (the oracle reads nothing else for it)
         pos = np.asarray(w["pos"][i:i + 1], np.float64)
@@ -169,6 +226,7 @@ def oracle_sample(w, I_meas_np, n_pos: int, workers: int, pool=None):
             out[:, ya - c[0]:yb - c[0], xa - c[1]:xb - c[1]] = vol[:, ya:yb, xa:xb]
             crop.append(out)
         jobs.append((p, crop[0], crop[1], w["probe"], pos - c, I_meas_np[i:i + 1]))
+        corners.append(c)
     own = pool is None
     if own:
         pool = oracle_pool(workers)
@@ -177,11 +235,41 @@ def oracle_sample(w, I_meas_np, n_pos: int, workers: int, pool=None):
         t = time.perf_counter()
         pool.map(_oracle_one, jobs)
         wall = time.perf_counter() - t
+        # outputs for the parity check: a second, untimed pass that also returns them
+        res = pool.map(_oracle_one_kept, jobs) if keep else None
     finally:
         if own:
             pool.close()
             pool.join()
-    return wall, n_pos
+    if not keep:
+        return wall, n_pos
+    return wall, n_pos, [(c, r[1][0], r[1][1]) for c, r in zip(corners, res)]
+
+
+def oracle_batch_parity(kept, shape, B, I_gpu, loss_gpu, gd_gpu, gb_gpu, gp_gpu, gpos_gpu):
+    """Relative L2 errors of one GPU loss_grad call on a minibatch against the oracle's outputs
+    for the same B positions (from oracle_sample(keep=True)), assembled into the batch's frame: the
+    per-position losses and probe / position gradients are rescaled from a one-position mean to
+    the batch mean (1/B), the patch gradients are added into the volume at each position's corner
+    (pixels outside the volume dropped)."""
+    import numpy as np
+    import oracle
+    Lz, Ly, Lx = shape
+    gd = np.zeros(shape)
+    gb = np.zeros(shape)
+    I = np.stack([k[1][0] for k in kept])
+    loss = sum(k[2][0] for k in kept) / B
+    gp = sum(k[2][3] for k in kept) / B
+    gpos = np.concatenate([k[2][4] for k in kept], 0) / B
+    for c, _, r in kept:
+        oracle.model.put_chunk_T(gd, c, r[1] / B)
+        oracle.model.put_chunk_T(gb, c, r[2] / B)
+
+    def rel(a, b):
+        a = np.asarray(a)
+        return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(np.asarray(b).ravel()))
+    return {"I": rel(I_gpu, I), "loss": abs(loss_gpu - loss) / abs(loss), "gd": rel(gd_gpu, gd),
+            "gb": rel(gb_gpu, gb), "gp": rel(gp_gpu, gp), "gpos": rel(gpos_gpu, gpos)}
 
 
 # ----------------------------------------------------------------------------- multi-rank host logic
@@ -285,6 +373,39 @@ def time_plain(w, dev, pos_b, I_meas_b, steps, warmup):
             times.append(s.elapsed_time(e))
         d.grad = b.grad = probe.grad = None
     return times
+
+
+def time_regularize(eng, oid, d, b, stream, flush, hbm_peak, reps=20):
+    """adorym_regularize on the workload's object (reweighted l1 + TV, value and gradient): kernel
+    time with CUDA events on the library's stream, L2 flushed before every call.  Algorithmic bytes
+    per voxel: delta, beta and the two weight arrays read (16 B) and the two gradients read and
+    written (16 B); neighbour reads of the TV stencil come from cache and are not counted."""
+    import torch
+    with torch.cuda.stream(stream):
+        wd = torch.ones_like(d)
+        wb = torch.ones_like(b)
+        eng.l1_weights(oid, 1e-8, wd, wb)
+        gd, gb = torch.zeros_like(d), torch.zeros_like(b)
+        loss = torch.zeros((), dtype=torch.float64, device=d.device)
+        kw = dict(alpha_delta=1e-3, alpha_beta=1e-3, gamma_tv=1e-2, w_delta=wd, w_beta=wb, loss_out=loss,
+                  g_delta=gd, g_beta=gb)
+        for _ in range(3):
+            eng.regularize(oid, **kw)
+        ms = []
+        for k in range(reps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            eng.regularize(oid, **kw)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    n = d.numel()
+    t = statistics.median(ms)
+    gbs = 32 * n / (t * 1e-3) / 1e9
+    return {"ms": t, "voxels": n, "bytes_per_voxel": 32, "achieved_gbs": gbs, "peak_gbs": hbm_peak,
+            "frac": gbs / hbm_peak, "case": "reweighted l1 + TV, value and gradient, median of "
+                                            f"{reps} L2-flushed calls"}
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -403,10 +524,20 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize(dev)
         wall = time.perf_counter() - t0
         n_launches = kernel_launches() - launches0   # this library's kernels in the timed region
+        # latency sample: at least 200 more steps, each timed on its own (L2 flushed before each),
+        # so that p99 is a percentile and not the maximum of a short run
+        n_lat = max(200, args.steps)
+        lat_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_lat)]
+        for k, bi in enumerate(rank_batches(rank, world, args.warmup + args.steps, n_lat, nb)):
+            flush.fill_(float(k))
+            lat_ev[k][0].record(stream)
+            step(bi)
+            lat_ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
     step_ms = [a.elapsed_time(bq) for a, bq in ev]
     t_ours = max_over_ranks(sum(step_ms) / 1e3, dev)
     value = units * args.steps * world / t_ours
-    ms_sorted = sorted(step_ms)
+    ms_sorted = sorted(a.elapsed_time(bq) for a, bq in lat_ev)
     p50 = ms_sorted[len(ms_sorted) // 2]
     p99 = ms_sorted[min(len(ms_sorted) - 1, int(math.ceil(0.99 * len(ms_sorted))) - 1)]
 
@@ -468,6 +599,7 @@ def run_ours(args, rank, world, local_rank):
                            else f"{launch_form(B, L, cp, props.multi_processor_count)}<{N},near>"),
                 "bytes_per_unit": bpu}
     hbm_ach = units * bytes_per_unit(N, L, cp) / (k_ms * 1e-3) / 1e9
+    reg = time_regularize(eng, oid, d, b, stream, flush, peaks.get("hbm_gbs", 6795.5)) if far else None
     src = kernel_source_bytes()
     traffic = profiled_traffic(hashlib.sha256(src).hexdigest()[:16])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -475,7 +607,8 @@ def run_ours(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC, "global_batch": B * world, "slices": L, "tile": N,
                        "parallelism": f"replica{world}" if world > 1 else "single", "l2": "flushed between steps"},
-            "latency_ms": {"p50": p50, "p99": p99},
+            "latency_ms": {"p50": p50, "p99": p99, "samples": len(ms_sorted),
+                           "how": "per-step device time of separately timed steps after the timed region"},
             "gpu_launches": n_launches,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": dict(roof, traffic=traffic if args.workload == WORKLOAD else None, kernel_ms=k_ms,
@@ -487,19 +620,42 @@ def run_ours(args, rank, world, local_rank):
     if plain is not None:
         plain["speedup_of_fused"] = value / plain["value"]
         line["plain_gpu"] = plain
+    if reg is not None:
+        line["regularize"] = reg
     if args.workload != WORKLOAD:
         line["config"]["workload"] = args.workload
     if args.batch:
         line["config"]["workload"] = f"{args.workload} with batch {args.batch}"
     if not args.no_cpu_baseline and world == 1 and args.workload == WORKLOAD:
+        # the oracle on the first minibatch (B positions x all slices): timed as it stands for the
+        # CPU baseline, then its outputs compared with one untimed GPU call on the same inputs.
+        # The measured intensities of this check come from the oracle (forward of the second
+        # object + Poisson noise), so no oracle input comes from the CUDA path.
         cores = os.cpu_count() or 1
-        n_pos = min(8 * cores, len(all_pos))
-        Im_np = I_meas.reshape(-1, N, N)[:n_pos].cpu().numpy()
-        ws = dict(w, pos=all_pos[:n_pos])
-        wall_c, npos = oracle_sample(ws, Im_np, n_pos, cores)
+        w0 = dict(w, pos=all_pos[:B])
+        pool = oracle_pool(cores)
+        try:
+            Im0 = oracle_measured(w0, B, cores, pool=pool)
+            wall_c, npos, kept = oracle_sample(w0, Im0, B, cores, pool=pool, keep=True)
+        finally:
+            pool.close()
+            pool.join()
         line["cpu_baseline"] = {"value": npos * L / wall_c, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"{npos} positions x {L} slices of the epoch, one position per "
-                                          f"single-threaded process ({wall_c:.1f} s wall)"}
+                                "sample": f"the {npos} positions x {L} slices of the first minibatch, one "
+                                          f"position per single-threaded process ({wall_c:.1f} s wall)"}
+        with torch.cuda.stream(stream):
+            Im0_d = torch.from_numpy(Im0).to(dev)
+            l0 = torch.zeros((), dtype=torch.float64, device=dev)
+            gd0, gb0 = torch.zeros_like(d), torch.zeros_like(b)
+            gp0 = torch.zeros_like(probe)
+            gpos0 = torch.zeros((B, 2), dtype=torch.float32, device=dev)
+            I0 = torch.empty((B, N, N), dtype=torch.float32, device=dev)
+            eng.loss_grad(prob, oid, probe, pos_b[0], Im0_d, l0, gd0, gb0, gp0, gpos0, I0)
+            stream.synchronize()
+        errs = oracle_batch_parity(kept, tuple(w["delta"].shape), B, I0.cpu().numpy(), float(l0.item()),
+                                   gd0.cpu().numpy(), gb0.cpu().numpy(), gp0.cpu().numpy(), gpos0.cpu().numpy())
+        line["parity"] = dict(errs, vs="FP64 oracle, first minibatch, same launch configuration as the timed steps",
+                              bars=parity_bars(args.workload))
     print(json.dumps(line), flush=True)
 
 
@@ -552,13 +708,24 @@ def run_serve(args):
                 for _ in range(2 * args.serve_slots)]
     gpos_buf = [torch.zeros((256, 2), dtype=torch.float32, device=dev) for _ in range(2 * args.serve_slots)]
     loss_buf = [torch.zeros((), dtype=torch.float64, device=dev) for _ in range(2 * args.serve_slots)]
-    # warm the graphs of every template once
+    # warm the graphs of every template (twice per slot set: capture, then update), then time each
+    # template alone on an idle device: its standalone service time, the denominator of the slowdown
+    for rep in range(2):
+        for t in templates:
+            gd, gb = per_slot[0][t["p"]["L"]]
+            tk = eng.submit(t["prob"], t["oid"], probes[t["p"]["N"]], t["pos"], t["I"], loss_buf[0], gd, gb, None,
+                            gpos_buf[0][:t["p"]["B"]])
+            eng.poll(tk, -1)
+    alone_ms = []
     for t in templates:
         gd, gb = per_slot[0][t["p"]["L"]]
         tk = eng.submit(t["prob"], t["oid"], probes[t["p"]["N"]], t["pos"], t["I"], loss_buf[0], gd, gb, None,
                         gpos_buf[0][:t["p"]["B"]])
+        t0a = time.perf_counter()
         eng.poll(tk, -1)
+        alone_ms.append((time.perf_counter() - t0a) * 1e3)
     done_t = [0.0] * n
+    parts = [(0.0, 0.0)] * n
     tickets = [None] * n
     t0 = time.perf_counter()
 
@@ -578,10 +745,15 @@ def run_serve(args):
     for i in range(n):
         while tickets[i] is None:
             time.sleep(0.0001)
-        assert eng.poll(tickets[i], -1) == OK
+        rc, queued_us, run_us, _ = eng.poll_times(tickets[i], -1)
+        assert rc == OK
         done_t[i] = time.perf_counter() - t0
+        parts[i] = (queued_us / 1e3, run_us / 1e3)
     th.join()
     lat = np.array(done_t) - arrivals
+    queued = np.array([q for q, _ in parts])
+    run = np.array([r for _, r in parts])
+    slowdown = lat * 1e3 / np.array([alone_ms[w] for w in which])
     units = np.array([templates[w]["units"] for w in which])
     span = done_t[-1] - arrivals[0]
     # plain path: per-template service time (sub-batches of <= 32 positions to bound autograd memory)
@@ -618,11 +790,37 @@ def run_serve(args):
             "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "throughput": float(units.sum() / span), "unit": UNIT,
             "admission_waits": eng.serve_stats()[1],
+            "breakdown_ms": {"queued_p50": float(np.percentile(queued, 50)),
+                             "queued_p99": float(np.percentile(queued, 99)),
+                             "run_p50": float(np.percentile(run, 50)), "run_p99": float(np.percentile(run, 99)),
+                             "how": "queued = submit to admission, run = admission to completion (poll_times)"},
+            "alone_ms": {"p50": float(np.percentile([alone_ms[w] for w in which], 50)),
+                         "p99": float(np.percentile([alone_ms[w] for w in which], 99)),
+                         "max": float(max(alone_ms)),
+                         "how": "each template submitted alone on an idle device, submit to poll return"},
+            "slowdown": {"p50": float(np.percentile(slowdown, 50)), "p99": float(np.percentile(slowdown, 99)),
+                         "how": "latency in the mix / the same request's latency alone"},
             "plain_one_at_a_time": {"p50_ms": float(np.percentile(plat, 50) * 1e3),
                                     "p99_ms": float(np.percentile(plat, 99) * 1e3),
                                     "throughput": float(units.sum() / (fin - arrivals[0])),
                                     "how": "measured service time per template, replayed on the same arrivals"}}
     print(json.dumps(line), flush=True)
+
+
+def parity_bars(workload: str):
+    """Relative-L2 bars against the FP64 oracle: 1e-4 for intensities and loss; for gradients
+    1e-3, or at full size the FP32 floor stored in tests/golden/fp32_floor.json (the error of the
+    same model evaluated with single-precision FFTs, written by tests/golden/make_fp32_floor.py
+    from the oracle alone) where that floor is higher."""
+    bars = {"I": 1e-4, "loss": 1e-4, "gd": 1e-3, "gb": 1e-3, "gp": 1e-3, "gpos": 1e-3}
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "fp32_floor.json")) as fh:
+            fl = json.load(fh)["workloads"][workload]["fp32_fft"]
+        for k in ("gd", "gb", "gp", "gpos"):
+            bars[k] = max(bars[k], fl[k])
+    except (OSError, KeyError, ValueError):
+        pass
+    return bars
 
 
 KERNEL_SOURCES = ("k_path.cuh", "fft_block.cuh", "numerics.cuh", "kernels.cuh")

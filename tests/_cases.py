@@ -181,24 +181,3 @@ def cuda_run(case, I_meas, want=(True, True, True), engine=None):
     eng.unregister_object(oid)
     f = lambda t: None if t is None else t.cpu().numpy()
     return dict(I=f(I_out), I2=f(I2), loss=float(loss.item()), gd=f(gd), gb=f(gb), gp=f(gp), gpos=f(gpos))
-
-
-def plain_errors(case, I_meas, ref):
-    """Relative errors of the plain torch GPU path (torch.fft/cuFFT + autograd, FP32) against the
-    oracle results `ref` on the same inputs: the FP32 conditioning yardstick for full-size bars."""
-    import torch
-    import bench
-    dev = torch.device("cuda:0")
-    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).to(dev)
-    d = t(case["delta"], np.float32).requires_grad_()
-    b = t(case["beta"], np.float32).requires_grad_()
-    probe = t(case["probe"], np.complex64).requires_grad_()
-    pos = t(case["pos"], np.float32).requires_grad_()
-    loss, _ = bench.plain_loss(d, b, probe, pos, t(I_meas, np.float32), case["problem"])
-    loss.backward()
-    out = {"loss": abs(loss.item() - ref[0]) / abs(ref[0]), "gd": rel(d.grad.cpu().numpy(), ref[1]),
-           "gb": rel(b.grad.cpu().numpy(), ref[2]), "gp": rel(probe.grad.cpu().numpy(), ref[3]),
-           "gpos": rel(pos.grad.cpu().numpy(), ref[4])}
-    del loss, d, b, probe, pos
-    torch.cuda.empty_cache()
-    return out

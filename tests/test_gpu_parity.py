@@ -82,11 +82,26 @@ def test_only_some_gradients_and_determinism():
     np.testing.assert_array_equal(r1["gp"], r2["gp"])
 
 
+def full_size_bars(name):
+    """Fixed relative-L2 bars of a full-size workload: 1e-4 for intensities and loss; for each
+    gradient 1e-3, or the stored FP32 floor where it is higher.  The floor (tests/golden/
+    fp32_floor.json, written from the oracle alone by tests/golden/make_fp32_floor.py) is the error
+    of the same model evaluated with single-precision FFTs: at full size a dark far-field pixel that
+    holds a count gets a large adjoint seed, and its value is set by the FP32 rounding noise of every
+    transform before it, so no FP32 evaluation reaches 1e-3 there."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "fp32_floor.json")) as fh:
+        floor = json.load(fh)["workloads"][name]["fp32_fft"]
+    bars = {"I": C.TOL_I, "loss": C.TOL_I}
+    bars.update({k: max(C.TOL_G, floor[k]) for k in ("gd", "gb", "gp", "gpos")})
+    return bars
+
+
 def _full(name, **over):
     """A workload at its full size, oracle on every CPU core (spawn pool)."""
     import os
     from paper_2012_12686_gb300 import synth
-    import oracle
     w = synth.workload(name, seed=0, **over)
     workers = os.cpu_count() or 1
     Im = C.measured_par(w, workers)
@@ -96,14 +111,10 @@ def _full(name, **over):
     errs = {"I": C.rel(r["I"], I_ref), "loss": abs(r["loss"] - ref[0]) / abs(ref[0]),
             "gd": C.rel(r["gd"], ref[1]), "gb": C.rel(r["gb"], ref[2]), "gp": C.rel(r["gp"], ref[3]),
             "gpos": C.rel(r["gpos"], ref[4])}
-    assert errs["I"] <= C.TOL_I and errs["loss"] <= C.TOL_I, errs
-    # At full size some gradient components are ill-conditioned with respect to FP32 rounding of
-    # the wavefields (weak beta signal, probe/position gradients): the bar for each gradient is
-    # 1e-3 or 1.5x the error of the plain cuFFT + autograd FP32 path on the same inputs.
-    pe = C.plain_errors(w, Im, ref)
-    bars = {k: max(C.TOL_G, 1.5 * pe[k]) for k in ("gd", "gb", "gp", "gpos")}
-    bad = {k: (errs[k], bars[k], pe[k]) for k in bars if errs[k] > bars[k]}
-    assert not bad, (bad, errs, pe)
+    bars = full_size_bars(name)
+    bad = {k: (errs[k], bars[k]) for k in bars if errs[k] > bars[k]}
+    assert not bad, (bad, errs)
+    print(name, errs)
     return errs
 
 
@@ -166,4 +177,38 @@ def test_host_buffers_match_device_buffers(far, N):
         for x, y in zip(g, r):
             x, y = x.cpu().numpy(), y.cpu().numpy()
             assert C.rel(x, y) <= 1e-6, (far, C.rel(x, y))
+    eng.unregister_object(oid)
+
+
+@pytest.mark.parametrize("kw", [dict(N=32, L=5, M=1, B=7, loss="poisson"),
+                                dict(N=16, L=9, M=1, B=4, loss="lsq", tomo=True, theta=0.4, Ly=20, Lx=17),
+                                dict(N=256, L=2, M=1, B=3, loss="lsq")])
+def test_position_offset_gradient(kw):
+    """Per-angle position offset (Sec. 2.3.2): g_offset of adorym_loss_grad_ext against the
+    oracle's offset_loss_grad, on the shared-memory path, through the rotation, and on the two-pass
+    path; also returned into host memory."""
+    import torch
+    import oracle
+    from paper_2012_12686_gb300.adorym import Engine
+    case = C.small_case(seed=41, **kw)
+    Im = C.measured(case).astype(np.float32)
+    L0, g_ref = oracle.model.offset_loss_grad(case["problem"], case["delta"], case["beta"], case["probe"],
+                                              case["pos"], Im)
+    dev = torch.device("cuda:0")
+    eng = Engine(0)
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).to(dev)
+    d, b = t(case["delta"], np.float32), t(case["beta"], np.float32)
+    oid = eng.register_object(d, b)
+    probe, pos, Imd = t(case["probe"], np.complex64), t(case["pos"], np.float32), t(Im, np.float32)
+    g_off = torch.zeros(2, dtype=torch.float32, device=dev)
+    gpos = torch.zeros_like(pos)
+    eng.loss_grad_ext(case["problem"], oid, probe, pos, Imd, g_pos=gpos, g_offset=g_off)
+    g_host = np.zeros(2, np.float32)
+    eng.loss_grad_ext(case["problem"], oid, probe, pos, Imd, g_offset=g_host)   # only the offset, host output
+    torch.cuda.synchronize()
+    got = g_off.cpu().numpy()
+    assert C.rel(got, g_ref) <= C.TOL_G, (got, g_ref)
+    np.testing.assert_array_equal(got, g_host)
+    np.testing.assert_allclose(got, gpos.cpu().numpy().astype(np.float64).sum(0), rtol=1e-5,
+                               atol=1e-6 * np.abs(gpos.cpu().numpy()).sum())
     eng.unregister_object(oid)
