@@ -72,8 +72,8 @@ typedef struct adorym_ctx adorym_ctx;
 /* One loss/gradient problem (the paper's reconstruct_ptychography parameters that reach the
  * forward model, Sec. 2.7 "User interface", reduced to dimensionless pixel units). */
 typedef struct adorym_problem {
-  int N;              /* tile (probe / detector) side in pixels: 8..128 (powers of two);
-                         near field also 256, 512, 1024                                    */
+  int N;              /* tile (probe / detector) side in pixels: a power of two in 8..1024
+                         (8..128: one fused kernel per call; 256..1024: two-pass path)     */
   int L;              /* slices each wave traverses                                        */
   int M;              /* incoherent probe modes (Eq. multimode)                            */
   int B;              /* far field: positions in the minibatch; near field: problems        */
@@ -119,6 +119,21 @@ int adorym_check(adorym_ctx* ctx);
  * serving graph count once, at capture).  Accounting only (no counterpart in the paper):
  * differences around a region give the kernels that region launched. */
 uint64_t adorym_kernel_launches(void);
+
+/* Test hook for the bounded device-side waits (no counterpart in the paper).  Three waits exist:
+ * a position waiting for a checkpoint segment that a recompute helper is working on (default
+ * about 2^28 SM cycles, then the position recomputes the segment itself), a helper waiting for a
+ * position's checkpoint (about 2^24 cycles, then the helper stops), and a two-pass column kernel
+ * waiting for its tile's TMA copy (about 2^31 cycles, then the call's status word reports
+ * ADORYM_EDATA "wait timed out", and the CTA waits for its copies with the default limit before it
+ * leaves).  Each argument is a limit in SM clock cycles (>= 0), ADORYM_WAIT_DEFAULT to restore the
+ * default, or for tile copies ADORYM_WAIT_GIVE_UP to report the timeout without waiting.  The
+ * limits are process-wide and apply to calls enqueued afterwards (serving graphs keep the limits
+ * of their capture).  Results do not depend on the first two limits; a tile-copy timeout makes
+ * the call's results meaningless.  Returns ADORYM_OK or ADORYM_EINVAL. */
+#define ADORYM_WAIT_DEFAULT (-1)
+#define ADORYM_WAIT_GIVE_UP (-2)
+int adorym_set_wait_limits(int64_t segment_cycles, int64_t checkpoint_cycles, int64_t tile_copy_cycles);
 
 /* Measured FP32 fused-multiply-add throughput of `device` in TFLOP/s (2 flops per FMA): a
  * throughput kernel of independent FMA chains on several CTAs per SM, best of four timed runs
@@ -171,6 +186,11 @@ typedef struct adorym_grads {
   float* I_out;     /* predicted intensities, overwritten                                        */
   float* g_gaps;    /* with variable spacing: [L-1] dL/d(lambda dz_j / dx^2), the slice-position
                        gradient (Sec. 2.3.2), summed over the batch, overwritten                  */
+  float* g_offset;  /* far field only: [2] (y, x) gradient w.r.t. one position offset shared by
+                       every position of the batch -- the per-angle probe-position offset of
+                       ptychotomography (Sec. 2.3.2 "Probe position offset"), for a batch that
+                       holds the positions of one angle.  Sum over the batch of the per-position
+                       gradients, taken in FP64 in a fixed order; overwritten.                   */
 } adorym_grads;
 
 /* adorym_loss_grad with its outputs in a struct, including the near-field distance gradient. */
@@ -216,16 +236,27 @@ typedef struct adorym_request {
 
 /* Serving loop.  adorym_submit queues a request and returns at once with *ticket.  A request
  * is admitted when a slot is free and its device workspace fits the context's footprint
- * budget; admitted requests run concurrently on separate streams as captured CUDA graphs
- * (one graph per problem shape and slot), so requests that arrive while others run overlap
- * with them on the device.  Array pointers must be device memory and stay valid until the
- * request completes.  Requests whose footprint can never fit return ENOMEM at submit. */
+ * budget, in arrival order except that requests which fit may go ahead of an older one that
+ * does not (at most 8 admissions past any one waiting request, so none is starved); admitted
+ * requests run concurrently on separate streams as captured CUDA graphs (one graph per problem
+ * shape and slot), so requests that arrive while others run overlap with them on the device.
+ * Completion is event driven (a blocked waiter per slot, no polling).  Array pointers must be
+ * device memory and stay valid until the request completes.  Requests whose footprint can never
+ * fit return ENOMEM at submit. */
 int adorym_submit(adorym_ctx* ctx, const adorym_request* req, uint64_t* ticket);
 
 /* Wait up to timeout_us microseconds (<0: forever, 0: test) for a ticket.  Returns ADORYM_OK
  * once the request's outputs are complete (the ticket is then retired), ETIMEDOUT if it is still
  * queued or running, ENOENT for an unknown ticket, or the request's own error code. */
 int adorym_poll(adorym_ctx* ctx, uint64_t ticket, int64_t timeout_us);
+
+/* adorym_poll that also reports where the request's time went (times_us[3], may be NULL):
+ * times_us[0] = time from submission to admission (queueing for a slot and memory),
+ * times_us[1] = time from admission to completion (graph capture or update, launch and device
+ * execution, including time shared with other admitted requests), times_us[2] = the admission
+ * instant since the serving loop was configured (-1 if never admitted).  Host clock,
+ * microseconds.  Same return codes. */
+int adorym_poll_times(adorym_ctx* ctx, uint64_t ticket, int64_t timeout_us, double* times_us);
 
 /* Serving configuration: number of concurrent slots (streams, 1..16) and the device-memory
  * footprint budget in bytes for admitted requests' workspaces (0 = no limit).  Only allowed
@@ -267,27 +298,34 @@ int adorym_workspace_bytes(const adorym_problem* p, int grads, uint64_t* bytes);
 /* adorym_loss_grad for callers that cannot allocate device memory.  The paper has no
  * counterpart: this is a deployment variant of the same computation.
  *
- * Who needs it: code that runs where cudaMalloc is not allowed or not wanted -- inside a CUDA
- * stream capture owned by someone else, in a plug-in whose host framework owns all device memory
- * through its own pool, or in a latency-critical loop that must not allocate.  This call takes
- * no context and allocates nothing (no cudaMalloc, cudaFree or allocating library routine):
- * its workspace and tables live in one file-scope device array of ADORYM_NOALLOC_SCRATCH_BYTES
- * (64 MiB), reserved on every GPU that loads the library until the process exits.
+ * Who needs it: code that runs where cudaMalloc is not allowed or not wanted -- a plug-in whose
+ * host framework owns all device memory through its own pool, or a latency-critical loop that
+ * must not allocate (an allocation can synchronise the device).  This call takes no context and
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine): its workspace and
+ * tables live in one file-scope device array of ADORYM_NOALLOC_SCRATCH_BYTES (64 MiB), reserved
+ * on every GPU that loads the library until the process exits.  The twiddle and propagator
+ * tables are computed into that array by a kernel on cuda_stream.
  *
  * Arguments are those of adorym_loss_grad (same layouts and accumulate/overwrite rules), except
- * that the object volumes delta, beta ([Lz][Ly][Lx] FP32) are passed directly and every pointer
- * must be device memory.  Work is enqueued on cuda_stream (a cudaStream_t) on the current device.
+ * that the object volumes delta, beta ([Lz][Ly][Lx] FP32) are passed directly, every pointer
+ * must be device memory, and variable slice spacing is not offered (p->gaps with L > 1 returns
+ * ADORYM_EINVAL).  Work is enqueued on cuda_stream (a cudaStream_t) on the current device.
+ *   status  optional device int: with it, the kernels OR the call's ADORYM status bits into
+ *           *status (the caller zeroes it beforehand; nonzero afterwards means a position was
+ *           not finite or beyond +-2^24 px, or a bounded device wait gave up, and the outputs are
+ *           then meaningless).  NULL: the status is kept in the scratch array only and not
+ *           reported.
  *
  * Returns ADORYM_ETOOBIG when the problem's workspace exceeds the array (e.g. large batches of
  * 128x128 tiles: use adorym_loss_grad there), EINVAL for invalid sizes or non-device pointers.
- * The array's device address is looked up on the first call made on each device, so make that
- * first call before any stream capture.  All calls share the array and it keeps the previous
- * call's contents (each call clears on its stream what must start at zero); calls that overlap
- * on the GPU -- on different streams or from several host threads -- race on it, so the caller
- * must serialise them (e.g. one stream). */
+ * The array's device address is looked up on the first call made on each device.  All calls
+ * share the array and it keeps the previous call's contents (each call clears on its stream what
+ * must start at zero); calls that overlap on the GPU -- on different streams or from several
+ * host threads -- race on it, so the caller must serialise them (e.g. one stream). */
 int adorym_loss_grad_noalloc(void* cuda_stream, const adorym_problem* p, const float* delta, const float* beta,
                              const float* probe, const float* pos, const float* I_meas, double* loss_out,
-                             float* g_delta, float* g_beta, float* g_probe, float* g_pos, float* I_out);
+                             float* g_delta, float* g_beta, float* g_probe, float* g_pos, float* I_out,
+                             int* status);
 
 #ifdef __cplusplus
 }

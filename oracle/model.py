@@ -387,3 +387,18 @@ def loss_grad(problem, delta, beta, probe, pos, I_meas, want_nf=False, want_gaps
     if want_gaps:
         out = out + (g_gaps,)
     return out
+
+
+# ------------------------------------------------------------------ per-angle position offset
+def offset_loss_grad(problem, delta, beta, probe, pos, I_meas):
+    """Loss and its gradient w.r.t. one position offset o shared by every position of the batch
+    (the per-angle probe-position offset of ptychotomography, Sec. 2.3.2 "Probe position offset":
+    one correction vector applies to all probe positions of an angle).  The model sees
+    pos_b + o for every b, so by the chain rule dL/do = sum_b dL/dpos_b.  Returns (loss, [2]).
+    """
+    pb = problem if isinstance(problem, Problem) else Problem.of(problem)
+    if not pb.farfield:
+        raise ValueError("the position offset is defined for the far-field geometry")
+    out = loss_grad(pb, delta, beta, probe, pos, I_meas)
+    return out[0], np.sum(out[4], axis=0)
+

@@ -23,7 +23,9 @@ EXPORTS = ["adorym_create", "adorym_destroy", "adorym_last_error", "adorym_regis
            "adorym_serve_config", "adorym_serve_stats", "adorym_workspace_bytes", "adorym_enable_kernel_timing",
            "adorym_kernel_ms", "adorym_loss_grad_noalloc", "adorym_loss_grad_ext", "adorym_regularize",
            "adorym_l1_weights", "adorym_check", "adorym_kernel_launches",
-           "adorym_fp32_peak", "adorym_cancel", "adorym_inject_alloc_failures"]
+           "adorym_fp32_peak", "adorym_cancel", "adorym_inject_alloc_failures", "adorym_set_wait_limits",
+           "adorym_poll_times"]
+WAIT_DEFAULT, WAIT_GIVE_UP = -1, -2
 
 
 class Problem(ctypes.Structure):
@@ -62,7 +64,7 @@ class Problem(ctypes.Structure):
 class Grads(ctypes.Structure):
     _fields_ = [("loss", ctypes.c_void_p), ("g_delta", ctypes.c_void_p), ("g_beta", ctypes.c_void_p),
                 ("g_probe", ctypes.c_void_p), ("g_pos", ctypes.c_void_p), ("g_nf", ctypes.c_void_p),
-                ("I_out", ctypes.c_void_p), ("g_gaps", ctypes.c_void_p)]
+                ("I_out", ctypes.c_void_p), ("g_gaps", ctypes.c_void_p), ("g_offset", ctypes.c_void_p)]
 
 
 class Reg(ctypes.Structure):
@@ -99,6 +101,7 @@ def lib() -> ctypes.CDLL:
         L.adorym_loss_grad.argtypes = [vp, ctypes.POINTER(Problem), i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.adorym_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(u64)]
         L.adorym_poll.argtypes = [vp, u64, ctypes.c_int64]
+        L.adorym_poll_times.argtypes = [vp, u64, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]
         L.adorym_serve_config.argtypes = [vp, i32, u64]
         L.adorym_serve_stats.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
         L.adorym_workspace_bytes.argtypes = [ctypes.POINTER(Problem), i32, ctypes.POINTER(u64)]
@@ -107,12 +110,14 @@ def lib() -> ctypes.CDLL:
         L.adorym_regularize.argtypes = [vp, i32, ctypes.POINTER(Reg), vp, vp, vp]
         L.adorym_l1_weights.argtypes = [vp, i32, ctypes.c_double, vp, vp]
         L.adorym_loss_grad_ext.argtypes = [vp, ctypes.POINTER(Problem), i32, vp, vp, vp, ctypes.POINTER(Grads)]
-        L.adorym_loss_grad_noalloc.argtypes = [vp, ctypes.POINTER(Problem), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.adorym_loss_grad_noalloc.argtypes = [vp, ctypes.POINTER(Problem), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                               vp]
         L.adorym_check.argtypes = [vp]
         L.adorym_kernel_launches.argtypes = []
         L.adorym_fp32_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         L.adorym_cancel.argtypes = [vp, u64]
         L.adorym_inject_alloc_failures.argtypes = [vp, i32]
+        L.adorym_set_wait_limits.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
         for name in EXPORTS:
             if name not in ("adorym_destroy", "adorym_last_error", "adorym_kernel_launches"):
                 getattr(L, name).restype = ctypes.c_int
@@ -211,13 +216,15 @@ class Engine:
                                                   _ptr(g_probe), _ptr(g_pos), _ptr(I_out)))
 
     def loss_grad_ext(self, problem, obj_id, probe, pos, I_meas, loss_out=None, g_delta=None, g_beta=None,
-                      g_probe=None, g_pos=None, g_nf=None, I_out=None, g_gaps=None):
-        """adorym_loss_grad_ext: as loss_grad, plus g_nf (near field: dL/dN_F per problem and distance)
-        and g_gaps (variable slice spacing: dL/d(lambda dz_j / dx^2))."""
+                      g_probe=None, g_pos=None, g_nf=None, I_out=None, g_gaps=None, g_offset=None):
+        """adorym_loss_grad_ext: as loss_grad, plus g_nf (near field: dL/dN_F per problem and distance),
+        g_gaps (variable slice spacing: dL/d(lambda dz_j / dx^2)) and g_offset (far field: [2] gradient
+        w.r.t. one position offset shared by the whole batch, the per-angle offset)."""
         p = problem if isinstance(problem, Problem) else Problem.of(problem)
         g = Grads()
         for k, v in (("loss", loss_out), ("g_delta", g_delta), ("g_beta", g_beta), ("g_probe", g_probe),
-                     ("g_pos", g_pos), ("g_nf", g_nf), ("I_out", I_out), ("g_gaps", g_gaps)):
+                     ("g_pos", g_pos), ("g_nf", g_nf), ("I_out", I_out), ("g_gaps", g_gaps),
+                     ("g_offset", g_offset)):
             setattr(g, k, _ptr(v))
         return self._check(lib().adorym_loss_grad_ext(self._ctx, ctypes.byref(p), obj_id, _ptr(probe), _ptr(pos),
                                                       _ptr(I_meas), ctypes.byref(g)))
@@ -263,6 +270,16 @@ class Engine:
             raise AdorymError(rc, self.last_error())
         return rc
 
+    def poll_times(self, ticket: int, timeout_us: int = -1):
+        """adorym_poll_times: (rc, queued_us, run_us, admitted_at_us) -- time waiting for admission,
+        time from admission to completion, and the admission instant (host clock); rc is OK or
+        ETIMEDOUT, other codes raise."""
+        t = (ctypes.c_double * 3)()
+        rc = lib().adorym_poll_times(self._ctx, ticket, timeout_us, t)
+        if rc not in (OK, ETIMEDOUT):
+            raise AdorymError(rc, self.last_error())
+        return rc, t[0], t[1], t[2]
+
     def check(self) -> int:
         """Wait for the context's stream and raise on the last call's device status word (EDATA:
         invalid positions / shifts found by the kernels)."""
@@ -283,13 +300,21 @@ class Engine:
 
 
 def loss_grad_noalloc(stream, problem, delta, beta, probe, pos, I_meas, loss_out=None, g_delta=None, g_beta=None,
-                      g_probe=None, g_pos=None, I_out=None) -> int:
+                      g_probe=None, g_pos=None, I_out=None, status=None) -> int:
     """adorym_loss_grad_noalloc: same computation as Engine.loss_grad with no device allocation
-    (fixed 64 MiB scratch); all arrays must be device memory.  Returns the library's code."""
+    (fixed 64 MiB scratch); all arrays must be device memory.  `status`: optional device int32
+    tensor, zeroed by the caller, into which the kernels OR the call's status bits.  Returns the
+    library's code."""
     p = problem if isinstance(problem, Problem) else Problem.of(problem)
     return lib().adorym_loss_grad_noalloc(ctypes.c_void_p(stream), ctypes.byref(p), _ptr(delta), _ptr(beta),
                                           _ptr(probe), _ptr(pos), _ptr(I_meas), _ptr(loss_out), _ptr(g_delta),
-                                          _ptr(g_beta), _ptr(g_probe), _ptr(g_pos), _ptr(I_out))
+                                          _ptr(g_beta), _ptr(g_probe), _ptr(g_pos), _ptr(I_out), _ptr(status))
+
+
+def set_wait_limits(segment_cycles=WAIT_DEFAULT, checkpoint_cycles=WAIT_DEFAULT, tile_copy_cycles=WAIT_DEFAULT):
+    """adorym_set_wait_limits: cycle limits of the bounded device-side waits (test hook; the
+    defaults are restored by WAIT_DEFAULT).  Returns the library's code."""
+    return lib().adorym_set_wait_limits(int(segment_cycles), int(checkpoint_cycles), int(tile_copy_cycles))
 
 
 def workspace_bytes(problem, grads: int = 7) -> int:

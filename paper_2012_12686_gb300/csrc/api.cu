@@ -47,6 +47,16 @@ int validate(const adorym_problem& p, const char** err) {
 
 std::atomic<unsigned long long> g_kernel_launches{0};
 
+static std::atomic<long long> g_wait_seg{WaitLimits{}.seg}, g_wait_ckpt{WaitLimits{}.ckpt}, g_wait_tma{WaitLimits{}.tma};
+
+WaitLimits wait_limits() {
+  WaitLimits w;
+  w.seg = g_wait_seg.load(std::memory_order_relaxed);
+  w.ckpt = g_wait_ckpt.load(std::memory_order_relaxed);
+  w.tma = g_wait_tma.load(std::memory_order_relaxed);
+  return w;
+}
+
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // SMs of the current device (0 when there is none)
@@ -69,7 +79,8 @@ int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan
   q.adj = adj;
   q.want_obj = adj && (grads & 1);
   q.want_probe = adj && (grads & 2);
-  q.want_pos = adj && (grads & 4);
+  q.want_offset = adj && (grads & 32) && p.farfield;
+  q.want_pos = adj && ((grads & 4) || q.want_offset);
   q.want_nf = adj && (grads & 8) && !p.farfield;
   q.gaps = p.gaps != nullptr && p.L > 1;
   q.want_gaps = adj && (grads & 16) && q.gaps;
@@ -120,6 +131,10 @@ int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan
   q.off_loss = take(sizeof(double));
   q.off_box = take(4 * sizeof(int));
   q.off_status = take(sizeof(int));
+  if (q.want_offset) {
+    q.off_posd = take(B * 2 * sizeof(double));
+    q.off_s_goff = take(2 * sizeof(float));
+  }
   if (q.want_gaps) {
     const int parts = two_pass(p.N) ? (int)(N / (N == 256 ? 32 : N == 512 ? 16 : 8)) : 1;
     q.off_spck = take(B * M * q.ncp * NN * f2);
@@ -329,6 +344,7 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
     t.adj = pl.adj ? 1 : 0;
     t.eps = (float)p.eps;
     t.kdz = (float)p.kdz;
+    t.wait_tma = wait_limits().tma;
     t.inv_npix = 1.0 / ((double)p.B * pl.nd * (double)pl.NN);
     t.T = T;
     t.probe = c.probe;
@@ -369,6 +385,7 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
       t.gdf = direct ? c.gd : nullptr;
       t.gbf = direct ? c.gb : nullptr;
       t.gpos = pl.want_pos ? c.g_pos : nullptr;
+      t.gposd = pl.want_offset ? reinterpret_cast<double*>(W(pl.off_posd)) : nullptr;
       t.g_probe = pl.want_probe ? c.g_probe : nullptr;
       t.loss_out = c.loss;
     }
@@ -395,6 +412,8 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
     a.pipe = pl.pipe ? 1 : 0;
     a.eps = (float)p.eps;
     a.kdz = (float)p.kdz;
+    a.wait_seg = wait_limits().seg;
+    a.wait_ckpt = wait_limits().ckpt;
     a.inv_npix = 1.0 / ((double)p.B * pl.nd * (double)pl.NN);
     a.T = T;
     a.probe = c.probe;
@@ -419,6 +438,7 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
       a.gdf = direct ? c.gd : nullptr;
       a.gbf = direct ? c.gb : nullptr;
       a.gpos = pl.want_pos ? c.g_pos : nullptr;
+      a.gposd = pl.want_offset ? reinterpret_cast<double*>(W(pl.off_posd)) : nullptr;
       a.gnf = pl.want_nf ? c.g_nf : nullptr;
       for (int d = 0; d < 4; ++d) a.nf[d] = p.nf[d];
       if (pl.want_gaps) {
@@ -460,6 +480,10 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
         join_side = true;
       }
     }
+  }
+  if (pl.want_offset && c.g_offset) {
+    if ((rc = chk(launch_offset_sum(reinterpret_cast<double*>(W(pl.off_posd)), p.B, c.g_offset, s), "offset_sum")))
+      return rc;
   }
   if (pl.want_obj && !direct) {
     if (pl.tomo)
@@ -590,6 +614,18 @@ int adorym_inject_alloc_failures(adorym_ctx* ctx, int count) {
 
 uint64_t adorym_kernel_launches(void) { return g_kernel_launches.load(std::memory_order_relaxed); }
 
+int adorym_set_wait_limits(int64_t segment_cycles, int64_t checkpoint_cycles, int64_t tile_copy_cycles) {
+  if (segment_cycles < ADORYM_WAIT_DEFAULT || checkpoint_cycles < ADORYM_WAIT_DEFAULT ||
+      tile_copy_cycles < ADORYM_WAIT_GIVE_UP)
+    return ADORYM_EINVAL;
+  const WaitLimits d;
+  g_wait_seg.store(segment_cycles == ADORYM_WAIT_DEFAULT ? d.seg : segment_cycles);
+  g_wait_ckpt.store(checkpoint_cycles == ADORYM_WAIT_DEFAULT ? d.ckpt : checkpoint_cycles);
+  g_wait_tma.store(tile_copy_cycles == ADORYM_WAIT_DEFAULT ? d.tma : tile_copy_cycles == ADORYM_WAIT_GIVE_UP ? -1
+                                                                                                         : tile_copy_cycles);
+  return ADORYM_OK;
+}
+
 int adorym_check(adorym_ctx* ctx) {
   if (!ctx) return ADORYM_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
@@ -639,7 +675,8 @@ int adorym_workspace_bytes(const adorym_problem* p, int grads, uint64_t* bytes) 
 
 static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const float* probe, const float* pos,
                     const float* I_meas, double* loss_out, float* g_delta, float* g_beta, float* g_probe,
-                    float* g_pos, float* I_out, bool adj, float* g_nf = nullptr, float* g_gaps = nullptr) {
+                    float* g_pos, float* I_out, bool adj, float* g_nf = nullptr, float* g_gaps = nullptr,
+                    float* g_offset = nullptr) {
   if (!ctx) return ADORYM_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (!p) return fail(ctx, ADORYM_EINVAL, "null problem");
@@ -655,7 +692,10 @@ static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const 
     return fail(ctx, ADORYM_EINVAL, "problem Lz/Ly/Lx differ from the registered object");
   if (g_delta && (ptr_kind(g_delta) != 1 || ptr_kind(g_beta) != 1))
     return fail(ctx, ADORYM_EINVAL, "g_delta / g_beta must be device memory");
-  const int grads = (g_delta ? 1 : 0) | (g_probe ? 2 : 0) | (g_pos ? 4 : 0) | (g_nf ? 8 : 0) | (g_gaps ? 16 : 0);
+  const int grads = (g_delta ? 1 : 0) | (g_probe ? 2 : 0) | (g_pos ? 4 : 0) | (g_nf ? 8 : 0) | (g_gaps ? 16 : 0) |
+                    (g_offset ? 32 : 0);
+  if (g_offset && !p->farfield)
+    return fail(ctx, ADORYM_EINVAL, "g_offset (per-angle position offset) is defined for the far-field geometry only");
   if (g_gaps && !(p->gaps && p->L > 1))
     return fail(ctx, ADORYM_EINVAL, "g_gaps needs variable slice spacing (gaps) and L > 1");
   if (g_nf && p->farfield) return fail(ctx, ADORYM_EINVAL, "g_nf is defined for the near-field geometry only");
@@ -726,6 +766,8 @@ static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const 
   const bool host_iout = I_out && ptr_kind(I_out) == 0;
   const bool host_gnf = g_nf && ptr_kind(g_nf) == 0;
   const bool host_ggap = g_gaps && ptr_kind(g_gaps) == 0;
+  const bool host_goff = g_offset && ptr_kind(g_offset) == 0;
+  if (g_offset) c.g_offset = host_goff ? reinterpret_cast<float*>(ws + pl.off_s_goff) : g_offset;
   if (g_gaps) c.g_gaps = host_ggap ? reinterpret_cast<float*>(ws + pl.off_s_ggap) : g_gaps;
   if (g_nf) c.g_nf = host_gnf ? reinterpret_cast<float*>(ws + pl.off_s_gnf) : g_nf;
   c.loss = loss_out ? (host_loss ? reinterpret_cast<double*>(ws + pl.off_loss) : loss_out) : nullptr;
@@ -777,6 +819,10 @@ static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const 
   }
   if (host_ggap) {
     cudaMemcpyAsync(g_gaps, c.g_gaps, (size_t)(p->L - 1) * sizeof(float), cudaMemcpyDeviceToHost, s);
+    sync_after = true;
+  }
+  if (host_goff) {
+    cudaMemcpyAsync(g_offset, c.g_offset, 2 * sizeof(float), cudaMemcpyDeviceToHost, s);
     sync_after = true;
   }
   // the call's status word goes to a pinned host int (read by adorym_check, or below)
@@ -880,7 +926,7 @@ int adorym_loss_grad_ext(adorym_ctx* ctx, const adorym_problem* p, int obj_id, c
   if (!out) return run_call(ctx, p, obj_id, probe, pos, I_meas, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                             true);
   return run_call(ctx, p, obj_id, probe, pos, I_meas, out->loss, out->g_delta, out->g_beta, out->g_probe, out->g_pos,
-                  out->I_out, true, out->g_nf, out->g_gaps);
+                  out->I_out, true, out->g_nf, out->g_gaps, out->g_offset);
 }
 
 }  // extern "C"

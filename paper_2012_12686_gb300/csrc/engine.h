@@ -30,6 +30,7 @@ struct Plan {
   bool far = true, tomo = false, adj = false;
   bool want_obj = false, want_probe = false, want_pos = false, want_loss = false, want_nf = false;
   bool gaps = false, want_gaps = false;   // variable slice spacing / its gradient
+  bool want_offset = false;                // far field: per-angle position offset gradient
   bool pipe = false;   // shared-memory path: two-CTA clusters (adjoint + segment recompute)
   int helpers = 0;     // shared-memory path: recompute-helper CTAs on SMs the batch leaves idle
   size_t NN = 0;
@@ -41,6 +42,7 @@ struct Plan {
   size_t off_hseg = 0, off_hctl = 0;   // helper segment store; helper control words (hnext, hprog, hflag)
   size_t off_status = 0;   // int device status word of the call (ADORYM_STATUS_* bits)
   size_t off_spck = 0, off_spseg = 0, off_gapp = 0, off_s_ggap = 0;   // slice-gap gradient
+  size_t off_posd = 0, off_s_goff = 0;   // FP64 position gradients [B][2]; staged offset gradient
   // staging for host-memory arguments
   size_t off_s_probe = 0, off_s_pos = 0, off_s_meas = 0, off_s_gprobe = 0, off_s_gpos = 0, off_s_iout = 0,
          off_s_gnf = 0;
@@ -61,6 +63,7 @@ struct CallPtrs {
   float* g_nf = nullptr;
   float* I_out = nullptr;
   float* g_gaps = nullptr;
+  float* g_offset = nullptr;   // far field: [2] per-angle position offset gradient (overwritten)
   // the measured intensities arrive on a side stream: the stream waits for this event before the
   // first kernel that reads them (the kernels before it overlap the copy); null when there is
   // nothing to wait for

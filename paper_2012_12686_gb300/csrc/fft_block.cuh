@@ -34,6 +34,27 @@
 
 namespace adorym {
 
+// Complex arithmetic.  With ADORYM_PACKED_F32X2 (default) the real and imaginary parts go through
+// the packed two-lane FP32 instructions of sm_100+ (__fadd2_rn, __fmul2_rn, __ffma2_rn): one
+// instruction per complex add, two per complex multiply, which halves the issue slots of the
+// butterflies.  Every lane rounds exactly as the scalar form does (a - b as fma(b, -1, a), and the
+// products in the same order: the cross term is rounded, then fused), so both forms give
+// bitwise the same results.
+#ifndef ADORYM_PACKED_F32X2
+#define ADORYM_PACKED_F32X2 1
+#endif
+#if ADORYM_PACKED_F32X2
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return __ffma2_rn(make_float2(a.x, a.x), b, __fmul2_rn(make_float2(a.y, a.y), make_float2(-b.y, b.x)));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return __ffma2_rn(a, make_float2(b.x, b.x), __fmul2_rn(make_float2(a.y, -a.x), make_float2(b.y, b.y)));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
+#else
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -43,8 +64,9 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
 }
-__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+#endif
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 
 // cos / sin of 2 pi q / 32 from the first-octant values cos(2 pi j / 32), j = 0..8, by symmetry
 struct Unit32 {
@@ -73,7 +95,11 @@ __device__ __forceinline__ float2 rot_const(float2 a) {
     constexpr int q = k * (32 / R);
     constexpr float c = (float)Unit32::cosq(q);
     constexpr float s = S > 0 ? (float)Unit32::sinq(q) : -(float)Unit32::sinq(q);
+#if ADORYM_PACKED_F32X2
+    return __ffma2_rn(make_float2(a.x, a.x), make_float2(c, s), __fmul2_rn(make_float2(a.y, a.y), make_float2(-s, c)));
+#else
     return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
+#endif
   }
 }
 
@@ -135,10 +161,14 @@ struct Geo;
 // The spatial passes (S4/S1, radix N1) carry the global-memory traffic of the pointwise ops, so
 // N1 is the smaller radix where the two differ.
 #ifndef ADORYM_NT128
-#define ADORYM_NT128 1024
+#define ADORYM_NT128 512
+#endif
+// ADORYM_FOURPASS64: N = 64 fused kernels on the four-pass scheme of fft_block4.cuh (256 threads)
+#ifndef ADORYM_FOURPASS64
+#define ADORYM_FOURPASS64 0
 #endif
 #ifndef ADORYM_NT64
-#define ADORYM_NT64 512
+#define ADORYM_NT64 (ADORYM_FOURPASS64 ? 256 : 512)
 #endif
 template <> struct Geo<8>   { static constexpr int N1 = 4, N2 = 2,  NT = 64,  MINB = 8; };
 template <> struct Geo<16>  { static constexpr int N1 = 4, N2 = 4,  NT = 64,  MINB = 8; };

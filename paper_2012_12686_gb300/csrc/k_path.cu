@@ -76,6 +76,31 @@ __global__ void k_gap_final(const double* __restrict__ gapp, int B, int ngap, in
   }
 }
 
+// Per-angle position offset of ptychotomography (Sec. 2.3.2): one correction vector shifts every
+// position of an angle, so its gradient is the sum of that batch's position gradients.  One warp:
+// lane l adds positions l, l + 32, ... in FP64, then a fixed shuffle tree (deterministic).
+__global__ void k_offset_sum(const double* __restrict__ gposd, int B, float* __restrict__ g_off) {
+  double sy = 0.0, sx = 0.0;
+  for (int b = threadIdx.x; b < B; b += 32) {
+    sy += gposd[2 * (size_t)b];
+    sx += gposd[2 * (size_t)b + 1];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+  }
+  if (threadIdx.x == 0) {
+    g_off[0] = (float)sy;
+    g_off[1] = (float)sx;
+  }
+}
+
+cudaError_t launch_offset_sum(const double* gposd, int B, float* g_off, cudaStream_t s) {
+  (k_offset_sum<<<1, 32, 0, s>>>(gposd, B, g_off), note_launch());
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gap_final(const double* gapp, int B, int ngap, int parts, float* g_gap, cudaStream_t s) {
   (k_gap_final<<<1, 256, 0, s>>>(gapp, B, ngap, parts, g_gap), note_launch());
   return cudaGetLastError();

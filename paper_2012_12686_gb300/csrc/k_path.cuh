@@ -38,6 +38,7 @@
 #pragma once
 #include "numerics.cuh"
 #include "fft_block.cuh"
+#include "fft_block4.cuh"
 #include "kernels.cuh"
 
 namespace adorym {
@@ -85,30 +86,32 @@ __device__ __forceinline__ void st_release_gpu(int* p, int v) {
 }
 
 // thread 0 of a position's CTA at segment s: take the segment (0 -> 3) or find it recomputed by a
-// helper.  Waits, bounded by about 2^28 cycles, only while a helper holds it (1).  True: the
-// helper's slices are complete and visible; false: the position recomputes the segment itself.
-__device__ __forceinline__ bool take_segment(int* flag) {
+// helper.  Waits, bounded by `limit` cycles (about 2^28 by default), only while a helper holds it
+// (1).  True: the helper's slices are complete and visible; false: the position recomputes the
+// segment itself.
+__device__ __forceinline__ bool take_segment(int* flag, long long limit) {
   int st = atomicCAS(flag, 0, 3);
   if (st == 1) {
     const long long t0 = clock64();
     do {
       __nanosleep(256);
       st = ld_acquire_gpu(flag);
-    } while (st == 1 && clock64() - t0 < (1ll << 28));
+    } while (st == 1 && clock64() - t0 < limit);
   }
   __threadfence();
   return st == 2;
 }
 
 // thread 0 of a helper: wait until the position's forward has written `need` checkpoints (1);
-// 0 when the position took the segment meanwhile; -1 after about 2^24 cycles (the position is
-// not progressing, e.g. not resident: the helper stops so that it does not hold the SM)
-__device__ __forceinline__ int wait_checkpoints(const int* prog, int need, const int* flag) {
+// 0 when the position took the segment meanwhile; -1 after `limit` cycles (about 2^24 by default:
+// the position is not progressing, e.g. not resident, and the helper stops so that it does not
+// hold the SM)
+__device__ __forceinline__ int wait_checkpoints(const int* prog, int need, const int* flag, long long limit) {
   const long long t0 = clock64();
   for (;;) {
     if (ld_acquire_gpu(prog) >= need) return 1;
     if (*reinterpret_cast<const volatile int*>(flag) != 0) return 0;
-    if (clock64() - t0 > (1ll << 24)) return -1;
+    if (clock64() - t0 > limit) return -1;
     __nanosleep(512);
   }
 }
@@ -121,10 +124,11 @@ template <int N, int FAR, bool GAP, bool PIPE, bool HELP = false>
 __device__ __forceinline__ void path_body(const PathArgs& a) {
   static_assert(!(HELP && (GAP || PIPE)), "recompute helpers serve the plain one-CTA form only");
   using F = Field<N>;
-  constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD, NT = F::NT;
+  using X = PathFFT<N>;
+  constexpr int CY = X::CY, YS = X::YS, RX = X::RX, KXS = X::KXS, LD = F::LD, NT = F::NT;
   constexpr size_t NN = (size_t)N * N;
-  using V1 = float2[N1];
-  using V2 = float2[N2];
+  using V1 = float2[CY];
+  using V2 = float2[RX];
   extern __shared__ float2 sm[];
   float2* A = sm;
   float2* tw = A + N * LD;             // F::TW_ENTRIES twiddles (tw, then the per-stage tables)
@@ -175,10 +179,10 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
     if (interior) {
       const float2* p = a.T + voff(j, t, x);
 #pragma unroll
-      for (int k = 0; k < N1; ++k) pa[k] = __ldg(p + (size_t)(N2 * k) * Lx);
+      for (int k = 0; k < CY; ++k) pa[k] = __ldg(p + (size_t)(YS * k) * Lx);
     } else {
 #pragma unroll
-      for (int k = 0; k < N1; ++k) pa[k] = tload(j, N2 * k + t, x);
+      for (int k = 0; k < CY; ++k) pa[k] = tload(j, YS * k + t, x);
     }
   };
   auto pre_T = [&](int j) {
@@ -189,20 +193,18 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
   // spec_out keeps F[psi_{gapj+1}] / N^2 for the slice-gap gradient, spec_in (adjoint)
   // accumulates dL/dc_gap = -pi sum |f|^2 Im(conj(F[psibar]) F[psi]) into gapp
   auto propagate_tail = [&](bool adjoint, int gapj, float2* spec_out, const float2* spec_in) {
-    pass_c23<N, false, -1>(A, tw);
-    __syncthreads();
-    pass_r14<N, true, -1>(A, tw);
+    X::template fwd_pair<-1>(A, tw);
     __syncthreads();
     float gs = 0.f;
     if constexpr (GAP) {
       const float2* hyp = a.hyj + (size_t)gapj * N;
       const float2* hxp = a.hxj + (size_t)gapj * N;
-      pass_r23<N, -1, +1>(A, tw, [&](V2& v, int ky, int t) {
+      X::template r23<-1, +1>(A, tw, [&](V2& v, int ky, int t) {
         const float2 h = hyp[ky];
         const float fy = freqf1(ky, N);
 #pragma unroll
-        for (int i = 0; i < N2; ++i) {
-          const int kx = t + N1 * i;
+        for (int i = 0; i < RX; ++i) {
+          const int kx = t + KXS * i;
           const float2 H = cmul(h, hxp[kx]);
           if (!adjoint) {
             v[i] = cmul(v[i], H);
@@ -217,22 +219,20 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
         }
       });
     } else if (adjoint) {
-      pass_r23<N, -1, +1>(A, tw, [&](V2& v, int ky, int t) {
+      X::template r23<-1, +1>(A, tw, [&](V2& v, int ky, int t) {
         const float2 h = hy[ky];
 #pragma unroll
-        for (int i = 0; i < N2; ++i) v[i] = cmulc(cmulc(v[i], h), hx[t + N1 * i]);
+        for (int i = 0; i < RX; ++i) v[i] = cmulc(cmulc(v[i], h), hx[t + KXS * i]);
       });
     } else {
-      pass_r23<N, -1, +1>(A, tw, [&](V2& v, int ky, int t) {
+      X::template r23<-1, +1>(A, tw, [&](V2& v, int ky, int t) {
         const float2 h = hy[ky];
 #pragma unroll
-        for (int i = 0; i < N2; ++i) v[i] = cmul(cmul(v[i], h), hx[t + N1 * i]);
+        for (int i = 0; i < RX; ++i) v[i] = cmul(cmul(v[i], h), hx[t + KXS * i]);
       });
     }
     __syncthreads();
-    pass_r14<N, false, +1>(A, tw);
-    __syncthreads();
-    pass_c23<N, true, +1>(A, tw);
+    X::template inv_pair<+1>(A, tw);
     __syncthreads();
     if constexpr (GAP) {
       if (adjoint && spec_in) {
@@ -281,8 +281,8 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
     auto fwd_op = [&](int j, bool from_pb) {
       return [&, j, from_pb](V1& v, V1& pa, V1& pb, int x, int t) {
 #pragma unroll
-        for (int k = 0; k < N1; ++k) {
-          const int y = N2 * k + t;
+        for (int k = 0; k < CY; ++k) {
+          const int y = YS * k + t;
           if (from_pb) v[k] = pb[k];
           if (adj) {
             if (j % cp == 0) ck[(size_t)(j / cp) * NN + y * N + x] = v[k];
@@ -295,18 +295,16 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
     if (FAR) {
       // psi_0 = IDFT_-(P^ ramp), built in Fourier space at the R23 layout
       const float2* ph = a.phat + (size_t)m * NN;
-      pass_r23<N, 0, +1>(A, tw, [&](V2& v, int ky, int t) {
+      X::template r23<0, +1>(A, tw, [&](V2& v, int ky, int t) {
         const float2 r = cscale(ry[ky], invNN);
 #pragma unroll
-        for (int i = 0; i < N2; ++i) {
-          const int kx = t + N1 * i;
+        for (int i = 0; i < RX; ++i) {
+          const int kx = t + KXS * i;
           v[i] = cmul(cmul(__ldg(&ph[ky * N + kx]), r), rx[kx]);
         }
       });
       __syncthreads();
-      pass_r14<N, false, +1>(A, tw);
-      __syncthreads();
-      pass_c23<N, true, +1>(A, tw);
+      X::template inv_pair<+1>(A, tw);
       __syncthreads();
     }
     for (int j = 0; j < L; ++j) {
@@ -315,15 +313,15 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
         // the illumination enters through pb; near field always starts its last transform with DFT_-
         const float2* pr = a.probe + (size_t)m * NN;
         auto T0 = pre_T(0);
-        pass_c14<N, 0, -1, false, true>(A, tw, [&](V1& pa, V1& pb, int x, int t) {
+        X::template c14<0, -1, false, true>(A, tw, [&](V1& pa, V1& pb, int x, int t) {
           T0(pa, pb, x, t);
 #pragma unroll
-          for (int k = 0; k < N1; ++k) pb[k] = __ldg(&pr[(N2 * k + t) * N + x]);
+          for (int k = 0; k < CY; ++k) pb[k] = __ldg(&pr[(YS * k + t) * N + x]);
         }, fwd_op(0, true));
       } else if (FAR && last) {
-        pass_c14<N, +1, +1, true, true>(A, tw, pre_T(j), fwd_op(j, false));
+        X::template c14<+1, +1, true, true>(A, tw, pre_T(j), fwd_op(j, false));
       } else {
-        pass_c14<N, +1, -1, true, true>(A, tw, pre_T(j), fwd_op(j, false));
+        X::template c14<+1, -1, true, true>(A, tw, pre_T(j), fwd_op(j, false));
       }
       __syncthreads();
       if constexpr (HELP) {
@@ -339,15 +337,13 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
       }
       if (FAR) {
         // Psi = (1/N) DFT_+[phi]; keep Psi, accumulate I over modes
-        pass_c23<N, false, +1>(A, tw);
-        __syncthreads();
-        pass_r14<N, true, +1>(A, tw);
+        X::template fwd_pair<+1>(A, tw);
         __syncthreads();
         float2* fm = a.far + ((size_t)b * M + m) * NN;
-        pass_r23<N, +1, 0>(A, tw, [&](V2& v, int ky, int t) {
+        X::template r23<+1, 0>(A, tw, [&](V2& v, int ky, int t) {
 #pragma unroll
-          for (int i = 0; i < N2; ++i) {
-            const int p = ky * N + t + N1 * i;
+          for (int i = 0; i < RX; ++i) {
+            const int p = ky * N + t + KXS * i;
             const float2 P = cscale(v[i], invN);
             fm[p] = P;
             const float I = fmaf(P.x, P.x, P.y * P.y);
@@ -357,14 +353,12 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
         __syncthreads();
       } else {
         // Phi = DFT_-[phi] kept at slot n_dist; then Psi_d = IDFT_-{Phi G_d} per distance
-        pass_c23<N, false, -1>(A, tw);
-        __syncthreads();
-        pass_r14<N, true, -1>(A, tw);
+        X::template fwd_pair<-1>(A, tw);
         __syncthreads();
         float2* Phi = a.far + (((size_t)b * (nd + 1) + nd) * M + m) * NN;
-        pass_r23<N, -1, 0>(A, tw, [&](V2& v, int ky, int t) {
+        X::template r23<-1, 0>(A, tw, [&](V2& v, int ky, int t) {
 #pragma unroll
-          for (int i = 0; i < N2; ++i) Phi[ky * N + t + N1 * i] = v[i];
+          for (int i = 0; i < RX; ++i) Phi[ky * N + t + KXS * i] = v[i];
         });
         __syncthreads();
         for (int d = 0; d < nd; ++d) {
@@ -373,25 +367,23 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
           ramp_table(rx, sd[1], N, NT);
           __syncthreads();
           const float2* hd = a.hd + (size_t)d * N;
-          pass_r23<N, 0, +1>(A, tw, [&](V2& v, int ky, int t) {
+          X::template r23<0, +1>(A, tw, [&](V2& v, int ky, int t) {
             const float2 gy = cscale(cmul(__ldg(&hd[ky]), ry[ky]), invNN);
 #pragma unroll
-            for (int i = 0; i < N2; ++i) {
-              const int kx = t + N1 * i;
+            for (int i = 0; i < RX; ++i) {
+              const int kx = t + KXS * i;
               v[i] = cmul(cmul(Phi[ky * N + kx], gy), cmul(__ldg(&hd[kx]), rx[kx]));
             }
           });
           __syncthreads();
-          pass_r14<N, false, +1>(A, tw);
-          __syncthreads();
-          pass_c23<N, true, +1>(A, tw);
+          X::template inv_pair<+1>(A, tw);
           __syncthreads();
           float2* fd = a.far + (((size_t)b * (nd + 1) + d) * M + m) * NN;
           float* gId = gI_b + (size_t)d * NN;
-          pass_c14<N, +1, 0, true, false>(A, tw, NoPre(), [&](V1& v, V1&, V1&, int x, int t) {
+          X::template c14<+1, 0, true, false>(A, tw, NoPre(), [&](V1& v, V1&, V1&, int x, int t) {
 #pragma unroll
-            for (int k = 0; k < N1; ++k) {
-              const int p = (N2 * k + t) * N + x;
+            for (int k = 0; k < CY; ++k) {
+              const int p = (YS * k + t) * N + x;
               fd[p] = v[k];
               const float I = fmaf(v[k].x, v[k].x, v[k].y * v[k].y);
               gId[p] = (m == 0) ? I : gId[p] + I;
@@ -463,19 +455,19 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
       for (int j = j0; j < j1; ++j) {
         if (j == j0) {
           auto T0 = pre_T(j);
-          pass_c14<N, 0, -1, false, true>(A, tw, [&](V1& pa, V1& pb, int x, int t) {
+          X::template c14<0, -1, false, true>(A, tw, [&](V1& pa, V1& pb, int x, int t) {
             T0(pa, pb, x, t);
 #pragma unroll
-            for (int k = 0; k < N1; ++k) pb[k] = __ldcg(ck + (size_t)s * NN + (N2 * k + t) * N + x);
+            for (int k = 0; k < CY; ++k) pb[k] = __ldcg(ck + (size_t)s * NN + (YS * k + t) * N + x);
           }, [&](V1& v, V1& pa, V1& pb, int, int) {
 #pragma unroll
-            for (int k = 0; k < N1; ++k) v[k] = cmul(pb[k], pa[k]);
+            for (int k = 0; k < CY; ++k) v[k] = cmul(pb[k], pa[k]);
           });
         } else {
-          pass_c14<N, +1, -1, true, true>(A, tw, pre_T(j), [&, j](V1& v, V1& pa, V1&, int x, int t) {
+          X::template c14<+1, -1, true, true>(A, tw, pre_T(j), [&, j](V1& v, V1& pa, V1&, int x, int t) {
 #pragma unroll
-            for (int k = 0; k < N1; ++k) {
-              sg[(size_t)(j - j0) * NN + (N2 * k + t) * N + x] = v[k];
+            for (int k = 0; k < CY; ++k) {
+              sg[(size_t)(j - j0) * NN + (YS * k + t) * N + x] = v[k];
               v[k] = cmul(v[k], pa[k]);
             }
           });
@@ -483,9 +475,9 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
         __syncthreads();
         propagate_tail(false, j, want_gap ? spsg + (size_t)(j + 1 - j0) * NN : nullptr, nullptr);
       }
-      pass_c14<N, +1, 0, true, false>(A, tw, NoPre(), [&](V1& v, V1&, V1&, int x, int t) {
+      X::template c14<+1, 0, true, false>(A, tw, NoPre(), [&](V1& v, V1&, V1&, int x, int t) {
 #pragma unroll
-        for (int k = 0; k < N1; ++k) sg[(size_t)(j1 - j0) * NN + (N2 * k + t) * N + x] = v[k];
+        for (int k = 0; k < CY; ++k) sg[(size_t)(j1 - j0) * NN + (YS * k + t) * N + x] = v[k];
       });
       __syncthreads();
     };
@@ -505,17 +497,15 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
       // phibar_{L-1} = (1/N) DFT_-[2 gI Psi]
       const float2* fm = a.far + ((size_t)b * M + m) * NN;
       const float sc = 2.0f * invN;
-      pass_r23<N, 0, -1>(A, tw, [&](V2& v, int ky, int t) {
+      X::template r23<0, -1>(A, tw, [&](V2& v, int ky, int t) {
 #pragma unroll
-        for (int i = 0; i < N2; ++i) {
-          const int p = ky * N + t + N1 * i;
+        for (int i = 0; i < RX; ++i) {
+          const int p = ky * N + t + KXS * i;
           v[i] = cscale(fm[p], sc * gI_b[p]);
         }
       });
       __syncthreads();
-      pass_r14<N, false, -1>(A, tw);
-      __syncthreads();
-      pass_c23<N, true, -1>(A, tw);
+      X::template inv_pair<-1>(A, tw);
       __syncthreads();
     } else {
       const float2* Phi = a.far + (((size_t)b * (nd + 1) + nd) * M + m) * NN;
@@ -528,30 +518,28 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
         const float* gId = gI_b + (size_t)d * NN;
         __syncthreads();
         // Q_d = DFT_-[2 gI_d Psi_d]
-        pass_c14<N, 0, -1, false, true>(A, tw, [&](V1& pa, V1& pb, int x, int t) {
+        X::template c14<0, -1, false, true>(A, tw, [&](V1& pa, V1& pb, int x, int t) {
 #pragma unroll
-          for (int k = 0; k < N1; ++k) {
-            const int p = (N2 * k + t) * N + x;
+          for (int k = 0; k < CY; ++k) {
+            const int p = (YS * k + t) * N + x;
             pa[k] = fd[p];
             pb[k].x = gId[p];
           }
         }, [&](V1& v, V1& pa, V1& pb, int, int) {
 #pragma unroll
-          for (int k = 0; k < N1; ++k) v[k] = cscale(pa[k], 2.0f * pb[k].x);
+          for (int k = 0; k < CY; ++k) v[k] = cscale(pa[k], 2.0f * pb[k].x);
         });
         __syncthreads();
-        pass_c23<N, false, -1>(A, tw);
-        __syncthreads();
-        pass_r14<N, true, -1>(A, tw);
+        X::template fwd_pair<-1>(A, tw);
         __syncthreads();
         const float2* hd = a.hd + (size_t)d * N;
-        pass_r23<N, -1, 0>(A, tw, [&](V2& v, int ky, int t) {
+        X::template r23<-1, 0>(A, tw, [&](V2& v, int ky, int t) {
           const float2 gy = cmul(__ldg(&hd[ky]), ry[ky]);
           const float fyk = freqf1(ky, N);
           float ay = 0.f, ax = 0.f, an = 0.f;
 #pragma unroll
-          for (int i = 0; i < N2; ++i) {
-            const int kx = t + N1 * i, p = ky * N + kx;
+          for (int i = 0; i < RX; ++i) {
+            const int kx = t + KXS * i, p = ky * N + kx;
             const float2 G = cmul(gy, cmul(__ldg(&hd[kx]), rx[kx]));
             const float2 base = cmul(cconj(v[i]), cmul(Phi[p], G));
             const float fxk = freqf1(kx, N);
@@ -568,14 +556,12 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
         __syncthreads();
       }
       // phibar_{L-1} = IDFT_-{sum_d conj(G_d) Q_d}
-      pass_r23<N, 0, +1>(A, tw, [&](V2& v, int ky, int t) {
+      X::template r23<0, +1>(A, tw, [&](V2& v, int ky, int t) {
 #pragma unroll
-        for (int i = 0; i < N2; ++i) v[i] = cscale(fb[ky * N + t + N1 * i], invNN);
+        for (int i = 0; i < RX; ++i) v[i] = cscale(fb[ky * N + t + KXS * i], invNN);
       });
       __syncthreads();
-      pass_r14<N, false, +1>(A, tw);
-      __syncthreads();
-      pass_c23<N, true, +1>(A, tw);
+      X::template inv_pair<+1>(A, tw);
       __syncthreads();
     }
 
@@ -588,7 +574,7 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
         if constexpr (HELP) {
           if (a.helpers) {
             bool done = false;
-            if (threadIdx.x == 0) done = take_segment(a.hflag + ((size_t)b * M + m) * ncp + s);
+            if (threadIdx.x == 0) done = take_segment(a.hflag + ((size_t)b * M + m) * ncp + s, a.wait_seg);
             // the vote is CTA-uniform; the lane-0 broadcast lets the compiler treat the branch
             // below as warp-uniform (a plain vote result cost ~6 % through extra spills)
             from_helper = __shfl_sync(0xffffffffu, __syncthreads_or(done), 0) != 0;
@@ -613,24 +599,24 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
           const float2* src = (j == j0) ? ck + (size_t)s * NN : seg_j + (size_t)(j - j0) * NN;
           tloads(pa, j, x, t);
 #pragma unroll
-          for (int k = 0; k < N1; ++k) pb[k] = __ldcg(src + (N2 * k + t) * N + x);   // L2: written by the partner CTA
+          for (int k = 0; k < CY; ++k) pb[k] = __ldcg(src + (YS * k + t) * N + x);   // L2: written by the partner CTA
         };
         float2* q0 = (!FAR && first && a.qacc) ? a.qacc + ((size_t)b * M + m) * NN : nullptr;
         auto op = [&, j, q0](V1& v, V1& pa, V1& pb, int x, int t) {
           const size_t o0 = interior ? voff(j, t, x) : 0;
 #pragma unroll
-          for (int k = 0; k < N1; ++k) {
-            const int y = N2 * k + t;
+          for (int k = 0; k < CY; ++k) {
+            const int y = YS * k + t;
             const float2 pbar = cmulc(v[k], pa[k]);     // psibar_j = conj(T_j) phibar_j
             if (!FAR && a.gdf) {
               // near field, one mode: this thread owns voxel (b L + j, y, x) for the whole call
               const float2 z = cmulc(pbar, pb[k]);
-              const size_t o = voff(j, t, x) + (size_t)(N2 * k) * Lx;
+              const size_t o = voff(j, t, x) + (size_t)(YS * k) * Lx;
               a.gdf[o] += kdz * z.y;
               a.gbf[o] -= kdz * z.x;
             } else if (want_obj) {
               const float2 z = cmulc(pbar, pb[k]);      // psibar conj(psi)
-              size_t o = o0 + (size_t)(N2 * k) * Lx;
+              size_t o = o0 + (size_t)(YS * k) * Lx;
               bool in = interior;
               if (!interior) {
                 const int gy = p0y + y, gx = p0x + x, gz = FAR ? j : b * L + j;
@@ -646,9 +632,9 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
             if (q0) q0[y * N + x] = pbar;               // near field: illumination gradient
           }
         };
-        if (FAR && j == L - 1) pass_c14<N, -1, -1, true, true>(A, tw, pre, op);
-        else if (!FAR && first) pass_c14<N, +1, 0, true, false>(A, tw, pre, op);
-        else pass_c14<N, +1, -1, true, true>(A, tw, pre, op);
+        if (FAR && j == L - 1) X::template c14<-1, -1, true, true>(A, tw, pre, op);
+        else if (!FAR && first) X::template c14<+1, 0, true, false>(A, tw, pre, op);
+        else X::template c14<+1, -1, true, true>(A, tw, pre, op);
         __syncthreads();
         if (!first) {
           const float2* sp_in = !want_gap ? nullptr : (j == j0) ? spck + (size_t)s * NN : spsg + (size_t)(j - j0) * NN;
@@ -657,19 +643,17 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
         }
         if (!FAR) continue;
         // far field, j = 0: Q = DFT_-[psibar_0] -> probe and position gradients
-        pass_c23<N, false, -1>(A, tw);
-        __syncthreads();
-        pass_r14<N, true, -1>(A, tw);
+        X::template fwd_pair<-1>(A, tw);
         __syncthreads();
         const float2* ph = a.phat + (size_t)m * NN;
         float2* q = a.qacc ? a.qacc + ((size_t)b * M + m) * NN : nullptr;
-        pass_r23<N, -1, 0>(A, tw, [&](V2& v, int ky, int t) {
+        X::template r23<-1, 0>(A, tw, [&](V2& v, int ky, int t) {
           const float2 r_y = ry[ky];
           const float fyk = freqf1(ky, N);
           float ay = 0.f, ax = 0.f;
 #pragma unroll
-          for (int i = 0; i < N2; ++i) {
-            const int kx = t + N1 * i, p = ky * N + kx;
+          for (int i = 0; i < RX; ++i) {
+            const int kx = t + KXS * i, p = ky * N + kx;
             const float2 r = cmul(r_y, rx[kx]);
             const float2 base = cmul(cconj(v[i]), cmul(__ldg(&ph[p]), r));
             ay += fyk * base.y;
@@ -684,7 +668,7 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
       if (PIPE) cluster_barrier();   // segment s consumed; rank 1 may overwrite its slot
     }
   }
-  if (rank == 0 && (a.gpos || a.gnf)) {
+  if (rank == 0 && (a.gpos || a.gposd || a.gnf)) {
     // dL/ds_a = (2 pi / N^2) sum f_a Im(base);  dL/dN_F = (pi / (N_F^2 N^2)) sum |f|^2 Im(base)
     const double pi = 3.14159265358979323846, sc = 2.0 * pi / (double)NN;
     for (int d = 0; d < nd; ++d) {
@@ -695,6 +679,10 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
         if (a.gpos) {
           a.gpos[((size_t)b * nd + d) * 2] = (float)(sc * gy);
           a.gpos[((size_t)b * nd + d) * 2 + 1] = (float)(sc * gx);
+        }
+        if (FAR && a.gposd) {
+          a.gposd[2 * (size_t)b] = sc * gy;
+          a.gposd[2 * (size_t)b + 1] = sc * gx;
         }
         if (!FAR && a.gnf) a.gnf[(size_t)b * nd + d] = (float)(pi * gn / (a.nf[d] * a.nf[d] * (double)NN));
       }
@@ -710,10 +698,11 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
 template <int N, int FAR>
 __device__ __forceinline__ void helper_body(const PathArgs& a) {
   using F = Field<N>;
-  constexpr int N1 = F::N1, N2 = F::N2, LD = F::LD, NT = F::NT;
+  using X = PathFFT<N>;
+  constexpr int CY = X::CY, YS = X::YS, RX = X::RX, KXS = X::KXS, LD = F::LD, NT = F::NT;
   constexpr size_t NN = (size_t)N * N;
-  using V1 = float2[N1];
-  using V2 = float2[N2];
+  using V1 = float2[CY];
+  using V2 = float2[RX];
   extern __shared__ float2 sm[];
   float2* A = sm;
   float2* tw = A + N * LD;
@@ -734,7 +723,7 @@ __device__ __forceinline__ void helper_body(const PathArgs& a) {
         const int s = tk / MB, m = (tk - s * MB) / B, bb = tk - s * MB - m * B;
         if (min(s * cp + cp, L) - 1 <= s * cp) continue;   // one-slice segment: nothing to recompute
         int* fl = a.hflag + ((size_t)bb * M + m) * ncp + s;
-        const int w = wait_checkpoints(a.hprog + (size_t)bb * M + m, s + 1, fl);
+        const int w = wait_checkpoints(a.hprog + (size_t)bb * M + m, s + 1, fl, a.wait_ckpt);
         if (w < 0) break;
         if (w > 0 && atomicCAS(fl, 0, 1) == 0) {
           got = tk;
@@ -755,11 +744,11 @@ __device__ __forceinline__ void helper_body(const PathArgs& a) {
       if (interior) {
         const float2* p = a.T + (gz * Ly + (p0y + t)) * Lx + (p0x + x);
 #pragma unroll
-        for (int k = 0; k < N1; ++k) pa[k] = __ldg(p + (size_t)(N2 * k) * Lx);
+        for (int k = 0; k < CY; ++k) pa[k] = __ldg(p + (size_t)(YS * k) * Lx);
       } else {
 #pragma unroll
-        for (int k = 0; k < N1; ++k) {
-          const int gy = p0y + N2 * k + t, gx = p0x + x;
+        for (int k = 0; k < CY; ++k) {
+          const int gy = p0y + YS * k + t, gx = p0x + x;
           pa[k] = (gy >= 0 && gy < Ly && gx >= 0 && gx < Lx) ? __ldg(a.T + (gz * Ly + gy) * Lx + gx)
                                                              : make_float2(1.f, 0.f);
         }
@@ -771,44 +760,40 @@ __device__ __forceinline__ void helper_body(const PathArgs& a) {
     const int j0 = s * cp, j1 = min(j0 + cp, L) - 1;
     for (int j = j0; j < j1; ++j) {
       if (j == j0) {
-        pass_c14<N, 0, -1, false, true>(A, tw, [&](V1& pa, V1& pb, int x, int t) {
+        X::template c14<0, -1, false, true>(A, tw, [&](V1& pa, V1& pb, int x, int t) {
           tloads(pa, j, x, t);
 #pragma unroll
-          for (int k = 0; k < N1; ++k) pb[k] = __ldcg(ck + (N2 * k + t) * N + x);
+          for (int k = 0; k < CY; ++k) pb[k] = __ldcg(ck + (YS * k + t) * N + x);
         }, [&](V1& v, V1& pa, V1& pb, int, int) {
 #pragma unroll
-          for (int k = 0; k < N1; ++k) v[k] = cmul(pb[k], pa[k]);
+          for (int k = 0; k < CY; ++k) v[k] = cmul(pb[k], pa[k]);
         });
       } else {
-        pass_c14<N, +1, -1, true, true>(A, tw, [&](V1& pa, V1&, int x, int t) { tloads(pa, j, x, t); },
+        X::template c14<+1, -1, true, true>(A, tw, [&](V1& pa, V1&, int x, int t) { tloads(pa, j, x, t); },
                                         [&](V1& v, V1& pa, V1&, int x, int t) {
 #pragma unroll
-          for (int k = 0; k < N1; ++k) {
-            sg[(size_t)(j - j0) * NN + (N2 * k + t) * N + x] = v[k];
+          for (int k = 0; k < CY; ++k) {
+            sg[(size_t)(j - j0) * NN + (YS * k + t) * N + x] = v[k];
             v[k] = cmul(v[k], pa[k]);
           }
         });
       }
       __syncthreads();
       // propagation tail: C2, R1, R23 (H), R4, C3
-      pass_c23<N, false, -1>(A, tw);
+      X::template fwd_pair<-1>(A, tw);
       __syncthreads();
-      pass_r14<N, true, -1>(A, tw);
-      __syncthreads();
-      pass_r23<N, -1, +1>(A, tw, [&](V2& v, int ky, int t) {
+      X::template r23<-1, +1>(A, tw, [&](V2& v, int ky, int t) {
         const float2 h = hy[ky];
 #pragma unroll
-        for (int i = 0; i < N2; ++i) v[i] = cmul(cmul(v[i], h), hx[t + N1 * i]);
+        for (int i = 0; i < RX; ++i) v[i] = cmul(cmul(v[i], h), hx[t + KXS * i]);
       });
       __syncthreads();
-      pass_r14<N, false, +1>(A, tw);
-      __syncthreads();
-      pass_c23<N, true, +1>(A, tw);
+      X::template inv_pair<+1>(A, tw);
       __syncthreads();
     }
-    pass_c14<N, +1, 0, true, false>(A, tw, NoPre(), [&](V1& v, V1&, V1&, int x, int t) {
+    X::template c14<+1, 0, true, false>(A, tw, NoPre(), [&](V1& v, V1&, V1&, int x, int t) {
 #pragma unroll
-      for (int k = 0; k < N1; ++k) sg[(size_t)(j1 - j0) * NN + (N2 * k + t) * N + x] = v[k];
+      for (int k = 0; k < CY; ++k) sg[(size_t)(j1 - j0) * NN + (YS * k + t) * N + x] = v[k];
     });
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -14,6 +14,8 @@ namespace adorym {
 
 __device__ __forceinline__ float sgn(float v) { return (v > 0.f) - (v < 0.f); }
 
+// One CTA per volume row (z, y) at a time (grid-stride over rows), threads along x: coalesced
+// loads, row and plane neighbours from L1/L2, and no per-voxel 64-bit index division.
 template <bool TV>
 __global__ void __launch_bounds__(256) k_regularize(const float* __restrict__ d, const float* __restrict__ b,
                                                     const float* __restrict__ wd, const float* __restrict__ wb,
@@ -21,36 +23,40 @@ __global__ void __launch_bounds__(256) k_regularize(const float* __restrict__ d,
                                                     float invNo, float* __restrict__ gd, float* __restrict__ gb,
                                                     double* __restrict__ part) {
   __shared__ double red[8];
-  const size_t n = (size_t)Lz * Ly * Lx;
   const size_t sy = Lx, sz = (size_t)Lx * Ly;
+  const int rows = Ly * Lz;
   Kahan acc;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % Lx), y = (int)((i / Lx) % Ly), z = (int)(i / sz);
-    const float vd = d[i], vb = b[i];
-    const float w1 = wd ? wd[i] : 1.f, w2 = wb ? wb[i] : 1.f;
-    float term = ad * w1 * fabsf(vd) + ab * w2 * fabsf(vb);
-    float g1 = ad * w1 * sgn(vd), g2 = ab * w2 * sgn(vb);
-    if (TV) {
-      const int pos[3] = {x, y, z}, lim[3] = {Lx, Ly, Lz};
-      const size_t st[3] = {1, sy, sz};
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int z = r / Ly, y = r - z * Ly;
+    const size_t base = (size_t)r * Lx;
+    for (int x = threadIdx.x; x < Lx; x += blockDim.x) {
+      const size_t i = base + x;
+      const float vd = d[i], vb = b[i];
+      const float w1 = wd ? wd[i] : 1.f, w2 = wb ? wb[i] : 1.f;
+      float term = ad * w1 * fabsf(vd) + ab * w2 * fabsf(vb);
+      float g1 = ad * w1 * sgn(vd), g2 = ab * w2 * sgn(vb);
+      if (TV) {
+        const int pos[3] = {x, y, z}, lim[3] = {Lx, Ly, Lz};
+        const size_t st[3] = {1, sy, sz};
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (pos[a] + 1 < lim[a]) {
-          const float fd = d[i + st[a]] - vd, fb = b[i + st[a]] - vb;
-          term += gam * (fabsf(fd) + fabsf(fb));
-          g1 -= gam * sgn(fd);
-          g2 -= gam * sgn(fb);
-        }
-        if (pos[a] > 0) {
-          g1 += gam * sgn(vd - d[i - st[a]]);
-          g2 += gam * sgn(vb - b[i - st[a]]);
+        for (int a = 0; a < 3; ++a) {
+          if (pos[a] + 1 < lim[a]) {
+            const float fd = d[i + st[a]] - vd, fb = b[i + st[a]] - vb;
+            term += gam * (fabsf(fd) + fabsf(fb));
+            g1 -= gam * sgn(fd);
+            g2 -= gam * sgn(fb);
+          }
+          if (pos[a] > 0) {
+            g1 += gam * sgn(vd - d[i - st[a]]);
+            g2 += gam * sgn(vb - b[i - st[a]]);
+          }
         }
       }
-    }
-    acc.add(term);
-    if (gd) {
-      gd[i] += g1 * invNo;
-      gb[i] += g2 * invNo;
+      acc.add(term);
+      if (gd) {
+        gd[i] += g1 * invNo;
+        gb[i] += g2 * invNo;
+      }
     }
   }
   double v = acc.value();
@@ -107,11 +113,16 @@ static unsigned reg_grid(size_t n) { return (unsigned)std::min<size_t>((n + 255)
 
 int reg_parts(size_t n) { return (int)reg_grid(n); }
 
+// rows of the regularizer kernel: at most reg_grid(n) CTAs (its partial-sum array), one row each
+static unsigned reg_rows_grid(int Ly, int Lz, size_t n) {
+  return (unsigned)std::min<size_t>((size_t)Ly * Lz, reg_grid(n));
+}
+
 cudaError_t launch_regularize(const float* d, const float* b, const float* wd, const float* wb, int Lz, int Ly, int Lx,
                               double ad, double ab, double gam, float* gd, float* gb, double* part, double* loss,
                               cudaStream_t s) {
   const size_t n = (size_t)Lz * Ly * Lx;
-  const unsigned grid = reg_grid(n);
+  const unsigned grid = reg_rows_grid(Ly, Lz, n);
   const float invNo = (float)(1.0 / (double)n);
   if (gam != 0.0)
     (k_regularize<true><<<grid, 256, 0, s>>>(d, b, wd, wb, Lz, Ly, Lx, (float)ad, (float)ab, (float)gam, invNo, gd,

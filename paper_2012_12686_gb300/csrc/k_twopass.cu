@@ -151,11 +151,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
   return ok != 0;
 }
 
-// wait for phase `phase` of the barrier for at most ~2^31 clock cycles
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+// wait for phase `phase` of the barrier for at most `limit` clock cycles (about 2^31, a second,
+// by default); a negative limit reports a timeout without waiting (the test hook of the
+// timeout branch: the caller then waits for its copies with the default limit before it leaves)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, long long limit = 1LL << 31) {
+  if (limit < 0) return false;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, phase))
-    if (clock64() - t0 > (1LL << 31)) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 
@@ -474,7 +477,7 @@ __global__ void __launch_bounds__(NT2, 2) k_col(const __grid_constant__ TPArgs a
 #pragma unroll
         for (int yb = 0; yb < N / BOXR; ++yb) tma_load_2d(C + yb * BOXR * CW, &a.tm[which], p0, row0 + yb * BOXR, bar);
       }
-      const bool ok = __syncthreads_and(mbar_wait_bounded(bar, phase));
+      const bool ok = __syncthreads_and(mbar_wait_bounded(bar, phase, a.wait_tma));
       phase ^= 1u;
       if (!ok) {
         if (threadIdx.x == 0) set_status(a.status, STATUS_WAIT_TIMEOUT);
@@ -825,7 +828,7 @@ __global__ void __launch_bounds__(1024) k_final2(const TPArgs a, int nloss, int 
     const double s = block_sum2(acc, red);
     if (threadIdx.x == 0) *a.loss_out = s * a.inv_npix;
   }
-  if (a.posp && (a.gpos || a.gnf)) {
+  if (a.posp && (a.gpos || a.gposd || a.gnf)) {
     const double pi = 3.14159265358979323846, NN = (double)a.N * a.N, sc = 2.0 * pi / NN;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int q = w; q < a.B * a.nd; q += nw) {
@@ -846,6 +849,10 @@ __global__ void __launch_bounds__(1024) k_final2(const TPArgs a, int nloss, int 
         if (a.gpos) {
           a.gpos[2 * q] = (float)(sc * sy);
           a.gpos[2 * q + 1] = (float)(sc * sx);
+        }
+        if (a.gposd) {   // far field (one distance): q is the position
+          a.gposd[2 * q] = sc * sy;
+          a.gposd[2 * q + 1] = sc * sx;
         }
         if (a.gnf) {
           const double nf = a.nf[q % a.nd];

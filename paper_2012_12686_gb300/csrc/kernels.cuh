@@ -60,6 +60,8 @@ struct PathArgs {
   float* gdf;
   float* gbf;
   float* gpos;            // [B][2] or [B][n_dist][2] (overwritten), or null
+  double* gposd;          // far field: [B][2] the same position gradients in FP64 (for the
+                          // per-angle offset sum), or null
   float* gnf;             // near field: [B][n_dist] dL/dN_F (overwritten), or null
   double nf[4];           // near field: Fresnel numbers
   // sparse / variable multislice: per-gap propagator factors [L-1][N] (null: uniform hy, hx)
@@ -76,6 +78,8 @@ struct PathArgs {
   float2* spck;           // gap gradient: spectra F[psi_j] / N^2 of checkpoint slices [B][M][ncp][N*N]
   float2* spseg;          //               and of segment slices [B][M][cp][N*N]
   double* gapp;           // [B][L-1] per-position slice-gap gradient partials, or null
+  long long wait_seg;     // cycle limits of the helper protocol's waits (a position for a helper's
+  long long wait_ckpt;    // segment; a helper for a checkpoint): WaitLimits
 };
 
 // Arguments of the two-pass path (N >= 256): fields in HBM, one row and one column kernel per
@@ -111,6 +115,7 @@ struct TPArgs {
   float* gdf;              // direct FP32 object gradient (near field, one probe mode), else null
   float* gbf;
   float* gpos;
+  double* gposd;           // far field: [B][2] position gradients in FP64, or null
   float* gnf;
   double nf[4];
   const float2* hyj;       // variable slice spacing: per-gap propagator factors [L-1][N], or null
@@ -129,7 +134,17 @@ struct TPArgs {
   unsigned long long tm_rows[4];
   CUtensorMap tm[4];
   int m, j, s, j0, j1, d, buf;
+  long long wait_tma;      // cycle limit of a column tile's TMA wait (negative: report a timeout at once)
 };
+
+// Cycle limits of the bounded device-side waits, read by every later call when it is enqueued
+// (adorym_set_wait_limits changes them for tests of the fallback branches)
+struct WaitLimits {
+  long long seg = 1LL << 28;    // a position waiting for a segment a helper is recomputing
+  long long ckpt = 1LL << 24;   // a helper waiting for a position's checkpoint
+  long long tma = 1LL << 31;    // a column tile's TMA copy
+};
+WaitLimits wait_limits();
 
 // launchers (return cudaGetLastError())
 cudaError_t launch_probe_hat(int N, int M, const float2* probe, float2* phat, const float2* tw, cudaStream_t s);
@@ -143,6 +158,8 @@ cudaError_t prepare_path_pipe(int N, int farfield);
 // the instantiation with recompute helpers (a.helpers > 0), in its own translation unit
 cudaError_t launch_path_help(const PathArgs& a, int farfield, cudaStream_t s);
 cudaError_t prepare_path_help(int N, int farfield);
+// per-angle position offset (Sec. 2.3.2): g_off[a] = sum_b gposd[b][a] in FP64, fixed order
+cudaError_t launch_offset_sum(const double* gposd, int B, float* g_off, cudaStream_t s);
 // g_gap[j] = sum_b gapp[b][j][k] over b and k < parts (fixed order)
 cudaError_t launch_gap_final(const double* gapp, int B, int ngap, int parts, float* g_gap, cudaStream_t s);
 cudaError_t launch_probe_grad(int N, int M, int B, int farfield, const float2* qacc, float2* qsum, float2* g_probe,

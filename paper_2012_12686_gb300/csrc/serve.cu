@@ -1,14 +1,17 @@
 // Serving loop: continuous batching of loss/gradient requests over several CUDA streams.
 //
-// A request is queued by adorym_submit.  A worker thread admits queued requests in arrival
-// order whenever a slot (stream) is free and the request's workspace fits the footprint budget;
-// the workspace is carved from one device arena with a first-fit allocator.  Admitted requests
-// are recorded by stream capture into a CUDA graph and launched; the executable graph of each
-// (slot, problem shape) is kept and updated in place (cudaGraphExecUpdate) for the next
-// request of that shape, so steady-state launches cost one graph launch.  Completion is
-// detected with events; adorym_poll waits on a condition variable with a host-side timeout.
-// No device-side waiting is involved: a request that never completes shows up as ETIMEDOUT on
-// the host, never as a spinning kernel.
+// A request is queued by adorym_submit.  A worker thread admits queued requests whenever a slot
+// (stream) is free and the request's workspace fits the footprint budget; the workspace is carved
+// from one device arena with a first-fit allocator.  Admission is in arrival order, except that
+// when the oldest request does not fit, later requests that do fit may go ahead of it -- at most
+// kMaxOvertakes admissions past one waiting request, after which nothing overtakes it, so a large
+// request is never starved.  Admitted requests are recorded by stream capture into a CUDA graph
+// and launched; the executable graph of each (slot, problem shape) is kept and updated in place
+// (cudaGraphExecUpdate) for the next request of that shape, so steady-state launches cost one
+// graph launch.  Completion is event driven: each slot has a waiter thread blocked in
+// cudaEventSynchronize on the slot's blocking-sync event, which retires the request and wakes the
+// admission worker and adorym_poll (no polling loop).  No device-side waiting is involved: a
+// request that never completes shows up as ETIMEDOUT on the host, never as a spinning kernel.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -68,6 +71,8 @@ struct Arena {
   }
 };
 
+using Clock = std::chrono::steady_clock;
+
 struct Ticket {
   adorym_request req{};
   Plan plan;
@@ -76,6 +81,8 @@ struct Ticket {
   int slot = -1;
   size_t ws_off = 0;
   bool waited = false;
+  int overtaken = 0;      // admissions of later requests while this one waited at the head
+  Clock::time_point t_submit, t_admit, t_done;
 };
 
 struct Slot {
@@ -85,8 +92,13 @@ struct Slot {
                           // only on bad input; zeroed by the host before each launch)
   int* status_dev = nullptr;
   uint64_t ticket = 0;    // 0 = free
+  bool launched = false;  // the ticket's graph and completion event are enqueued (waiter may wait)
   std::map<std::string, cudaGraphExec_t> graphs;
+  std::thread waiter;     // blocks on `done` and retires the slot's ticket
 };
+
+// admissions of later requests allowed past a request that waits at the head of the queue
+constexpr int kMaxOvertakes = 8;
 
 struct Serve {
   int nslots = 4;
@@ -98,8 +110,10 @@ struct Serve {
   uint64_t next = 1;
   uint64_t completed = 0, waits = 0;
   bool stop = false;
+  uint64_t epoch = 0;     // bumped by every submission, completion and cancellation
+  Clock::time_point t_start = Clock::now();
   std::thread worker;
-  std::condition_variable cv_work, cv_done;
+  std::condition_variable cv_work, cv_done, cv_slot;
 };
 
 static std::string shape_key(const Plan& pl, const adorym_request& r) {
@@ -180,6 +194,8 @@ static int launch_ticket(adorym_ctx* ctx, Serve& S, uint64_t id) {
     ctx->err = std::string("graph launch: ") + cudaGetErrorString(e);
     return ADORYM_EDEVICE;
   }
+  sl.launched = true;
+  S.cv_slot.notify_all();
   return ADORYM_OK;
 }
 
@@ -187,84 +203,115 @@ static void finish(Serve& S, uint64_t id, int rc) {
   Ticket& t = S.tickets[id];
   if (t.slot >= 0) {
     S.slots[t.slot].ticket = 0;
+    S.slots[t.slot].launched = false;
     S.arena.release(t.ws_off, t.plan.total);
   }
   t.state = 2;
   t.rc = rc;
+  t.t_done = Clock::now();
   S.completed++;
+  S.epoch++;
+}
+
+// waiter of slot i: sleeps until the slot's ticket is launched, blocks (without the context lock)
+// until its completion event, then retires it and wakes the admission worker and pollers
+static void slot_waiter(adorym_ctx* ctx, int i) {
+  Serve& S = *ctx->serve;
+  cudaSetDevice(ctx->device);
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  for (;;) {
+    S.cv_slot.wait(lk, [&] { return S.stop || (S.slots[i].ticket && S.slots[i].launched); });
+    if (S.stop && !(S.slots[i].ticket && S.slots[i].launched)) return;
+    Slot& sl = S.slots[i];
+    const uint64_t id = sl.ticket;
+    const cudaEvent_t ev = sl.done;
+    lk.unlock();
+    const cudaError_t q = cudaEventSynchronize(ev);
+    lk.lock();
+    const bool bad_data = q == cudaSuccess && sl.status && *sl.status != 0;
+    if (q != cudaSuccess) {
+      cudaGetLastError();
+      ctx->err = std::string("request failed: ") + cudaGetErrorString(q);
+    }
+    if (bad_data) ctx->err = std::string("request failed: ") + status_message(*sl.status);
+    finish(S, id, q != cudaSuccess ? ADORYM_EDEVICE : bad_data ? ADORYM_EDATA : ADORYM_OK);
+    S.cv_done.notify_all();
+    S.cv_work.notify_all();
+  }
+}
+
+// admit one queued request into `slot` if one may go now: the head if it fits; else, unless the
+// head has been overtaken kMaxOvertakes times already, the oldest later request that fits
+static bool admit_one(adorym_ctx* ctx, Serve& S, int slot) {
+  for (size_t i = 0; i < S.queue.size(); ++i) {
+    const uint64_t id = S.queue[i];
+    Ticket& t = S.tickets[id];
+    size_t off = 0;
+    if (!S.arena.alloc(t.plan.total, &off)) {
+      if (!t.waited) S.waits++;
+      t.waited = true;
+      if (i == 0 && t.overtaken >= kMaxOvertakes) return false;
+      continue;
+    }
+    if (i > 0) S.tickets[S.queue.front()].overtaken++;
+    S.queue.erase(S.queue.begin() + (std::ptrdiff_t)i);
+    t.slot = slot;
+    t.ws_off = off;
+    t.state = 1;
+    t.t_admit = Clock::now();
+    S.slots[slot].ticket = id;
+    S.slots[slot].launched = false;
+    const int rc = launch_ticket(ctx, S, id);
+    if (rc) {
+      finish(S, id, rc);
+      S.cv_done.notify_all();
+    }
+    return true;
+  }
+  return false;
 }
 
 static void worker_main(adorym_ctx* ctx) {
   Serve& S = *ctx->serve;
   cudaSetDevice(ctx->device);
   std::unique_lock<std::mutex> lk(ctx->mu);
+  uint64_t seen = ~(uint64_t)0;
   while (!S.stop) {
-    bool progress = false;
-    // retire finished slots
-    for (auto& sl : S.slots) {
-      if (!sl.ticket) continue;
-      cudaError_t q = cudaEventQuery(sl.done);
-      if (q == cudaErrorNotReady) continue;
-      const uint64_t id = sl.ticket;
-      const bool bad_data = q == cudaSuccess && sl.status && *sl.status != 0;
-      finish(S, id, q != cudaSuccess ? ADORYM_EDEVICE : bad_data ? ADORYM_EDATA : ADORYM_OK);
-      if (q != cudaSuccess) ctx->err = std::string("request failed: ") + cudaGetErrorString(q);
-      if (bad_data) ctx->err = std::string("request failed: ") + status_message(*sl.status);
-      progress = true;
-    }
-    // admit in arrival order while a slot and memory are free
-    while (!S.queue.empty()) {
-      const uint64_t id = S.queue.front();
-      Ticket& t = S.tickets[id];
-      int free_slot = -1;
-      for (int i = 0; i < (int)S.slots.size(); ++i)
-        if (!S.slots[i].ticket) {
-          free_slot = i;
-          break;
-        }
-      size_t off = 0;
-      if (free_slot < 0 || !S.arena.alloc(t.plan.total, &off)) {
-        if (!t.waited) S.waits++;
-        t.waited = true;
-        break;
+    if (seen != S.epoch) {
+      seen = S.epoch;
+      // admit while a slot is free and a queued request may go
+      for (;;) {
+        int free_slot = -1;
+        for (int i = 0; i < (int)S.slots.size(); ++i)
+          if (!S.slots[i].ticket) {
+            free_slot = i;
+            break;
+          }
+        if (free_slot < 0 || S.queue.empty() || !admit_one(ctx, S, free_slot)) break;
       }
-      S.queue.pop_front();
-      t.slot = free_slot;
-      t.ws_off = off;
-      t.state = 1;
-      S.slots[free_slot].ticket = id;
-      const int rc = launch_ticket(ctx, S, id);
-      if (rc) finish(S, id, rc);
-      progress = true;
     }
-    if (progress) S.cv_done.notify_all();
-    bool busy = false;
-    for (auto& sl : S.slots) busy |= sl.ticket != 0;
-    if (busy) {
-      lk.unlock();
-      std::this_thread::sleep_for(std::chrono::microseconds(20));
-      lk.lock();
-    } else {
-      S.cv_work.wait(lk, [&] { return S.stop || !S.queue.empty(); });
-    }
+    S.cv_work.wait(lk, [&] { return S.stop || S.epoch != seen; });
   }
 }
 
-static int serve_start(adorym_ctx* ctx) {
-  if (ctx->serve) return ADORYM_OK;
+// create the serving state of ctx (ctx->mu held): arena, slots, worker and slot waiters
+static int serve_create(adorym_ctx* ctx, int nslots, size_t budget_bytes) {
   auto S = std::make_unique<Serve>();
+  S->nslots = nslots;
+  S->budget = budget_bytes;
   size_t freeb = 0, totalb = 0;
   cudaSetDevice(ctx->device);
   cudaMemGetInfo(&freeb, &totalb);
-  size_t budget = S->budget ? S->budget : std::min(freeb / 2, (size_t)8 << 30);
-  if (!S->arena.init(budget)) {
+  const size_t bytes = budget_bytes ? budget_bytes : std::min(freeb / 2, (size_t)8 << 30);
+  if (!S->arena.init(bytes)) {
     ctx->err = "serving arena allocation failed";
     return ADORYM_ENOMEM;
   }
-  S->slots.resize(S->nslots);
+  S->slots.resize(nslots);
   for (auto& sl : S->slots) {
     cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
-    cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    // blocking sync: the slot's waiter thread sleeps in cudaEventSynchronize instead of spinning
+    cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming | cudaEventBlockingSync);
     void* h = nullptr;
     void* hd = nullptr;
     if (cudaHostAlloc(&h, sizeof(int), cudaHostAllocMapped) == cudaSuccess &&
@@ -278,7 +325,13 @@ static int serve_start(adorym_ctx* ctx) {
   }
   ctx->serve = S.release();
   ctx->serve->worker = std::thread(worker_main, ctx);
+  for (int i = 0; i < nslots; ++i) ctx->serve->slots[i].waiter = std::thread(slot_waiter, ctx, i);
   return ADORYM_OK;
+}
+
+static int serve_start(adorym_ctx* ctx) {
+  if (ctx->serve) return ADORYM_OK;
+  return serve_create(ctx, 4, 0);
 }
 
 void serve_shutdown(adorym_ctx* ctx) {
@@ -288,8 +341,11 @@ void serve_shutdown(adorym_ctx* ctx) {
     ctx->serve->stop = true;
   }
   ctx->serve->cv_work.notify_all();
+  ctx->serve->cv_slot.notify_all();
   if (ctx->serve->worker.joinable()) ctx->serve->worker.join();
   Serve& S = *ctx->serve;
+  for (auto& sl : S.slots)   // a waiter retires its launched ticket (the GPU work completes) first
+    if (sl.waiter.joinable()) sl.waiter.join();
   for (auto& sl : S.slots) {
     cudaStreamSynchronize(sl.stream);
     for (auto& kv : sl.graphs) cudaGraphExecDestroy(kv.second);
@@ -326,35 +382,7 @@ int adorym_serve_config(adorym_ctx* ctx, int slots, uint64_t budget_bytes) {
   }
   serve_shutdown(ctx);
   std::lock_guard<std::mutex> lk(ctx->mu);
-  auto S = std::make_unique<Serve>();
-  S->nslots = slots;
-  S->budget = budget_bytes;
-  size_t freeb = 0, totalb = 0;
-  cudaSetDevice(ctx->device);
-  cudaMemGetInfo(&freeb, &totalb);
-  const size_t bytes = budget_bytes ? budget_bytes : std::min(freeb / 2, (size_t)8 << 30);
-  if (!S->arena.init(bytes)) {
-    ctx->err = "serving arena allocation failed";
-    return ADORYM_ENOMEM;
-  }
-  S->slots.resize(slots);
-  for (auto& sl : S->slots) {
-    cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
-    cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
-    void* h = nullptr;
-    void* hd = nullptr;
-    if (cudaHostAlloc(&h, sizeof(int), cudaHostAllocMapped) == cudaSuccess &&
-        cudaHostGetDevicePointer(&hd, h, 0) == cudaSuccess) {
-      sl.status = static_cast<int*>(h);
-      sl.status_dev = static_cast<int*>(hd);
-      *sl.status = 0;
-    } else {
-      cudaGetLastError();
-    }
-  }
-  ctx->serve = S.release();
-  ctx->serve->worker = std::thread(worker_main, ctx);
-  return ADORYM_OK;
+  return serve_create(ctx, slots, budget_bytes);
 }
 
 int adorym_submit(adorym_ctx* ctx, const adorym_request* req, uint64_t* ticket) {
@@ -415,14 +443,20 @@ int adorym_submit(adorym_ctx* ctx, const adorym_request* req, uint64_t* ticket) 
     return rc;
   }
   const uint64_t id = S.next++;
+  t.t_submit = Clock::now();
   S.tickets[id] = t;
   S.queue.push_back(id);
   *ticket = id;
+  S.epoch++;
   S.cv_work.notify_all();
   return ADORYM_OK;
 }
 
 int adorym_poll(adorym_ctx* ctx, uint64_t ticket, int64_t timeout_us) {
+  return adorym_poll_times(ctx, ticket, timeout_us, nullptr);
+}
+
+int adorym_poll_times(adorym_ctx* ctx, uint64_t ticket, int64_t timeout_us, double* times_us) {
   if (!ctx) return ADORYM_EINVAL;
   std::unique_lock<std::mutex> lk(ctx->mu);
   if (!ctx->serve) return ADORYM_ENOENT;
@@ -433,7 +467,15 @@ int adorym_poll(adorym_ctx* ctx, uint64_t ticket, int64_t timeout_us) {
   if (timeout_us < 0) S.cv_done.wait(lk, ready);
   else if (timeout_us > 0) S.cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
   if (!ready()) return ADORYM_ETIMEDOUT;
-  const int rc = S.tickets[ticket].rc;
+  const Ticket& t = S.tickets[ticket];
+  const int rc = t.rc;
+  if (times_us) {
+    const bool ran = t.slot >= 0;
+    auto us = [](Clock::duration d) { return std::chrono::duration<double, std::micro>(d).count(); };
+    times_us[0] = us((ran ? t.t_admit : t.t_done) - t.t_submit);   // waiting for admission
+    times_us[1] = ran ? us(t.t_done - t.t_admit) : 0.0;             // admitted until retired
+    times_us[2] = ran ? us(t.t_admit - S.t_start) : -1.0;           // admission instant
+  }
   S.tickets.erase(ticket);
   return rc;
 }
@@ -456,6 +498,8 @@ int adorym_cancel(adorym_ctx* ctx, uint64_t ticket) {
     }
   it->second.state = 2;
   it->second.rc = ADORYM_ECANCELED;
+  it->second.t_done = Clock::now();
+  S.epoch++;
   S.cv_done.notify_all();
   S.cv_work.notify_all();   // the request behind it may now fit
   return ADORYM_OK;

@@ -67,3 +67,13 @@ def test_null_context_is_rejected(lib):
     assert lib.adorym_inject_alloc_failures(None, 1) == EINVAL
     assert lib.adorym_check(None) == EINVAL
     assert lib.adorym_last_error(None) == b"null context"
+
+
+def test_wait_limits_are_validated(lib):
+    """adorym_set_wait_limits (test hook of the bounded device waits) checks its arguments on the host."""
+    from paper_2012_12686_gb300.adorym import set_wait_limits, EINVAL, OK, WAIT_DEFAULT, WAIT_GIVE_UP
+    assert set_wait_limits(-3, WAIT_DEFAULT, WAIT_DEFAULT) == EINVAL
+    assert set_wait_limits(WAIT_DEFAULT, -3, WAIT_DEFAULT) == EINVAL
+    assert set_wait_limits(WAIT_DEFAULT, WAIT_DEFAULT, -3) == EINVAL
+    assert set_wait_limits(0, 0, WAIT_GIVE_UP) == OK
+    assert set_wait_limits() == OK

@@ -180,3 +180,25 @@ def test_slice_gap_gradient_brute_force(far):
     pe = model.Problem.of(dict(base, gaps=None, lambda_dz_over_px2=0.5))
     np.testing.assert_allclose(model.forward(pu, delta, beta, probe, pos), model.forward(pe, delta, beta, probe, pos),
                                rtol=1e-13)
+
+
+@pytest.mark.parametrize("tomo,loss", [(1, "lsq"), (0, "poisson")])
+def test_position_offset_gradient_brute_force(tomo, loss):
+    """Per-angle position offset (Sec. 2.3.2): central differences of the loss in one offset added
+    to every position of the batch against offset_loss_grad."""
+    if tomo:
+        pb = _far_problem(loss, Lz=9, Ly=10, Lx=9, L=9, M=1, B=3, tomo=1, theta=0.45)
+    else:
+        pb = _far_problem(loss)
+    g = np.random.default_rng(17)
+    delta = g.uniform(0, 1e-3, (pb.Lz, pb.Ly, pb.Lx)); beta = g.uniform(0, 2e-4, delta.shape)
+    probe = _cplx(g, (pb.M, pb.N, pb.N)) * 3.0
+    pos = np.array([[1.2, 0.3], [0.4, 1.8], [2.1, -0.7]])[:pb.B]
+    Im = model.forward(pb, delta * 1.2, beta, probe, pos + 0.15)
+    L0, g_off = model.offset_loss_grad(pb, delta, beta, probe, pos, Im)
+    h = 1e-6
+    for a in range(2):
+        e = np.zeros(2)
+        e[a] = h
+        fd = (model.loss(pb, delta, beta, probe, pos + e, Im) - model.loss(pb, delta, beta, probe, pos - e, Im)) / (2 * h)
+        assert abs(fd - g_off[a]) <= 2e-6 * max(abs(fd), 1e-12) + 1e-12, (a, fd, g_off[a])

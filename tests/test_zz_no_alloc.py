@@ -1,8 +1,8 @@
 """adorym_loss_grad_noalloc against adorym_loss_grad, through the C ABI.
 
-The no-allocation entry point serves callers that cannot call cudaMalloc (inside someone else's
-stream capture, under a host framework that owns device memory, in loops that must not
-allocate): its workspace is a fixed file-scope device array.  Its results must match the
+The no-allocation entry point serves callers that cannot call cudaMalloc (under a host framework
+that owns all device memory through its own pool, in loops that must not allocate): its workspace
+is a fixed file-scope device array.  Its results must match the
 regular entry point within the parity tolerances, on two calls in a row (the shared array keeps
 the previous call's contents), and problems too large for the array must be refused cleanly.
 This file is collected last so that a failure here cannot hide the other tests' results.
@@ -77,3 +77,42 @@ def test_noalloc_refuses_problems_beyond_its_scratch():
     assert loss_grad_noalloc(s, p, d, d, probe, pos, Im) == ETOOBIG
     # host pointers are refused (everything must already be on the device)
     assert loss_grad_noalloc(s, p, d, d, probe, pos.cpu(), Im) == EINVAL
+    # variable slice spacing is not offered by this entry point
+    assert loss_grad_noalloc(s, dict(p, B=2, N=32, gaps=[0.02] * (p["L"] - 1)), d, d, probe[:, :32, :32].contiguous(),
+                             pos[:2].contiguous(), Im[:2, :32, :32].contiguous()) == EINVAL
+
+
+def test_noalloc_reports_bad_positions_through_the_caller_status_word():
+    """A non-finite position is seen only by the kernels: they set a bit in the caller's device
+    status word (no trap, corners clamped); a valid call after it gives the regular results."""
+    import math
+    import torch
+    from paper_2012_12686_gb300.adorym import Engine, loss_grad_noalloc, OK
+    dev = torch.device("cuda:0")
+    case = C.small_case(N=32, L=4, M=1, B=3, loss="poisson", seed=23)
+    x = _inputs(case, dev)
+    stream = torch.cuda.current_stream(dev)
+    eng = Engine(0, stream.cuda_stream)
+    oid = eng.register_object(x["d"], x["b"])
+    ref = _outs(x, False)
+    eng.loss_grad(case["problem"], oid, x["probe"], x["pos"], x["Im"], ref["loss"], ref["gd"], ref["gb"],
+                  ref["gp"], ref["gpos"])
+    status = torch.zeros((), dtype=torch.int32, device=dev)
+    bad = x["pos"].clone()
+    bad.view(-1)[1] = math.nan
+    got = _outs(x, False)
+    assert loss_grad_noalloc(stream.cuda_stream, case["problem"], x["d"], x["b"], x["probe"], bad, x["Im"],
+                             got["loss"], got["gd"], got["gb"], got["gp"], got["gpos"], status=status) == OK
+    torch.cuda.synchronize()
+    assert int(status.item()) != 0
+    status.zero_()
+    got = _outs(x, False)
+    assert loss_grad_noalloc(stream.cuda_stream, case["problem"], x["d"], x["b"], x["probe"], x["pos"], x["Im"],
+                             got["loss"], got["gd"], got["gb"], got["gp"], got["gpos"], status=status) == OK
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert abs(got["loss"].item() - ref["loss"].item()) <= C.TOL_I * abs(ref["loss"].item())
+    for k in ("gd", "gb", "gp", "gpos"):
+        assert C.rel(got[k].cpu().numpy(), ref[k].cpu().numpy()) <= C.TOL_G, k
+    eng.unregister_object(oid)
+    eng.close()
