@@ -36,10 +36,12 @@ namespace adorym {
 
 // Complex arithmetic.  With ADORYM_PACKED_F32X2 (default) the real and imaginary parts go through
 // the packed two-lane FP32 instructions of sm_100+ (__fadd2_rn, __fmul2_rn, __ffma2_rn): one
-// instruction per complex add, two per complex multiply, which halves the issue slots of the
-// butterflies.  Every lane rounds exactly as the scalar form does (a - b as fma(b, -1, a), and the
-// products in the same order: the cross term is rounded, then fused), so both forms give
-// bitwise the same results.
+// instruction per complex add, two per complex multiply.  Measured on the 128 x 128 multislice
+// launch: 1.32 ms packed against 1.53 ms scalar (678 M against 887 M instructions; the scalar form
+// needs more registers and spills inside the passes), although in an isolated loop of transforms
+// with no pointwise work the scalar form ran 5 % faster.  Every lane rounds exactly as the scalar
+// form does (a - b as fma(b, -1, a), the products in the same order), so both forms give bitwise
+// the same results.
 #ifndef ADORYM_PACKED_F32X2
 #define ADORYM_PACKED_F32X2 1
 #endif
@@ -163,7 +165,11 @@ struct Geo;
 #ifndef ADORYM_NT128
 #define ADORYM_NT128 512
 #endif
-// ADORYM_FOURPASS64: N = 64 fused kernels on the four-pass scheme of fft_block4.cuh (256 threads)
+// ADORYM_FOURPASS64: N = 64 fused kernels on the four-pass scheme of fft_block4.cuh (256 threads).
+// Off by default: its radix-16 stages raised the full-size tomography probe-gradient error above
+// the stored FP32 floor (1.68e-3 against a bar of 1.58e-3; the six-pass form gives 1.49e-3), and
+// the one tomography launch measured with it (scalar arithmetic) took 1.35 ms against 1.22 ms
+// for the packed six-pass form.
 #ifndef ADORYM_FOURPASS64
 #define ADORYM_FOURPASS64 0
 #endif

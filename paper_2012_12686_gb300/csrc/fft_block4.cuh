@@ -202,10 +202,10 @@ struct PathFFT {
 template <int N>
 struct PathFFT4 {
   using G = G4<N>;
-  static_assert(Geo<N>::NT == G::NT, "the four-pass scheme sets the CTA's thread count");
   static constexpr int CY = G::NY1, YS = G::NY2, RX = G::NX2, KXS = G::NX1;
   template <int S4, int S1, bool LOAD, bool STORE, class Pre, class Op>
   __device__ static __forceinline__ void c14(float2* A, const float2* tw, Pre pre, Op op) {
+    static_assert(Geo<N>::NT == G::NT, "the four-pass scheme sets the CTA's thread count");
     pass4_a<G, S4, S1, LOAD, STORE>(A, tw, pre, op);
   }
   template <int S>

@@ -5,7 +5,12 @@
 // from one device arena with a first-fit allocator.  Admission is in arrival order, except that
 // when the oldest request does not fit, later requests that do fit may go ahead of it -- at most
 // kMaxOvertakes admissions past one waiting request, after which nothing overtakes it, so a large
-// request is never starved.  Admitted requests are recorded by stream capture into a CUDA graph
+// request is never starved.  Half of the slots (rounded down) are short-request slots: their
+// streams have the highest scheduling priority and only requests with a small amount of work
+// (kShortWork) are admitted to them, so a short request neither waits for a slot behind long
+// ones nor waits on the device for long requests' queued thread blocks.  Long requests take the
+// other slots, at normal priority; short ones take any free slot, short-request slots first.
+// Admitted requests are recorded by stream capture into a CUDA graph
 // and launched; the executable graph of each (slot, problem shape) is kept and updated in place
 // (cudaGraphExecUpdate) for the next request of that shape, so steady-state launches cost one
 // graph launch.  Completion is event driven: each slot has a waiter thread blocked in
@@ -76,6 +81,7 @@ using Clock = std::chrono::steady_clock;
 struct Ticket {
   adorym_request req{};
   Plan plan;
+  bool is_short = false;  // work below kShortWork: may use the high-priority slots
   int state = 0;          // 0 queued, 1 running, 2 done
   int rc = ADORYM_OK;
   int slot = -1;
@@ -86,6 +92,7 @@ struct Ticket {
 };
 
 struct Slot {
+  bool fast = false;      // short-request slot: highest-priority stream, short requests only
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   int* status = nullptr;  // mapped pinned host word: the running ticket's status (kernels write it
@@ -99,6 +106,15 @@ struct Slot {
 
 // admissions of later requests allowed past a request that waits at the head of the queue
 constexpr int kMaxOvertakes = 8;
+
+// A request is short when its work, B * M * L * N^2 pixel-slices (doubled for the two-pass path at
+// N >= 256, whose fields make HBM round trips), is at most 2^26: about a millisecond of device time
+// on this part (a 128 x 128 batch of 4096 position-slices is 2^26 and takes ~1.4 ms).
+constexpr double kShortWork = 67108864.0;
+static bool short_request(const adorym_problem& p) {
+  const double w = (double)p.B * p.M * p.L * (double)p.N * p.N * (two_pass(p.N) ? 2.0 : 1.0);
+  return w <= kShortWork;
+}
 
 struct Serve {
   int nslots = 4;
@@ -240,14 +256,31 @@ static void slot_waiter(adorym_ctx* ctx, int i) {
   }
 }
 
-// admit one queued request into `slot` if one may go now: the head if it fits; else, unless the
-// head has been overtaken kMaxOvertakes times already, the oldest later request that fits
-static bool admit_one(adorym_ctx* ctx, Serve& S, int slot) {
+// a free slot for ticket t: short requests take a short-request slot first, then a normal one;
+// long requests only normal slots (-1: none)
+static int free_slot_for(const Serve& S, const Ticket& t) {
+  int normal = -1;
+  for (int i = 0; i < (int)S.slots.size(); ++i) {
+    if (S.slots[i].ticket) continue;
+    if (S.slots[i].fast) {
+      if (t.is_short) return i;
+    } else if (normal < 0) {
+      normal = i;
+    }
+  }
+  return normal;
+}
+
+// admit one queued request if one may go now: the head if a slot and memory are free for it;
+// else, unless the head has been overtaken kMaxOvertakes times already, the oldest later request
+// for which they are
+static bool admit_one(adorym_ctx* ctx, Serve& S) {
   for (size_t i = 0; i < S.queue.size(); ++i) {
     const uint64_t id = S.queue[i];
     Ticket& t = S.tickets[id];
+    const int slot = free_slot_for(S, t);
     size_t off = 0;
-    if (!S.arena.alloc(t.plan.total, &off)) {
+    if (slot < 0 || !S.arena.alloc(t.plan.total, &off)) {
       if (!t.waited) S.waits++;
       t.waited = true;
       if (i == 0 && t.overtaken >= kMaxOvertakes) return false;
@@ -279,15 +312,8 @@ static void worker_main(adorym_ctx* ctx) {
   while (!S.stop) {
     if (seen != S.epoch) {
       seen = S.epoch;
-      // admit while a slot is free and a queued request may go
-      for (;;) {
-        int free_slot = -1;
-        for (int i = 0; i < (int)S.slots.size(); ++i)
-          if (!S.slots[i].ticket) {
-            free_slot = i;
-            break;
-          }
-        if (free_slot < 0 || S.queue.empty() || !admit_one(ctx, S, free_slot)) break;
+      // admit while a queued request may go
+      while (!S.queue.empty() && admit_one(ctx, S)) {
       }
     }
     S.cv_work.wait(lk, [&] { return S.stop || S.epoch != seen; });
@@ -308,8 +334,12 @@ static int serve_create(adorym_ctx* ctx, int nslots, size_t budget_bytes) {
     return ADORYM_ENOMEM;
   }
   S->slots.resize(nslots);
-  for (auto& sl : S->slots) {
-    cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);   // (least, greatest)
+  for (int i = 0; i < nslots; ++i) {
+    Slot& sl = S->slots[i];
+    sl.fast = i < nslots / 2;
+    cudaStreamCreateWithPriority(&sl.stream, cudaStreamNonBlocking, sl.fast ? prio_hi : prio_lo);
     // blocking sync: the slot's waiter thread sleeps in cudaEventSynchronize instead of spinning
     cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming | cudaEventBlockingSync);
     void* h = nullptr;
@@ -443,6 +473,7 @@ int adorym_submit(adorym_ctx* ctx, const adorym_request* req, uint64_t* ticket) 
     return rc;
   }
   const uint64_t id = S.next++;
+  t.is_short = short_request(r.problem);
   t.t_submit = Clock::now();
   S.tickets[id] = t;
   S.queue.push_back(id);
