@@ -858,7 +858,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain torch GPU path")
-    ap.add_argument("--workload", default=WORKLOAD, choices=["multislice", "ptycho2d", "tomo", "holo"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=["multislice", "ptycho2d", "tomo", "holo", "farfield256"],
                     help="workload of the timed steps (default: the metric's multislice configuration)")
     ap.add_argument("--batch", type=int, default=0,
                     help="override the workload's batch (positions / problems per call), e.g. a small case for "

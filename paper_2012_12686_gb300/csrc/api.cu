@@ -33,6 +33,9 @@ int validate(const adorym_problem& p, const char** err) {
     if (p.Lz != p.L) return bad("far field: Lz must equal L (the wave crosses every slice)");
     if (p.Ly < 1 || p.Lx < 1) return bad("object dims must be >= 1");
     if (p.tomo && !std::isfinite(p.theta)) return bad("theta not finite");
+    if (p.tomo && (p.Lz >= 65536 || p.Lx >= 65536 || (long long)p.Lz * p.Lx >= (1LL << 31) ||
+                   (long long)p.Lz * p.Ly * p.Lx >= (1LL << 32)))
+      return bad("tomography: Lz and Lx below 65536 and fewer than 2^32 voxels");
   } else {
     if (!pow2_in(p.N, 8, 1024)) return bad("near field: N must be a power of two in 8..1024");
     if (p.tomo) return bad("tomography is defined for the far-field geometry only");
@@ -146,6 +149,7 @@ int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan
     const size_t V = (size_t)p.Lz * p.Ly * p.Lx;
     q.off_T = take(V * f2);
     if (q.want_obj) q.off_grot = take(2 * V * sizeof(double));   // FP64 object-gradient accumulators
+    if (q.want_obj && q.tomo) q.off_rtab = take(rot_table_ints(p.Lz, p.Lx) * sizeof(int));
   }
   q.bytes_probe = M * NN * f2;
   q.bytes_pos = B * q.nd * 2 * sizeof(float);
@@ -487,7 +491,9 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
   }
   if (pl.want_obj && !direct) {
     if (pl.tomo)
-      rc = chk(launch_rotate_adj(gd, gb, c.gd, c.gb, p.Lz, p.Ly, p.Lx, (float)cth, (float)sth, box, s), "rotate_adj");
+      rc = chk(launch_rotate_adj(gd, gb, c.gd, c.gb, p.Lz, p.Ly, p.Lx, (float)cth, (float)sth, box,
+                                 reinterpret_cast<int*>(W(pl.off_rtab)), s),
+               "rotate_adj");
     else
       rc = chk(launch_grad_add(gd, gb, c.gd, c.gb, p.Lz, p.Ly, p.Lx, box, s), "grad_add");
     if (rc) return rc;

@@ -43,6 +43,7 @@ struct Plan {
   size_t off_status = 0;   // int device status word of the call (ADORYM_STATUS_* bits)
   size_t off_spck = 0, off_spseg = 0, off_gapp = 0, off_s_ggap = 0;   // slice-gap gradient
   size_t off_posd = 0, off_s_goff = 0;   // FP64 position gradients [B][2]; staged offset gradient
+  size_t off_rtab = 0;                   // tomography: rotation-transpose table [Lz][Lx]
   // staging for host-memory arguments
   size_t off_s_probe = 0, off_s_pos = 0, off_s_meas = 0, off_s_gprobe = 0, off_s_gpos = 0, off_s_iout = 0,
          off_s_gnf = 0;

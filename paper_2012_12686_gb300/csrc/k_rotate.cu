@@ -152,45 +152,70 @@ __global__ void k_transmission(const float* __restrict__ vd, const float* __rest
   }
 }
 
-// transpose of the rotation: each unrotated node (z, y, x) with y in the box collects the
-// rotated-frame accumulators whose sample point lies within one pixel of it
-__global__ void k_rotate_adj(const double* __restrict__ gdr, const double* __restrict__ gbr, float* __restrict__ gd,
-                             float* __restrict__ gb, int Lz, int Ly, int Lx, float c, float s,
-                             const int* __restrict__ box) {
-  const Region R = region(box, Lz);
+// transpose of the rotation, step 1 (per call, independent of y): for each unrotated node (z, x)
+// the rotated-frame nodes (z_t, x_t) whose sample point lies within one pixel of it, with the
+// forward pass's own bilinear weights, in the order z_t, then x_t ascending.  Table planes of
+// P = Lz * Lx ints: [0] count, [1 + k] packed node z_t * 65536 + x_t, [1 + kRotTaps + k] weight.
+__global__ void __launch_bounds__(256) k_rotate_table(int* __restrict__ tab, int Lz, int Lx, float c, float s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int P = Lz * Lx;
+  if (i >= P) return;
+  const int z = i / Lx, x = i - z * Lx;
   const float cx = 0.5f * (float)(Lx - 1), cz = 0.5f * (float)(Lz - 1);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n; i += (size_t)gridDim.x * blockDim.x) {
-    const int x = R.x0 + (int)(i % R.w);
-    const int y = R.y0 + (int)((i / R.w) % R.h);
-    const int z = (int)(i / ((size_t)R.w * R.h));
-    // rotated-frame point that maps exactly onto this node (inverse rotation)
-    const float u = (float)x - cx, w = (float)z - cz;
-    const float xs = c * u + s * w + cx, zs = -s * u + c * w + cz;
-    // a contributing voxel samples within one pixel of the node in x and z, so (inverse rotation)
-    // it lies within |c| + |s| <= sqrt(2) of (xs, zs) along each axis: at most 3 x 3 candidates
-    // (the margin covers FP32 rounding of xs, zs and of the forward taps); the membership test
-    // below is the forward pass's own
-    const float r = fabsf(c) + fabsf(s) + 0.01f;
-    const int xa = max(0, (int)ceilf(xs - r)), xb = min(Lx - 1, (int)floorf(xs + r));
-    const int za = max(0, (int)ceilf(zs - r)), zb = min(Lz - 1, (int)floorf(zs + r));
-    // the taps are FP64 sums over positions; each is narrowed once (integer arithmetic, round to
-    // nearest) and the <= 4 weighted taps are added in FP32, like the caller's FP32 gradient
-    float ad = 0.f, ab = 0.f;
-    for (int zt = za; zt <= zb; ++zt) {
-      for (int xt = xa; xt <= xb; ++xt) {
-        const Tap t = tap(zt, xt, Lz, Lx, c, s);
-        float wx, wz;
-        if (t.fx == x) wx = 1.f - t.ax;
-        else if (t.fx + 1 == x) wx = t.ax;
-        else continue;
-        if (t.fz == z) wz = 1.f - t.az;
-        else if (t.fz + 1 == z) wz = t.az;
-        else continue;
-        const float wt = wx * wz;
-        const size_t o = ((size_t)zt * Ly + y) * Lx + xt;
-        ad = fmaf(wt, f64_to_f32(gdr + o), ad);
-        ab = fmaf(wt, f64_to_f32(gbr + o), ab);
+  // rotated-frame point that maps exactly onto this node (inverse rotation)
+  const float u = (float)x - cx, w = (float)z - cz;
+  const float xs = c * u + s * w + cx, zs = -s * u + c * w + cz;
+  // a contributing voxel samples within one pixel of the node in x and z, so (inverse rotation)
+  // it lies within |c| + |s| <= sqrt(2) of (xs, zs) along each axis: at most 3 x 3 candidates
+  // (the margin covers FP32 rounding of xs, zs and of the forward taps); the membership test
+  // below is the forward pass's own
+  const float r = fabsf(c) + fabsf(s) + 0.01f;
+  const int xa = max(0, (int)ceilf(xs - r)), xb = min(Lx - 1, (int)floorf(xs + r));
+  const int za = max(0, (int)ceilf(zs - r)), zb = min(Lz - 1, (int)floorf(zs + r));
+  int n = 0;
+  for (int zt = za; zt <= zb; ++zt) {
+    for (int xt = xa; xt <= xb; ++xt) {
+      const Tap t = tap(zt, xt, Lz, Lx, c, s);
+      float wx, wz;
+      if (t.fx == x) wx = 1.f - t.ax;
+      else if (t.fx + 1 == x) wx = t.ax;
+      else continue;
+      if (t.fz == z) wz = 1.f - t.az;
+      else if (t.fz + 1 == z) wz = t.az;
+      else continue;
+      if (n < kRotTaps) {   // always true: at most 3 x 3 candidates
+        tab[(size_t)(1 + n) * P + i] = (zt << 16) | xt;
+        tab[(size_t)(1 + kRotTaps + n) * P + i] = __float_as_int(wx * wz);
+        ++n;
       }
+    }
+  }
+  tab[i] = n;
+}
+
+// step 2: each unrotated node (z, y, x) of the box collects its rotated-frame accumulators from
+// the table (flat index over the box's rows and columns, threads along x).  The taps are FP64
+// sums over positions; each is narrowed once (integer arithmetic, round to nearest) and the
+// weighted taps are added in FP32 in the table's order, like the caller's FP32 gradient
+__global__ void __launch_bounds__(256) k_rotate_adj(const double* __restrict__ gdr, const double* __restrict__ gbr,
+                                                    float* __restrict__ gd, float* __restrict__ gb, int Lz, int Ly,
+                                                    int Lx, const int* __restrict__ tab, const int* __restrict__ box) {
+  const Region R = region(box, Lz);
+  const int P = Lz * Lx;
+  const unsigned n = (unsigned)R.n;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned row = i / (unsigned)R.w;
+    const int x = R.x0 + (int)(i - row * (unsigned)R.w);
+    const int z = (int)(row / (unsigned)R.h), y = R.y0 + (int)(row - (unsigned)z * (unsigned)R.h);
+    const int node = z * Lx + x;
+    const int cnt = __ldg(tab + node);
+    float ad = 0.f, ab = 0.f;
+    for (int k = 0; k < cnt; ++k) {
+      const int zx = __ldg(tab + (size_t)(1 + k) * P + node);
+      const float wk = __int_as_float(__ldg(tab + (size_t)(1 + kRotTaps + k) * P + node));
+      const size_t o = ((size_t)(zx >> 16) * Ly + y) * Lx + (zx & 0xFFFF);
+      ad = fmaf(wk, f64_to_f32(gdr + o), ad);
+      ab = fmaf(wk, f64_to_f32(gbr + o), ab);
     }
     const size_t io = ((size_t)z * Ly + y) * Lx + x;
     gd[io] += ad;
@@ -228,8 +253,10 @@ cudaError_t launch_transmission(const float* vd, const float* vb, float2* T, int
 }
 
 cudaError_t launch_rotate_adj(const double* gdr, const double* gbr, float* gd, float* gb, int Lz, int Ly, int Lx,
-                              float c, float sn, const int* box, cudaStream_t s) {
-  (k_rotate_adj<<<vol_grid((size_t)Lz * Ly * Lx), 256, 0, s>>>(gdr, gbr, gd, gb, Lz, Ly, Lx, c, sn, box), note_launch());
+                              float c, float sn, const int* box, int* tab, cudaStream_t s) {
+  const int nodes = Lz * Lx;
+  (k_rotate_table<<<(nodes + 255) / 256, 256, 0, s>>>(tab, Lz, Lx, c, sn), note_launch());
+  (k_rotate_adj<<<vol_grid((size_t)Lz * Ly * Lx), 256, 0, s>>>(gdr, gbr, gd, gb, Lz, Ly, Lx, tab, box), note_launch());
   return cudaGetLastError();
 }
 

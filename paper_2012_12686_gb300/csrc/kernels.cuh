@@ -180,9 +180,17 @@ cudaError_t launch_bbox(const float* pos, int B, int N, int Ly, int Lx, int far,
 cudaError_t launch_transmission(const float* vd, const float* vb, float2* T, int Lz, int Ly, int Lx, float kdz,
                                 int rotate, float c, float sn, const int* box, double* zero_a, double* zero_b,
                                 cudaStream_t s);
-// transpose of the rotation applied to the FP64 rotated-frame accumulators, added into gd/gb (rows of the box)
+// The rotation's transpose per unrotated node (z, x), independent of y: the rotated-frame nodes
+// (z_t, x_t) that contribute and their bilinear weights.  The candidates lie in a 3 x 3 window
+// (|cos| + |sin| <= sqrt 2 on each side), so nine entries always suffice (up to five contribute
+// at some angles).  Stored as planes over the Lz * Lx nodes (coalesced reads): a count, then per
+// entry k the packed node z_t * 65536 + x_t and the weight.
+constexpr int kRotTaps = 9;
+inline size_t rot_table_ints(int Lz, int Lx) { return (size_t)Lz * Lx * (1 + 2 * kRotTaps); }
+// transpose of the rotation applied to the FP64 rotated-frame accumulators, added into gd/gb (rows
+// of the box); tab: rot_table_ints(Lz, Lx) ints of scratch, filled by the call (Lz, Lx < 65536)
 cudaError_t launch_rotate_adj(const double* gd_rot, const double* gb_rot, float* gd, float* gb, int Lz, int Ly,
-                              int Lx, float c, float sn, const int* box, cudaStream_t s);
+                              int Lx, float c, float sn, const int* box, int* tab, cudaStream_t s);
 // FP64 accumulators: add the box into the caller's FP32 gradient
 cudaError_t launch_grad_add(const double* acc_d, const double* acc_b, float* gd, float* gb, int Lz, int Ly, int Lx,
                             const int* box, cudaStream_t s);

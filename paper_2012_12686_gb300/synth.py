@@ -19,6 +19,8 @@ Workloads (sizes and magnitudes follow the paper's experiments):
 * ``tomo``      -- ptychographic tomography: 128^3 ellipsoid volume (delta in
   [0, 1e-5], beta = delta/20), 180 angles over [0, 180) deg, 8x8 positions at
   16 px centred on the volume, 64x64 probe, 128 slices, one angle per batch.
+* ``farfield256`` -- one serving-mix request shape at the two-pass tile: 256x256 probe, 8
+  slices, 64 positions on an 8x8 raster at 96 px over a 1024x1024x8 volume, Poisson loss.
 * ``holo``      -- near-field multi-distance holography: 1024x1024 single
   slice, phase in [0, 2] rad, absorption at most 0.05, plane wave, Fresnel
   numbers 1e-3..8e-3, per-hologram shifts of +-5 px plus a sub-pixel part,
@@ -209,6 +211,24 @@ def workload(name: str, seed: int = 0, **over):
         pos = raster(side, side, 16, (p["Ly"] - span) / 2.0)
         return dict(problem=p, delta=d, beta=b, delta_meas=dm, beta_meas=bm,
                     probe=probe, pos=pos, photons=1.0, grads=("object", "probe", "positions"))
+    if name == "farfield256":
+        # one request shape of the serving mix at the two-pass tile: 256 x 256 probe, 8 slices,
+        # 64 positions over a resident 1024 x 1024 x 8 volume, Poisson loss
+        p = dict(N=256, L=8, M=1, B=64, Lz=8, Ly=1024, Lx=1024, kdz=KDZ_10NM,
+                 lambda_dz_over_px2=LAMBDA_DZ_OVER_PX2_10NM, farfield=1, nf=[],
+                 loss="poisson", eps=1e-6, tomo=0, theta=0.0, checkpoint_every=0)
+        p.update(over)
+        shape = (p["Lz"], p["Ly"], p["Lx"])
+
+        def obj(s):
+            d = ellipsoid_volume(shape, 96, (16, 96), (1, 4), (1e-6, 3e-6), 5e-6, s)
+            return d, (d / 10.0).astype(np.float32)
+        d, b = obj(seed)
+        dm, bm = obj(seed + 1)
+        probe = probe_phase_screen(p["N"], 32.0, 8.0, 1.0, 1e6, seed + 2, p["M"])
+        pos = raster(8, 8, 96, 8, jitter=0.5, seed=seed + 3)
+        return dict(problem=p, delta=d, beta=b, delta_meas=dm, beta_meas=bm,
+                    probe=probe, pos=pos[: p["B"]], photons=1.0, grads=("object", "probe", "positions"))
     if name == "holo":
         p = dict(N=1024, L=1, M=1, B=8, Lz=8, Ly=1024, Lx=1024, kdz=KDZ_10NM,
                  lambda_dz_over_px2=0.0, farfield=0, nf=[1e-3, 2e-3, 4e-3, 8e-3],
