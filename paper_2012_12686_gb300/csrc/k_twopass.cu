@@ -57,6 +57,23 @@ constexpr int col_smem_bytes() {
 enum RowMode { R_FWD, R_RC_FIRST, R_RC, R_ADJ, R_NEAR_DET, R_NEAR_SEED, R_PHAT, R_PG_OUT, R_NEAR_DSEED, R_NEAR_DSEED_P };
 enum ColMode { C_PROP, C_PROP_ADJ, C_PSI0, C_FAR, C_SEED, C_Q, C_PHAT, C_PG, C_NEAR_PHI, C_NEAR_Q, C_FAR_SEED, C_FAR_SEED_P };
 
+// Resident CTAs per SM the register budget of a row / column kernel is sized for.  At N = 256 the
+// slice-step kernels of the forward and recompute sweeps and the propagation column kernels fit
+// three per SM without spilling (80 registers; shared memory 37 / 71 KB per CTA), which puts more
+// loads in flight in these latency-bound passes; the other modes keep two (their larger register
+// sets would spill).  ADORYM_TP256_OCC3 = 0 keeps two everywhere.
+#ifndef ADORYM_TP256_OCC3
+#define ADORYM_TP256_OCC3 1
+#endif
+template <int N, int MODE>
+constexpr int row_minb() {
+  return (ADORYM_TP256_OCC3 && N == 256 && (MODE == R_FWD || MODE == R_RC_FIRST)) ? 3 : 2;
+}
+template <int N, int MODE>
+constexpr int col_minb() {
+  return (ADORYM_TP256_OCC3 && N == 256 && (MODE == C_PROP || MODE == C_PROP_ADJ)) ? 3 : 2;
+}
+
 __device__ __forceinline__ float freqf(int k, int N) { return (float)(k <= (N - 1) / 2 ? k : k - N) / (float)N; }
 
 // per-pixel term of Eq. lsq_loss (amplitudes, I + eps) or Eq. poisson_loss, and dL/dI before the
@@ -172,7 +189,7 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 
 // ============================================================================ row kernel
 template <int N, int MODE>
-__global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
+__global__ void __launch_bounds__(NT2, row_minb<N, MODE>()) k_row(const TPArgs a) {
   constexpr int N1 = Geo2<N>::N1, N2 = Geo2<N>::N2, RB = Geo2<N>::RB, LDR = N + N1;
   constexpr size_t NN = (size_t)N * N;
   extern __shared__ float2 sm[];
@@ -413,7 +430,7 @@ __global__ void __launch_bounds__(NT2, 2) k_row(const TPArgs a) {
 
 // ============================================================================ column kernel
 template <int N, int MODE>
-__global__ void __launch_bounds__(NT2, 2) k_col(const __grid_constant__ TPArgs a) {
+__global__ void __launch_bounds__(NT2, col_minb<N, MODE>()) k_col(const __grid_constant__ TPArgs a) {
   constexpr int N1 = Geo2<N>::N1, N2 = Geo2<N>::N2, CW = Geo2<N>::CW;
   constexpr size_t NN = (size_t)N * N;
   constexpr int BOXR = N < 256 ? N : 256;   // rows per TMA box

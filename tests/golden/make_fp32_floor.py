@@ -35,7 +35,7 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 OUT = os.path.join(HERE, "fp32_floor.json")
-WORKLOADS = ("multislice", "tomo")
+WORKLOADS = ("multislice", "tomo", "farfield256")
 
 
 def _transforms(mode):

@@ -20,21 +20,21 @@ def _floor():
 
 def test_floor_file_covers_the_full_size_workloads():
     fl = _floor()
-    assert set(fl["workloads"]) >= {"multislice", "tomo"}
+    assert set(fl["workloads"]) >= {"multislice", "tomo", "farfield256"}
     for name, rec in fl["workloads"].items():
         for mode in ("rounded_transforms", "fp32_fft"):
             for k in ("loss", "gd", "gb", "gp", "gpos"):
                 assert 0.0 < rec[mode][k] < 0.1, (name, mode, k)
 
 
-@pytest.mark.parametrize("name", ["multislice", "tomo"])
+@pytest.mark.parametrize("name", ["multislice", "tomo", "farfield256"])
 def test_fp32_fft_floor_is_at_least_the_rounding_floor(name):
     rec = _floor()["workloads"][name]
     for k in ("gd", "gb", "gp", "gpos"):
         assert rec["fp32_fft"][k] >= rec["rounded_transforms"][k], k
 
 
-@pytest.mark.parametrize("name", ["multislice", "tomo"])
+@pytest.mark.parametrize("name", ["multislice", "tomo", "farfield256"])
 def test_bench_parity_bars_are_the_gpu_test_bars(name):
     import bench
     from tests.test_gpu_parity import full_size_bars

@@ -130,6 +130,13 @@ def test_tomo_full_workload():
     _full("tomo")
 
 
+def test_farfield256_full_workload():
+    """One serving-mix request shape at the two-pass tile, full size: 256 x 256 probe, 8 slices,
+    64 positions over a 1024 x 1024 x 8 volume, Poisson; row / column kernels with TMA-staged
+    column tiles, every output compared with the FP64 oracle."""
+    _full("farfield256")
+
+
 def test_multimode_probe():
     """Five incoherent probe modes (the paper's fly-scan / ptychotomography setting)."""
     case = C.small_case(N=64, L=6, M=5, B=6, loss="lsq", seed=31)
