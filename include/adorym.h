@@ -242,7 +242,9 @@ typedef struct adorym_request {
  * shape and slot), so requests that arrive while others run overlap with them on the device.
  * Half of the slots (rounded down) are reserved for short requests (B M L N^2 pixel-slices of at
  * most 2^26, doubled for N >= 256) and run at the device's highest stream priority, so a short
- * request does not wait behind long ones, neither for a slot nor on the device.
+ * request does not wait behind long ones for a slot (a short request that takes a short-request
+ * slot while a long one waits for a normal slot neither waits nor counts as overtaking it) and its
+ * thread blocks are scheduled first when SMs free up.
  * Completion is event driven (a blocked waiter per slot, no polling).  Array pointers must be
  * device memory and stay valid until the request completes.  Requests whose footprint can never
  * fit return ENOMEM at submit. */

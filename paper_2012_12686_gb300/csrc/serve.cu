@@ -273,20 +273,28 @@ static int free_slot_for(const Serve& S, const Ticket& t) {
 
 // admit one queued request if one may go now: the head if a slot and memory are free for it;
 // else, unless the head has been overtaken kMaxOvertakes times already, the oldest later request
-// for which they are
+// for which they are.  A later request that takes a short-request slot while a long head waits
+// for a normal slot does not compete with it: it is always allowed and does not count as an
+// overtake (a long request can never use that slot).
 static bool admit_one(adorym_ctx* ctx, Serve& S) {
+  bool head_closed = false;      // the head has been overtaken kMaxOvertakes times
+  bool head_wants_slot = false;  // the head is long and waits for a normal slot (memory not tried)
   for (size_t i = 0; i < S.queue.size(); ++i) {
     const uint64_t id = S.queue[i];
     Ticket& t = S.tickets[id];
     const int slot = free_slot_for(S, t);
+    const bool beside_head = i > 0 && head_wants_slot && slot >= 0 && S.slots[slot].fast;
     size_t off = 0;
-    if (slot < 0 || !S.arena.alloc(t.plan.total, &off)) {
+    if (slot < 0 || (head_closed && !beside_head) || !S.arena.alloc(t.plan.total, &off)) {
       if (!t.waited) S.waits++;
       t.waited = true;
-      if (i == 0 && t.overtaken >= kMaxOvertakes) return false;
+      if (i == 0) {
+        head_closed = t.overtaken >= kMaxOvertakes;
+        head_wants_slot = slot < 0 && !t.is_short;
+      }
       continue;
     }
-    if (i > 0) S.tickets[S.queue.front()].overtaken++;
+    if (i > 0 && !beside_head) S.tickets[S.queue.front()].overtaken++;
     S.queue.erase(S.queue.begin() + (std::ptrdiff_t)i);
     t.slot = slot;
     t.ws_off = off;
