@@ -8,18 +8,21 @@
 
 namespace adorym {
 
-// Exact binary32 -> binary64 widening from the IEEE 754 encodings, in integer arithmetic: same
-// sign, biased exponent moved from bias 127 to bias 1023, 23-bit significand placed at the top
-// of the 52-bit one.  Infinities and NaNs keep the all-ones exponent.  Subnormal inputs
-// (|x| < 2^-126) become a signed zero: an absolute change below 1.2e-38.
+// Exact binary32 -> binary64 widening from the IEEE 754 encodings, in integer arithmetic.  With
+// a = |x| as bits (biased exponent e in bits 23..30, significand m in bits 0..22), a >> 3 puts e at
+// bit 20 and the top 20 significand bits below it, so adding (1023 - 127) << 20 rebiases the
+// exponent; the 3 lowest significand bits become the top of the low word.  Infinities and NaNs
+// (e = 255) get the rebias that lands on the all-ones exponent 2047 instead; zeros and subnormal
+// inputs (|x| < 2^-126) become a signed zero (an absolute change below 1.2e-38).  About ten
+// integer instructions, none on the FP64 pipe.
 __device__ __forceinline__ double f32_to_f64(float x) {
   const unsigned u = __float_as_uint(x);
-  const unsigned e = (u >> 23) & 0xFFu;
-  const unsigned sign = u & 0x80000000u;
-  const unsigned m = u & 0x7FFFFFu;
-  const unsigned ed = (e == 0xFFu) ? 0x7FFu : e + (1023u - 127u);
-  const unsigned hi = (e == 0u) ? sign : (sign | (ed << 20) | (m >> 3));
-  const unsigned lo = (e == 0u) ? 0u : (m << 29);
+  const unsigned a = u & 0x7FFFFFFFu;
+  const bool tiny = a < 0x00800000u;
+  const unsigned bias = tiny ? 0u : (a >= 0x7F800000u ? 0x70000000u : 0x38000000u);
+  const unsigned mag = tiny ? 0u : a;
+  const unsigned hi = ((mag >> 3) + bias) | (u & 0x80000000u);
+  const unsigned lo = mag << 29;
   return __hiloint2double((int)hi, (int)lo);
 }
 
