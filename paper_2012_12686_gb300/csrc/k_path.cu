@@ -122,10 +122,15 @@ __global__ void __launch_bounds__(Geo<N>::NT) k_probe_grad(const float2* __restr
   extern __shared__ float2 sm[];
   float2* A = sm;
   float2* tw = A + N * F::LD;
-  if (loss_out && blockIdx.x == 0 && threadIdx.x == 0) {
+  if (loss_out && blockIdx.x == 0 && threadIdx.x < 32) {
+    // FP64 sum of the per-position partials in a fixed order: lane l adds positions l, l + 32, ...
+    // in turn, then a fixed xor tree over the lanes (one warp keeps B / 32 loads in flight instead of
+    // one thread walking all B partials)
     double s = 0.0;
-    for (int b = 0; b < B; ++b) s += lossp[b];
-    *loss_out = s * inv_npix;
+    for (int b = (int)threadIdx.x; b < B; b += 32) s += lossp[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) *loss_out = s * inv_npix;
   }
   if (!g) return;
   const float2* q = qsum + blockIdx.x * NN;

@@ -107,47 +107,79 @@ __device__ __forceinline__ Region region(const int* __restrict__ box, int Lz) {
   return r;
 }
 
+// Work split of the box kernels below: a warp takes one chunk of PER_LANE x 32 consecutive voxels
+// of a box row (z, y) at a time, lanes along x, so the row and column of a voxel come from one
+// integer division per chunk instead of per voxel, and each lane keeps PER_LANE loads in flight.
+struct BoxChunks {
+  static constexpr int PER_LANE = 4;
+  unsigned y0, h, cpr, items;   // first box row, box rows per slice, chunks per row, chunks in the box
+  __device__ BoxChunks(const Region& R, int Lz) {
+    y0 = (unsigned)R.y0;
+    h = (unsigned)R.h;
+    cpr = (unsigned)((R.w + 32 * PER_LANE - 1) / (32 * PER_LANE));
+    items = (unsigned)Lz * h * cpr;
+  }
+  __device__ static unsigned first() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+  __device__ static unsigned stride() { return (gridDim.x * blockDim.x) >> 5; }
+  // chunk -> slice z, volume row y, first column xc of the chunk relative to the box
+  __device__ void split(unsigned item, int* z, int* y, int* xc) const {
+    const unsigned row = item / cpr, c = item - row * cpr;
+    const unsigned zz = row / h;
+    *z = (int)zz;
+    *y = (int)(y0 + row - zz * h);
+    *xc = (int)c * 32 * PER_LANE;
+  }
+};
+
 // T = exp(-kdz beta) exp(i kdz delta) of the (optionally rotated) volume over the box, Eq.
 // ri_modulation.  Computed once per call so the fused kernels gather a complex64 per voxel
 // instead of evaluating sincos/exp for every (position, slice, pixel) they touch.
 template <bool ROT>
-__global__ void k_transmission(const float* __restrict__ vd, const float* __restrict__ vb, float2* __restrict__ T,
-                               int Lz, int Ly, int Lx, float kdz, float c, float s, const int* __restrict__ box,
-                               double* __restrict__ zero_a, double* __restrict__ zero_b) {
+__global__ void __launch_bounds__(256) k_transmission(const float* __restrict__ vd, const float* __restrict__ vb,
+                                                      float2* __restrict__ T, int Lz, int Ly, int Lx, float kdz,
+                                                      float c, float s, const int* __restrict__ box,
+                                                      double* __restrict__ zero_a, double* __restrict__ zero_b) {
   const Region R = region(box, Lz);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n; i += (size_t)gridDim.x * blockDim.x) {
-    const int xt = R.x0 + (int)(i % R.w);
-    const int y = R.y0 + (int)((i / R.w) % R.h);
-    const int zt = (int)(i / ((size_t)R.w * R.h));
-    const size_t io = ((size_t)zt * Ly + y) * Lx + xt;
-    float sd, sb;
-    if (ROT) {
-      const Tap t = tap(zt, xt, Lz, Lx, c, s);
-      sd = 0.f;
-      sb = 0.f;
+  BoxChunks K(R, Lz);
+  for (unsigned item = K.first(); item < K.items; item += K.stride()) {
+    int zt, y, xc;
+    K.split(item, &zt, &y, &xc);
+    const size_t base = ((size_t)zt * Ly + y) * Lx;
 #pragma unroll
-      for (int dz = 0; dz < 2; ++dz) {
+    for (int u = 0; u < BoxChunks::PER_LANE; ++u) {
+      const int xi = xc + 32 * u + (int)(threadIdx.x & 31);
+      if (xi >= R.w) break;
+      const int xt = R.x0 + xi;
+      const size_t io = base + xt;
+      float sd, sb;
+      if (ROT) {
+        const Tap t = tap(zt, xt, Lz, Lx, c, s);
+        sd = 0.f;
+        sb = 0.f;
 #pragma unroll
-        for (int dx = 0; dx < 2; ++dx) {
-          const int z = t.fz + dz, x = t.fx + dx;
-          if (z < 0 || z >= Lz || x < 0 || x >= Lx) continue;
-          const float w = (dz ? t.az : 1.f - t.az) * (dx ? t.ax : 1.f - t.ax);
-          const size_t o = ((size_t)z * Ly + y) * Lx + x;
-          sd = fmaf(w, __ldg(vd + o), sd);
-          sb = fmaf(w, __ldg(vb + o), sb);
+        for (int dz = 0; dz < 2; ++dz) {
+#pragma unroll
+          for (int dx = 0; dx < 2; ++dx) {
+            const int z = t.fz + dz, x = t.fx + dx;
+            if (z < 0 || z >= Lz || x < 0 || x >= Lx) continue;
+            const float w = (dz ? t.az : 1.f - t.az) * (dx ? t.ax : 1.f - t.ax);
+            const size_t o = ((size_t)z * Ly + y) * Lx + x;
+            sd = fmaf(w, __ldg(vd + o), sd);
+            sb = fmaf(w, __ldg(vb + o), sb);
+          }
         }
+      } else {
+        sd = __ldg(vd + io);
+        sb = __ldg(vb + io);
       }
-    } else {
-      sd = __ldg(vd + io);
-      sb = __ldg(vb + io);
-    }
-    float sn, cs;
-    sincosf(kdz * sd, &sn, &cs);
-    const float e = expf(-kdz * sb);
-    T[io] = make_float2(e * cs, e * sn);
-    if (zero_a) {
-      zero_a[io] = 0.0;
-      zero_b[io] = 0.0;
+      float sn, cs;
+      sincosf(kdz * sd, &sn, &cs);
+      const float e = expf(-kdz * sb);
+      T[io] = make_float2(e * cs, e * sn);
+      if (zero_a) {
+        zero_a[io] = 0.0;
+        zero_b[io] = 0.0;
+      }
     }
   }
 }
@@ -224,18 +256,34 @@ __global__ void __launch_bounds__(256) k_rotate_adj(const double* __restrict__ g
 }
 
 // FP64 object-gradient accumulators (zeroed over the box by the transmission pass): add the box
-// into the caller's gradient
-__global__ void k_grad_add(const double* __restrict__ ad, const double* __restrict__ ab, float* __restrict__ gd,
-                           float* __restrict__ gb, int Lz, int Ly, int Lx, const int* __restrict__ box) {
+// into the caller's gradient (work split as in BoxChunks)
+__global__ void __launch_bounds__(256) k_grad_add(const double* __restrict__ ad, const double* __restrict__ ab,
+                                                  float* __restrict__ gd, float* __restrict__ gb, int Lz, int Ly,
+                                                  int Lx, const int* __restrict__ box) {
   const Region R = region(box, Lz);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < R.n; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t io = ((size_t)(i / ((size_t)R.w * R.h)) * Ly + R.y0 + (i / R.w) % R.h) * Lx + R.x0 + i % R.w;
-    gd[io] += f64_to_f32(ad + io);   // narrowed in integer arithmetic, then one FP32 add
-    gb[io] += f64_to_f32(ab + io);
+  BoxChunks K(R, Lz);
+  for (unsigned item = K.first(); item < K.items; item += K.stride()) {
+    int z, y, xc;
+    K.split(item, &z, &y, &xc);
+    const size_t base = ((size_t)z * Ly + y) * Lx + R.x0;
+#pragma unroll
+    for (int u = 0; u < BoxChunks::PER_LANE; ++u) {
+      const int xi = xc + 32 * u + (int)(threadIdx.x & 31);
+      if (xi >= R.w) break;
+      const size_t io = base + xi;
+      gd[io] += f64_to_f32(ad + io);   // narrowed in integer arithmetic, then one FP32 add
+      gb[io] += f64_to_f32(ab + io);
+    }
   }
 }
 
 static unsigned vol_grid(size_t n) { return (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16); }
+// one warp per BoxChunks chunk of a box inside Lz x Ly x Lx (eight warps per block), at most 16
+// blocks per SM; the warps loop over the chunks beyond that
+static unsigned box_grid(int Lz, int Ly, int Lx) {
+  const size_t chunks = (size_t)Lz * Ly * (((size_t)Lx + 127) / 128);
+  return (unsigned)std::min<size_t>((chunks + 7) / 8, 152 * 16);
+}
 
 cudaError_t launch_bbox(const float* pos, int B, int N, int Ly, int Lx, int far, int full_x, int* box,
                         int npos_values, int* status, cudaStream_t s, int* zero, int nzero) {
@@ -246,7 +294,7 @@ cudaError_t launch_bbox(const float* pos, int B, int N, int Ly, int Lx, int far,
 cudaError_t launch_transmission(const float* vd, const float* vb, float2* T, int Lz, int Ly, int Lx, float kdz,
                                 int rotate, float c, float sn, const int* box, double* zero_a, double* zero_b,
                                 cudaStream_t s) {
-  const unsigned grid = vol_grid((size_t)Lz * Ly * Lx);
+  const unsigned grid = box_grid(Lz, Ly, Lx);
   if (rotate) (k_transmission<true><<<grid, 256, 0, s>>>(vd, vb, T, Lz, Ly, Lx, kdz, c, sn, box, zero_a, zero_b), note_launch());
   else (k_transmission<false><<<grid, 256, 0, s>>>(vd, vb, T, Lz, Ly, Lx, kdz, c, sn, box, zero_a, zero_b), note_launch());
   return cudaGetLastError();
@@ -262,7 +310,7 @@ cudaError_t launch_rotate_adj(const double* gdr, const double* gbr, float* gd, f
 
 cudaError_t launch_grad_add(const double* ad, const double* ab, float* gd, float* gb, int Lz, int Ly, int Lx,
                             const int* box, cudaStream_t s) {
-  (k_grad_add<<<vol_grid((size_t)Lz * Ly * Lx), 256, 0, s>>>(ad, ab, gd, gb, Lz, Ly, Lx, box), note_launch());
+  (k_grad_add<<<box_grid(Lz, Ly, Lx), 256, 0, s>>>(ad, ab, gd, gb, Lz, Ly, Lx, box), note_launch());
   return cudaGetLastError();
 }
 
