@@ -793,7 +793,12 @@ static int run_call(adorym_ctx* ctx, const adorym_problem* p, int obj_id, const 
   }
   if (ADORYM_SIDE_STREAM && !two_pass(p->N)) {
     if (!ctx->side_stream) {
-      bool ok = cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking) == cudaSuccess;
+      // highest priority: the one-CTA probe kernels on it must not queue behind the many-block
+      // box kernels of the call's stream that they overlap (transmission before the fused kernel,
+      // object-gradient add after it)
+      int least = 0, greatest = 0;
+      bool ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess;
+      ok = ok && cudaStreamCreateWithPriority(&ctx->side_stream, cudaStreamNonBlocking, greatest) == cudaSuccess;
       for (cudaEvent_t& e : ctx->ev_side) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
       if (!ok) return cuda_fail(ctx, cudaGetLastError(), "side stream");
     }
