@@ -141,13 +141,25 @@ __global__ void __launch_bounds__(256) k_transmission(const float* __restrict__ 
                                                       double* __restrict__ zero_a, double* __restrict__ zero_b) {
   const Region R = region(box, Lz);
   BoxChunks K(R, Lz);
+  constexpr int U = BoxChunks::PER_LANE;
   for (unsigned item = K.first(); item < K.items; item += K.stride()) {
     int zt, y, xc;
     K.split(item, &zt, &y, &xc);
     const size_t base = ((size_t)zt * Ly + y) * Lx;
+    const int x0 = xc + (int)(threadIdx.x & 31);
+    // unrotated volume: all of the chunk's loads first, so that they are in flight together
+    float ld[U], lb[U];
+    if (!ROT) {
 #pragma unroll
-    for (int u = 0; u < BoxChunks::PER_LANE; ++u) {
-      const int xi = xc + 32 * u + (int)(threadIdx.x & 31);
+      for (int u = 0; u < U; ++u) {
+        const bool in = x0 + 32 * u < R.w;
+        ld[u] = in ? __ldg(vd + base + R.x0 + x0 + 32 * u) : 0.f;
+        lb[u] = in ? __ldg(vb + base + R.x0 + x0 + 32 * u) : 0.f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int xi = x0 + 32 * u;
       if (xi >= R.w) break;
       const int xt = R.x0 + xi;
       const size_t io = base + xt;
@@ -169,8 +181,8 @@ __global__ void __launch_bounds__(256) k_transmission(const float* __restrict__ 
           }
         }
       } else {
-        sd = __ldg(vd + io);
-        sb = __ldg(vb + io);
+        sd = ld[u];
+        sb = lb[u];
       }
       float sn, cs;
       sincosf(kdz * sd, &sn, &cs);
@@ -262,17 +274,29 @@ __global__ void __launch_bounds__(256) k_grad_add(const double* __restrict__ ad,
                                                   int Lx, const int* __restrict__ box) {
   const Region R = region(box, Lz);
   BoxChunks K(R, Lz);
+  constexpr int U = BoxChunks::PER_LANE;
   for (unsigned item = K.first(); item < K.items; item += K.stride()) {
     int z, y, xc;
     K.split(item, &z, &y, &xc);
     const size_t base = ((size_t)z * Ly + y) * Lx + R.x0;
+    const int x0 = xc + (int)(threadIdx.x & 31);
+    // all of the chunk's loads first (in flight together), then the adds and stores
+    float gd_[U], gb_[U], ad_[U], ab_[U];
 #pragma unroll
-    for (int u = 0; u < BoxChunks::PER_LANE; ++u) {
-      const int xi = xc + 32 * u + (int)(threadIdx.x & 31);
-      if (xi >= R.w) break;
-      const size_t io = base + xi;
-      gd[io] += f64_to_f32(ad + io);   // narrowed in integer arithmetic, then one FP32 add
-      gb[io] += f64_to_f32(ab + io);
+    for (int u = 0; u < U; ++u) {
+      const bool in = x0 + 32 * u < R.w;
+      const size_t io = base + x0 + 32 * u;
+      ad_[u] = in ? f64_to_f32(ad + io) : 0.f;   // narrowed in integer arithmetic
+      ab_[u] = in ? f64_to_f32(ab + io) : 0.f;
+      gd_[u] = in ? gd[io] : 0.f;
+      gb_[u] = in ? gb[io] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (x0 + 32 * u >= R.w) break;
+      const size_t io = base + x0 + 32 * u;
+      gd[io] = gd_[u] + ad_[u];   // one FP32 add
+      gb[io] = gb_[u] + ab_[u];
     }
   }
 }
