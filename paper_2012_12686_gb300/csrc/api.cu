@@ -123,7 +123,6 @@ int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan
       q.off_ckpt = take(B * M * q.ncp * NN * f2);
       q.off_seg = take(B * M * (q.pipe ? 2 : 1) * q.cp * NN * f2);
       q.off_park = take(B * N * path_field_ld((int)N) * f2);
-      if (pipe_offload(q)) q.off_pbar = take(B * 2 * q.cp * NN * f2);
       if (!q.far) q.off_fbar = take(B * NN * f2);
       q.off_qacc = take(B * M * NN * f2);
       q.off_qsum = take(M * NN * f2);
@@ -436,7 +435,6 @@ int enqueue(const Plan& pl, const Object& obj, const Tables& tab, const CallPtrs
       a.ckpt = reinterpret_cast<float2*>(W(pl.off_ckpt));
       a.seg = reinterpret_cast<float2*>(W(pl.off_seg));
       a.park = reinterpret_cast<float2*>(W(pl.off_park));
-      a.pbar = pipe_offload(pl) ? reinterpret_cast<float2*>(W(pl.off_pbar)) : nullptr;
       a.fbar = pl.far ? nullptr : reinterpret_cast<float2*>(W(pl.off_fbar));
       a.qacc = pl.want_probe ? reinterpret_cast<float2*>(W(pl.off_qacc)) : nullptr;
       a.gd = pl.want_obj ? gd : nullptr;

@@ -34,7 +34,7 @@ struct Plan {
   bool pipe = false;   // shared-memory path: two-CTA clusters (adjoint + segment recompute)
   int helpers = 0;     // shared-memory path: recompute-helper CTAs on SMs the batch leaves idle
   size_t NN = 0;
-  size_t off_phat = 0, off_ckpt = 0, off_seg = 0, off_park = 0, off_pbar = 0, off_far = 0, off_gI = 0, off_fbar = 0,
+  size_t off_phat = 0, off_ckpt = 0, off_seg = 0, off_park = 0, off_far = 0, off_gI = 0, off_fbar = 0,
          off_lossp = 0, off_qacc = 0, off_qsum = 0, off_T = 0, off_grot = 0, off_loss = 0;
   // two-pass path (N >= 256)
   size_t off_FA = 0, off_FR = 0, off_tmp = 0, off_posp = 0;
@@ -50,17 +50,6 @@ struct Plan {
   size_t bytes_probe = 0, bytes_pos = 0, bytes_meas = 0, bytes_iout = 0;
   size_t total = 0;
 };
-
-// ADORYM_PIPE_OFFLOAD: in the pipelined form at N <= 64 the recompute CTA forms the FP64 object
-// gradient of every second slice of a segment from the adjoint fields the sweep CTA stores (0: the
-// sweep CTA adds all of it itself).  Near field with one mode adds its gradient in place, without
-// FP64 accumulators, and is not offloaded.
-#ifndef ADORYM_PIPE_OFFLOAD
-#define ADORYM_PIPE_OFFLOAD 1
-#endif
-inline bool pipe_offload(const Plan& q) {
-  return ADORYM_PIPE_OFFLOAD && q.pipe && q.want_obj && q.p.N <= 64 && (q.far || q.p.M > 1);
-}
 
 // Device pointers of one call after staging.
 struct CallPtrs {

@@ -447,48 +447,6 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
   // ------------------------------------------------------------------ adjoint
   double gacc[3 * 4] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};   // per distance: shift y, x; N_F
   const bool want_obj = a.gd != nullptr;   // FP64 accumulators (else a.gdf or nothing)
-  // pipelined form, N <= 64: for every second slice of a segment (odd j - j0) rank 0 stores
-  // psibar_j and rank 1 forms the FP64 object gradient one segment later, beside its recompute.
-  // Rank 0's reverse sweep of a segment is longer than rank 1's recompute of one; moving all the
-  // slices made rank 1 the longer one (tomography: 1.200 against 1.155 ms), and at N = 128 the
-  // extra code spilled.
-  constexpr bool CAN_OFFLOAD = PIPE && N <= 64;
-  const bool offload = CAN_OFFLOAD && want_obj && a.pbar != nullptr && !(!FAR && a.gdf);
-  float2* pbar_b = offload ? a.pbar + (size_t)b * 2 * cp * NN : nullptr;
-  // dL/d(delta, beta)_j += kdz (Im, -Re)(psibar_j conj(psi_j)) for the odd slices of segment s of
-  // mode m, from the psibar_j rank 0 stored (slot s % 2) and the psi_j of segment slot s % 2;
-  // pixels in row-major order across the CTA, all of a slice's loads in flight together
-  auto object_grad = [&](int m, int s) {
-    if constexpr (CAN_OFFLOAD) {
-      constexpr int E = (int)(NN / NT);   // pixels per thread and slice
-      static_assert(E * NT == (int)NN, "whole slices per CTA pass");
-      const int j0 = s * cp, j1 = min(j0 + cp, L) - 1;
-      const float2* sgs = seg_slot(m, s);
-      const float2* pbs = pbar_b + (size_t)(s & 1) * cp * NN;
-      for (int j = j0 + 1; j <= j1; j += 2) {
-        float2 u[E], w[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const size_t i = (size_t)(j - j0) * NN + threadIdx.x + e * NT;
-          u[e] = __ldcg(pbs + i);
-          w[e] = __ldcg(sgs + i);
-        }
-        const int gz = FAR ? j : b * L + j;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const float2 z = cmulc(u[e], w[e]);   // psibar conj(psi)
-          const int i = (int)threadIdx.x + e * NT, y = i / N, x = i % N;
-          const int gy = p0y + y, gx = p0x + x;
-          if (interior || (gy >= 0 && gy < Ly && gx >= 0 && gx < Lx)) {
-            const size_t o = ((size_t)gz * Ly + gy) * Lx + gx;
-            atomicAdd(a.gd + o, f32_to_f64(kdz * z.y));
-            atomicAdd(a.gb + o, f32_to_f64(-kdz * z.x));
-          }
-        }
-      }
-      __syncthreads();   // every read of the segment slot precedes the recompute that overwrites it
-    }
-  };
   for (int m = 0; m < M; ++m) {
     cur_mode = m;
     float2* ck = ck_b + (size_t)m * ncp * NN;
@@ -531,17 +489,11 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
       // checkpoints (and, for m > 0, the previous mode's sweep) are complete
       cluster_barrier();
       if (rank == 1) {
-        // recompute segment s - 1 while rank 0 reverses segment s; one barrier per segment.  With
-        // the gradient offloaded, first add the offloaded object gradient of segment s + 1
-        // (reversed by rank 0 in the previous period; its psi_j are still in slot (s + 1) % 2,
-        // which the recompute of s - 1 then overwrites), and after the last period that of
-        // segment 0
+        // recompute segment s - 1 while rank 0 reverses segment s; one barrier per segment
         for (int s = ncp - 1; s >= 0; --s) {
-          if (offload && s + 1 <= ncp - 1) object_grad(m, s + 1);
           if (s >= 1 && min((s - 1) * cp + cp, L) - 1 > (s - 1) * cp) recompute(s - 1, seg_slot(m, s - 1));
           cluster_barrier();
         }
-        if (offload) object_grad(m, 0);
         continue;
       }
     }
@@ -646,19 +598,15 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
       for (int j = j1; j >= j0; --j) {
         const bool first = (j == 0);
         // prefetch T_j and psi_j (checkpoint or recomputed segment)
-        const bool off_j = offload && ((j - j0) & 1);   // rank 1 forms this slice's object gradient
-        auto pre = [&, j, off_j](V1& pa, V1& pb, int x, int t) {
+        auto pre = [&, j](V1& pa, V1& pb, int x, int t) {
           const float2* seg_j = from_helper ? a.hseg + (((size_t)b * M + m) * (ncp - 1) + s) * cp * NN : sg;
           const float2* src = (j == j0) ? ck + (size_t)s * NN : seg_j + (size_t)(j - j0) * NN;
           tloads(pa, j, x, t);
-          if (!off_j) {
 #pragma unroll
-            for (int k = 0; k < CY; ++k) pb[k] = __ldcg(src + (YS * k + t) * N + x);   // L2: written by the partner CTA
-          }
+          for (int k = 0; k < CY; ++k) pb[k] = __ldcg(src + (YS * k + t) * N + x);   // L2: written by the partner CTA
         };
-        float2* pbj = off_j ? pbar_b + ((size_t)(s & 1) * cp + (j - j0)) * NN : nullptr;
         float2* q0 = (!FAR && first && a.qacc) ? a.qacc + ((size_t)b * M + m) * NN : nullptr;
-        auto op = [&, j, q0, pbj, off_j](V1& v, V1& pa, V1& pb, int x, int t) {
+        auto op = [&, j, q0](V1& v, V1& pa, V1& pb, int x, int t) {
           const size_t o0 = interior ? voff(j, t, x) : 0;
 #pragma unroll
           for (int k = 0; k < CY; ++k) {
@@ -670,8 +618,6 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
               const size_t o = voff(j, t, x) + (size_t)(YS * k) * Lx;
               a.gdf[o] += kdz * z.y;
               a.gbf[o] -= kdz * z.x;
-            } else if (off_j) {
-              pbj[y * N + x] = pbar;                    // the partner CTA forms the gradient
             } else if (want_obj) {
               const float2 z = cmulc(pbar, pb[k]);      // psibar conj(psi)
               size_t o = o0 + (size_t)(YS * k) * Lx;

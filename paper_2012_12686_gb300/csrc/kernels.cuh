@@ -62,8 +62,6 @@ struct PathArgs {
   float2* ckpt;           // [B][M][ncp][N*N] checkpoints psi_{j0}
   float2* seg;            // [B][M][cp][N*N] recomputed psi_j of one segment
   float2* park;           // [B][N*(N+1)] adjoint field parked during a recompute
-  float2* pbar;           // pipelined form: [B][2][cp][N*N] psibar_j of a segment (slot = s % 2), for the
-                          // partner CTA's object-gradient pass; null: rank 0 adds the gradient itself
   float2* far;            // [B][M][N*N] detector field (far) or [B][n_dist][M][N*N] (near)
   float* gI;              // [B][N*N] (or [B][n_dist][N*N]) intensity, then dL/dI
   float2* fbar;           // near field: [B][N*N] accumulated Fourier-space adjoint
