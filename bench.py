@@ -829,7 +829,7 @@ def parity_bars(workload: str):
     return bars
 
 
-KERNEL_SOURCES = ("k_path.cuh", "fft_block.cuh", "fft_block4.cuh", "fft_warp64.cuh", "numerics.cuh", "kernels.cuh")
+KERNEL_SOURCES = ("k_path.cuh", "fft_block.cuh", "fft_block4.cuh", "numerics.cuh", "kernels.cuh")
 
 
 def kernel_source_bytes() -> bytes:

@@ -122,7 +122,7 @@ int make_plan(const adorym_problem& p, bool adj, int grads, bool want_loss, Plan
     if (adj) {
       q.off_ckpt = take(B * M * q.ncp * NN * f2);
       q.off_seg = take(B * M * (q.pipe ? 2 : 1) * q.cp * NN * f2);
-      q.off_park = take(B * N * path_field_ld((int)N) * f2);
+      q.off_park = take(B * N * (N + 1) * f2);
       if (!q.far) q.off_fbar = take(B * NN * f2);
       q.off_qacc = take(B * M * NN * f2);
       q.off_qsum = take(M * NN * f2);

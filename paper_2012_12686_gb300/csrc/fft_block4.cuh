@@ -25,7 +25,6 @@
 // index t k stays below N.
 #pragma once
 #include "fft_block.cuh"
-#include "fft_warp64.cuh"
 
 namespace adorym {
 
@@ -173,17 +172,11 @@ namespace adorym {
 //                                              where they are separate passes)
 //   r23<S2, S3>(A, tw, op)                     x-S2 | frequency op | x-S3
 //   inv_pair<S>(A, tw)                         x-S4 then y-S3
-// N <= 64: the six-pass scheme of fft_block.cuh (at N = 64 the warp-exchange scheme of
-// fft_warp64.cuh with ADORYM_WARP64=1); N = 128: the four-pass scheme above.
-// LD: leading dimension of the field in shared memory; SCRATCH: float2 of scratch the scheme keeps
-// just before the field; PAIRS: fwd_pair / inv_pair touch shared memory (and need the barrier
-// after them).
+// N <= 64: the six-pass scheme of fft_block.cuh; N = 128: the four-pass scheme above.
 template <int N>
 struct PathFFT {
   using F = Field<N>;
   static constexpr int CY = F::N1, YS = F::N2, RX = F::N2, KXS = F::N1;
-  static constexpr int LD = F::LD, SCRATCH = 0;
-  static constexpr bool PAIRS = true;
   template <int S4, int S1, bool LOAD, bool STORE, class Pre, class Op>
   __device__ static __forceinline__ void c14(float2* A, const float2* tw, Pre pre, Op op) {
     pass_c14<N, S4, S1, LOAD, STORE>(A, tw, pre, op);
@@ -210,8 +203,6 @@ template <int N>
 struct PathFFT4 {
   using G = G4<N>;
   static constexpr int CY = G::NY1, YS = G::NY2, RX = G::NX2, KXS = G::NX1;
-  static constexpr int LD = G::LD, SCRATCH = 0;
-  static constexpr bool PAIRS = true;
   template <int S4, int S1, bool LOAD, bool STORE, class Pre, class Op>
   __device__ static __forceinline__ void c14(float2* A, const float2* tw, Pre pre, Op op) {
     static_assert(Geo<N>::NT == G::NT, "the four-pass scheme sets the CTA's thread count");
@@ -236,9 +227,6 @@ struct PathFFT<128> : PathFFT4<128> {};
 #if ADORYM_FOURPASS64
 template <>
 struct PathFFT<64> : PathFFT4<64> {};
-#elif ADORYM_WARP64
-template <>
-struct PathFFT<64> : PathFFTW64 {};
 #endif
 
 }  // namespace adorym

@@ -125,13 +125,12 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
   static_assert(!(HELP && (GAP || PIPE)), "recompute helpers serve the plain one-CTA form only");
   using F = Field<N>;
   using X = PathFFT<N>;
-  constexpr int CY = X::CY, YS = X::YS, RX = X::RX, KXS = X::KXS, LD = X::LD, NT = F::NT;
-  static_assert(LD == path_field_ld(N), "park buffer and field share one leading dimension");
+  constexpr int CY = X::CY, YS = X::YS, RX = X::RX, KXS = X::KXS, LD = F::LD, NT = F::NT;
   constexpr size_t NN = (size_t)N * N;
   using V1 = float2[CY];
   using V2 = float2[RX];
   extern __shared__ float2 sm[];
-  float2* A = sm + X::SCRATCH;         // the pass scheme's scratch, if any, lies before the field
+  float2* A = sm;
   float2* tw = A + N * LD;             // F::TW_ENTRIES twiddles (tw, then the per-stage tables)
   float2* hy = tw + F::TW_ENTRIES;
   float2* hx = hy + N;
@@ -195,7 +194,7 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
   // accumulates dL/dc_gap = -pi sum |f|^2 Im(conj(F[psibar]) F[psi]) into gapp
   auto propagate_tail = [&](bool adjoint, int gapj, float2* spec_out, const float2* spec_in) {
     X::template fwd_pair<-1>(A, tw);
-    if constexpr (X::PAIRS) __syncthreads();
+    __syncthreads();
     float gs = 0.f;
     if constexpr (GAP) {
       const float2* hyp = a.hyj + (size_t)gapj * N;
@@ -234,7 +233,7 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
     }
     __syncthreads();
     X::template inv_pair<+1>(A, tw);
-    if constexpr (X::PAIRS) __syncthreads();
+    __syncthreads();
     if constexpr (GAP) {
       if (adjoint && spec_in) {
         const double g = block_sum<NT>(f32_to_f64(gs), red);
@@ -309,7 +308,7 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
       });
       __syncthreads();
       X::template inv_pair<+1>(A, tw);
-      if constexpr (X::PAIRS) __syncthreads();
+      __syncthreads();
     }
     for (int j = 0; j < L; ++j) {
       const bool last = (j == L - 1);
@@ -342,7 +341,7 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
       if (FAR) {
         // Psi = (1/N) DFT_+[phi]; keep Psi, accumulate I over modes
         X::template fwd_pair<+1>(A, tw);
-        if constexpr (X::PAIRS) __syncthreads();
+        __syncthreads();
         float2* fm = a.far + ((size_t)b * M + m) * NN;
         X::template r23<+1, 0>(A, tw, [&](V2& v, int ky, int t) {
 #pragma unroll
@@ -358,7 +357,7 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
       } else {
         // Phi = DFT_-[phi] kept at slot n_dist; then Psi_d = IDFT_-{Phi G_d} per distance
         X::template fwd_pair<-1>(A, tw);
-        if constexpr (X::PAIRS) __syncthreads();
+        __syncthreads();
         float2* Phi = a.far + (((size_t)b * (nd + 1) + nd) * M + m) * NN;
         X::template r23<-1, 0>(A, tw, [&](V2& v, int ky, int t) {
 #pragma unroll
@@ -381,7 +380,7 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
           });
           __syncthreads();
           X::template inv_pair<+1>(A, tw);
-          if constexpr (X::PAIRS) __syncthreads();
+          __syncthreads();
           float2* fd = a.far + (((size_t)b * (nd + 1) + d) * M + m) * NN;
           float* gId = gI_b + (size_t)d * NN;
           X::template c14<+1, 0, true, false>(A, tw, NoPre(), [&](V1& v, V1&, V1&, int x, int t) {
@@ -510,7 +509,7 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
       });
       __syncthreads();
       X::template inv_pair<-1>(A, tw);
-      if constexpr (X::PAIRS) __syncthreads();
+      __syncthreads();
     } else {
       const float2* Phi = a.far + (((size_t)b * (nd + 1) + nd) * M + m) * NN;
       float2* fb = a.fbar + (size_t)b * NN;
@@ -535,7 +534,7 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
         });
         __syncthreads();
         X::template fwd_pair<-1>(A, tw);
-        if constexpr (X::PAIRS) __syncthreads();
+        __syncthreads();
         const float2* hd = a.hd + (size_t)d * N;
         X::template r23<-1, 0>(A, tw, [&](V2& v, int ky, int t) {
           const float2 gy = cmul(__ldg(&hd[ky]), ry[ky]);
@@ -566,7 +565,7 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
       });
       __syncthreads();
       X::template inv_pair<+1>(A, tw);
-      if constexpr (X::PAIRS) __syncthreads();
+      __syncthreads();
     }
 
     for (int s = ncp - 1; s >= 0; --s) {
@@ -648,7 +647,7 @@ __device__ __forceinline__ void path_body(const PathArgs& a) {
         if (!FAR) continue;
         // far field, j = 0: Q = DFT_-[psibar_0] -> probe and position gradients
         X::template fwd_pair<-1>(A, tw);
-        if constexpr (X::PAIRS) __syncthreads();
+        __syncthreads();
         const float2* ph = a.phat + (size_t)m * NN;
         float2* q = a.qacc ? a.qacc + ((size_t)b * M + m) * NN : nullptr;
         X::template r23<-1, 0>(A, tw, [&](V2& v, int ky, int t) {
@@ -703,13 +702,12 @@ template <int N, int FAR>
 __device__ __forceinline__ void helper_body(const PathArgs& a) {
   using F = Field<N>;
   using X = PathFFT<N>;
-  constexpr int CY = X::CY, YS = X::YS, RX = X::RX, KXS = X::KXS, LD = X::LD, NT = F::NT;
-  static_assert(LD == path_field_ld(N), "park buffer and field share one leading dimension");
+  constexpr int CY = X::CY, YS = X::YS, RX = X::RX, KXS = X::KXS, LD = F::LD, NT = F::NT;
   constexpr size_t NN = (size_t)N * N;
   using V1 = float2[CY];
   using V2 = float2[RX];
   extern __shared__ float2 sm[];
-  float2* A = sm + X::SCRATCH;
+  float2* A = sm;
   float2* tw = A + N * LD;
   float2* hy = tw + F::TW_ENTRIES;
   float2* hx = hy + N;
@@ -786,7 +784,7 @@ __device__ __forceinline__ void helper_body(const PathArgs& a) {
       __syncthreads();
       // propagation tail: C2, R1, R23 (H), R4, C3
       X::template fwd_pair<-1>(A, tw);
-      if constexpr (X::PAIRS) __syncthreads();
+      __syncthreads();
       X::template r23<-1, +1>(A, tw, [&](V2& v, int ky, int t) {
         const float2 h = hy[ky];
 #pragma unroll
@@ -794,7 +792,7 @@ __device__ __forceinline__ void helper_body(const PathArgs& a) {
       });
       __syncthreads();
       X::template inv_pair<+1>(A, tw);
-      if constexpr (X::PAIRS) __syncthreads();
+      __syncthreads();
     }
     X::template c14<+1, 0, true, false>(A, tw, NoPre(), [&](V1& v, V1&, V1&, int x, int t) {
 #pragma unroll
@@ -829,12 +827,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Geo<N>::NT, Geo<N>::
   path_body<N, FAR, false, true>(a);
 }
 
-// pass scratch + field + twiddle tables (3N) + hy, hx, ry, rx tables + one double per warp for
-// block reductions
+// field + twiddle tables (3N) + hy, hx, ry, rx tables + one double per warp for block reductions
 template <int N>
 constexpr int path_smem_bytes_t() {
-  return (PathFFT<N>::SCRATCH + N * PathFFT<N>::LD + Field<N>::TW_ENTRIES + 4 * N) * (int)sizeof(float2) +
-         (Geo<N>::NT / 32) * (int)sizeof(double);
+  return (N * (N + 1) + Field<N>::TW_ENTRIES + 4 * N) * (int)sizeof(float2) + (Geo<N>::NT / 32) * (int)sizeof(double);
 }
 
 template <int N, int FAR, bool GAP>

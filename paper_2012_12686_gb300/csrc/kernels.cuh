@@ -25,20 +25,6 @@ inline int current_device() {
   return (d >= 0 && d < kMaxDevices) ? d : -1;
 }
 
-// ADORYM_WARP64: the fused kernels at N = 64 finish each 1-D transform inside a warp
-// (fft_warp64.cuh: two shared-memory round trips and two CTA barriers per propagation step instead
-// of six).  Off by default: on the tomography workload (64 positions, 128 slices) it made the
-// forward-only launch faster (0.426 against 0.463 ms) but the loss-and-gradient launch slower
-// (1.220 against 1.143 ms), as a warp's global accesses there (checkpoint reads, FP64 gradient
-// atomics) cover 8 rows x 4 columns instead of one row of 32 columns.
-#ifndef ADORYM_WARP64
-#define ADORYM_WARP64 0
-#endif
-
-// Leading dimension (in float2) of the fused kernels' shared-memory field, and of the buffer a
-// position parks that field in while it recomputes a segment.
-__host__ __device__ constexpr int path_field_ld(int N) { return (N == 64 && ADORYM_WARP64) ? 68 : N + 1; }
-
 // One far-field (or near-field) loss/gradient launch over a batch, as seen by the fused kernel.
 struct PathArgs {
   int N, L, M, B, Ly, Lx;
