@@ -147,14 +147,28 @@ __global__ void __launch_bounds__(256) k_transmission(const float* __restrict__ 
     K.split(item, &zt, &y, &xc);
     const size_t base = ((size_t)zt * Ly + y) * Lx;
     const int x0 = xc + (int)(threadIdx.x & 31);
-    // unrotated volume: all of the chunk's loads first, so that they are in flight together
-    float ld[U], lb[U];
-    if (!ROT) {
+    // all of the chunk's loads first, so that they are in flight together: one voxel per lane
+    // and step u (unrotated volume), or the four bilinear taps of each (rotated volume)
+    float ld[U][ROT ? 4 : 1], lb[U][ROT ? 4 : 1];
+    Tap tp[ROT ? U : 1];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const bool in = x0 + 32 * u < R.w;
-        ld[u] = in ? __ldg(vd + base + R.x0 + x0 + 32 * u) : 0.f;
-        lb[u] = in ? __ldg(vb + base + R.x0 + x0 + 32 * u) : 0.f;
+    for (int u = 0; u < U; ++u) {
+      const int xi = x0 + 32 * u;
+      const bool in = xi < R.w;
+      if (ROT) {
+        tp[ROT ? u : 0] = tap(zt, R.x0 + xi, Lz, Lx, c, s);
+        const Tap& t = tp[ROT ? u : 0];
+#pragma unroll
+        for (int q = 0; q < (ROT ? 4 : 1); ++q) {
+          const int z = t.fz + (q >> 1), x = t.fx + (q & 1);
+          const bool ok = in && z >= 0 && z < Lz && x >= 0 && x < Lx;
+          const size_t o = ((size_t)z * Ly + y) * Lx + x;
+          ld[u][q] = ok ? __ldg(vd + o) : 0.f;
+          lb[u][q] = ok ? __ldg(vb + o) : 0.f;
+        }
+      } else {
+        ld[u][0] = in ? __ldg(vd + base + R.x0 + xi) : 0.f;
+        lb[u][0] = in ? __ldg(vb + base + R.x0 + xi) : 0.f;
       }
     }
 #pragma unroll
@@ -165,24 +179,21 @@ __global__ void __launch_bounds__(256) k_transmission(const float* __restrict__ 
       const size_t io = base + xt;
       float sd, sb;
       if (ROT) {
-        const Tap t = tap(zt, xt, Lz, Lx, c, s);
+        // taps in (dz, dx) order, those outside the volume skipped
+        const Tap& t = tp[ROT ? u : 0];
         sd = 0.f;
         sb = 0.f;
 #pragma unroll
-        for (int dz = 0; dz < 2; ++dz) {
-#pragma unroll
-          for (int dx = 0; dx < 2; ++dx) {
-            const int z = t.fz + dz, x = t.fx + dx;
-            if (z < 0 || z >= Lz || x < 0 || x >= Lx) continue;
-            const float w = (dz ? t.az : 1.f - t.az) * (dx ? t.ax : 1.f - t.ax);
-            const size_t o = ((size_t)z * Ly + y) * Lx + x;
-            sd = fmaf(w, __ldg(vd + o), sd);
-            sb = fmaf(w, __ldg(vb + o), sb);
-          }
+        for (int q = 0; q < (ROT ? 4 : 1); ++q) {
+          const int dz = q >> 1, dx = q & 1, z = t.fz + dz, x = t.fx + dx;
+          if (z < 0 || z >= Lz || x < 0 || x >= Lx) continue;
+          const float w = (dz ? t.az : 1.f - t.az) * (dx ? t.ax : 1.f - t.ax);
+          sd = fmaf(w, ld[u][q], sd);
+          sb = fmaf(w, lb[u][q], sb);
         }
       } else {
-        sd = ld[u];
-        sb = lb[u];
+        sd = ld[u][0];
+        sb = lb[u][0];
       }
       float sn, cs;
       sincosf(kdz * sd, &sn, &cs);
