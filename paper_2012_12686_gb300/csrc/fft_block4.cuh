@@ -172,7 +172,8 @@ namespace adorym {
 //                                              where they are separate passes)
 //   r23<S2, S3>(A, tw, op)                     x-S2 | frequency op | x-S3
 //   inv_pair<S>(A, tw)                         x-S4 then y-S3
-// N <= 64: the six-pass scheme of fft_block.cuh; N = 128: the four-pass scheme above.
+// N <= 32: the six-pass scheme of fft_block.cuh; N = 64: its column passes with the row passes in
+// a warp (below); N = 128: the four-pass scheme above.
 template <int N>
 struct PathFFT {
   using F = Field<N>;
@@ -227,6 +228,83 @@ struct PathFFT<128> : PathFFT4<128> {};
 #if ADORYM_FOURPASS64
 template <>
 struct PathFFT<64> : PathFFT4<64> {};
+#else
+// N = 64: the column passes as in the six-pass scheme, the x transforms of a step in one row pass.
+// The eight tasks of a row (t < 8) are eight lanes of one warp, so the slot exchange between a
+// row's two radix-8 stages (S1 -> S2 forward, S3 -> S4 inverse) goes through a per-warp scratch
+// area with warp-level synchronisation instead of a shared-memory pass and a CTA barrier:
+//   C14 | C2 | R (x-S1 | exchange | x-S2 | frequency op | x-S3 | exchange | x-S4) | C3
+// is four passes and four barriers per propagation step instead of six, with the same stages,
+// twiddles and order (the same values).  The spatial pass keeps the six-pass thread mapping
+// (consecutive x across a warp: coalesced global accesses); only the row pass, which touches no
+// global memory, uses the warp layout: lane 8 g + t of warp w holds task t of row
+// (w & 7) + 8 g + 32 (w >> 3), so the two rows of a half-warp differ by 8 and every 64-bit row
+// access of a warp covers all 32 banks at leading dimension 65.
+// Exchange: lane (g, a) stores its value k at scratch[72 g + a + 9 k]; lane (g, b) reads its
+// value i from scratch[72 g + i + 9 b] (both conflict-free).
+
+// per-warp exchange scratch of the row pass: one array per CTA
+__device__ __forceinline__ float2* row64_scratch() {
+  __shared__ float2 scratch[(Geo<64>::NT / 32) * 288];
+  return scratch;
+}
+
+template <int S>
+__device__ __forceinline__ void row64_line(float2 (&v)[8], const float2 (&wt)[8], float2* __restrict__ ws, int g,
+                                           int a) {
+  dft<8, S>(v);
+#pragma unroll
+  for (int k = 1; k < 8; ++k) v[k] = S < 0 ? cmul(v[k], wt[k]) : cmulc(v[k], wt[k]);   // twiddle<S>
+  __syncwarp();   // the previous exchange of this warp has read its slots
+#pragma unroll
+  for (int k = 0; k < 8; ++k) ws[72 * g + a + 9 * k] = v[k];
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = ws[72 * g + i + 9 * a];
+  dft<8, S>(v);
+}
+
+template <>
+struct PathFFT<64> {
+  using F = Field<64>;
+  static_assert(F::N1 == 8 && F::N2 == 8 && F::NT == 512 && !F::PAIRED_TW, "row pass layout");
+  static constexpr int CY = F::N1, YS = F::N2, RX = F::N2, KXS = F::N1;
+  template <int S4, int S1, bool LOAD, bool STORE, class Pre, class Op>
+  __device__ static __forceinline__ void c14(float2* A, const float2* tw, Pre pre, Op op) {
+    pass_c14<64, S4, S1, LOAD, STORE>(A, tw, pre, op);
+  }
+  template <int S>
+  __device__ static __forceinline__ void fwd_pair(float2* A, const float2* tw) {
+    pass_c23<64, false, S>(A, tw);
+  }
+  // row r (y-frequency row_freq(r)): S2 != 0 reads samples x = 8 i + t and runs x-S1, x-S2; op
+  // sees x-frequencies t + 8 i; S3 != 0 runs x-S3, x-S4 and stores samples in place
+  template <int S2, int S3, class Op>
+  __device__ static __forceinline__ void r23(float2* A, const float2* tw, Op op) {
+    constexpr int LD = F::LD;
+    const int lane = (int)(threadIdx.x & 31), w = (int)(threadIdx.x >> 5), g = lane >> 3, t = lane & 7;
+    const int r = (w & 7) + 8 * g + 32 * (w >> 3);
+    float2* ws = row64_scratch() + w * 288;
+    float2 v[8], wt[8];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) wt[k] = tw[t * k];
+    if (S2) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = A[r * LD + 8 * i + t];
+      row64_line<S2>(v, wt, ws, g, t);
+    }
+    op(v, F::row_freq(r), t);
+    if (S3) {
+      row64_line<S3>(v, wt, ws, g, t);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) A[r * LD + 8 * k + t] = v[k];
+    }
+  }
+  template <int S>
+  __device__ static __forceinline__ void inv_pair(float2* A, const float2* tw) {
+    pass_c23<64, true, S>(A, tw);
+  }
+};
 #endif
 
 }  // namespace adorym
