@@ -167,9 +167,9 @@ struct Geo;
 #endif
 // ADORYM_FOURPASS64: N = 64 fused kernels on the four-pass scheme of fft_block4.cuh (256 threads).
 // Off by default: its radix-16 stages raised the full-size tomography probe-gradient error above
-// the stored FP32 floor (1.68e-3 against a bar of 1.58e-3; the six-pass form gives 1.49e-3), and
-// the one tomography launch measured with it (scalar arithmetic) took 1.35 ms against 1.22 ms
-// for the packed six-pass form.
+// the stored FP32 floor (1.68e-3 against a bar of 1.58e-3; the radix-8 stages of the default form
+// give 1.49e-3), and the one tomography launch measured with it (scalar arithmetic) took 1.35 ms
+// against 1.22 ms for the packed six-pass form of the time.
 #ifndef ADORYM_FOURPASS64
 #define ADORYM_FOURPASS64 0
 #endif

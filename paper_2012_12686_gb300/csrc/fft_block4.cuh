@@ -1,5 +1,6 @@
 // Block-wide complex64 N x N FFT in four shared-memory passes per propagation step (N = 128, and
-// N = 64 with ADORYM_FOURPASS64).
+// N = 64 with ADORYM_FOURPASS64; by default N = 64 takes the six-pass column passes with a row
+// pass in a warp, at the end of this file, also four passes).
 //
 // The field is stored row-major in shared memory with leading dimension LD = N + 1, as in
 // fft_block.cuh, and each 1-D transform uses the same two-stage Cooley-Tukey split (stages S1..S4
